@@ -1,0 +1,410 @@
+#!/usr/bin/env python3
+"""Benchmark of the spkMC cycle on the 1024^3 Ising lattice (16^3-site domains).
+
+Metric: spin-flip events per second, null events included (one event per
+active domain per cycle, arXiv:1005.4713 Sec. 3.1 step 4).  A step is one
+pass of the whole hot path over the lattice: 10 spkMC cycles (every colour
+visited in turn) plus the observables M, E, M^2, M^4, as in the 500-cycle
+run with observables every 10 cycles.
+
+Arms:
+  default           the CUDA library through its C ABI (this package);
+  --impl reference  the CPU oracle on the host cores (no GPU), one cycle per
+                    step, same lattice and metric.
+
+Multi-GPU (torchrun, one rank per GPU): independent replicas with their own
+seeds, no collective on the data path (weak scaling); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L_BENCH, D_BENCH, SEED_BENCH = 1024, 16, 3
+CYCLES_PER_STEP = 10
+# Algorithmic bytes per event of this design (restated from the paper's
+# linear frequency-line pass, Sec. 5): the domain's 14 class counts (int32)
+# plus its spins and one-site halo bit-packed, (d^3 + 6 d^2)/8 bytes.
+def bytes_per_event(d: int) -> int:
+    return 14 * 4 + (d ** 3 + 6 * d * d) // 8
+
+
+def int8_bytes_per_event(d: int) -> int:
+    return d ** 3 + 6 * d * d
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling (NVML through ctypes, falling back to nvidia-smi)
+# ---------------------------------------------------------------------------
+REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+           0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown", 0x2: "applications_clocks",
+           0x1: "gpu_idle", 0x10: "sync_boost", 0x100: "display_clock"}
+
+
+class ClockSampler:
+    def __init__(self, device_index: int = 0, period_s: float = 0.002):
+        self.period = period_s
+        self.samples = []  # (t, sm_mhz, reasons_mask)
+        self.max_mhz = None
+        self._stop = threading.Event()
+        self._thread = None
+        self._smi = None
+        self._nvml = None
+        self._handle = ctypes.c_void_p()
+        try:
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit failed")
+            handle = ctypes.c_void_p()
+            bus = self._pci_bus_id(device_index)
+            rc = 1
+            if bus:
+                rc = nv.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(handle))
+            if rc != 0:
+                rc = nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(device_index), ctypes.byref(handle))
+            if rc != 0:
+                raise OSError("no NVML handle")
+            mx = ctypes.c_uint()
+            if nv.nvmlDeviceGetMaxClockInfo(handle, 1, ctypes.byref(mx)) == 0:
+                self.max_mhz = int(mx.value)
+            self._nvml, self._handle = nv, handle
+        except OSError:
+            self._nvml = None
+
+    @staticmethod
+    def _pci_bus_id(idx):
+        try:
+            import torch
+            return getattr(torch.cuda.get_device_properties(idx), "pci_bus_id", None)
+        except Exception:
+            return None
+
+    def _read(self):
+        nv, h = self._nvml, self._handle
+        clk = ctypes.c_uint()
+        rs = ctypes.c_ulonglong()
+        nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk))
+        fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        fn(h, ctypes.byref(rs))
+        return int(clk.value), int(rs.value)
+
+    def _loop(self):
+        while not self._stop.is_set():
+            try:
+                c, r = self._read()
+                self.samples.append((time.perf_counter(), c, r))
+            except Exception:
+                pass
+            time.sleep(self.period)
+
+    def start(self):
+        if self._nvml is not None:
+            self._thread = threading.Thread(target=self._loop, daemon=True)
+            self._thread.start()
+        else:
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active")
+            try:
+                self._smi = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                              "-lms", "50"], stdout=subprocess.PIPE, text=True)
+            except OSError:
+                self._smi = None
+        return self
+
+    def stop(self):
+        self._stop.set()
+        if self._thread:
+            self._thread.join()
+        if self._smi:
+            self._smi.terminate()
+            out, _ = self._smi.communicate()
+            for line in out.splitlines():
+                parts = [p.strip() for p in line.split(",")]
+                try:
+                    self.samples.append((0.0, int(float(parts[1])), int(parts[4], 16)))
+                    self.max_mhz = int(float(parts[2]))
+                except (ValueError, IndexError):
+                    pass
+
+    def summary(self, t0=None, t1=None):
+        s = [x for x in self.samples if t0 is None or (t0 <= x[0] <= t1) or x[0] == 0.0]
+        if not s:
+            s = self.samples
+        if not s:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": [], "samples": 0}
+        mask = 0
+        for _, _, r in s:
+            mask |= r
+        names = sorted(n for b, n in REASONS.items() if mask & b and n != "gpu_idle")
+        return {"sm_mhz": statistics.median(c for _, c, _ in s), "sm_max_mhz": self.max_mhz,
+                "reasons": names, "samples": len(s)}
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("SPKMC_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def max_over_ranks(value: float, pg, device=None) -> float:
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(pg, device=None):
+    if pg is None:
+        return
+    if device is not None:
+        pg.barrier(device_ids=[device.index])
+    else:
+        pg.barrier()
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("spkmc_kernels.cu", "spkmc_internal.h"):
+        with open(os.path.join(ROOT, "paper_1005_4713_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    for path in (os.path.join(ROOT, "MEASURED_PEAKS.json"),):
+        try:
+            with open(path) as f:
+                j = json.load(f)
+            return float(j["hbm_gbs"]), "measured"
+        except (OSError, KeyError, ValueError):
+            pass
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(workload: str):
+    """Per-launch DRAM bytes of the cycle kernel from the committed ncu
+    summary, only if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            j = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = j.get(workload)
+    if not e or e.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(rank: int, world: int, cycles: int = 8):
+    import oracle
+    cores = os.cpu_count() or 1
+    st = oracle.State(L_BENCH, D_BENCH, 1.0, 0.0, 4.5115, SEED_BENCH)
+    t0 = time.perf_counter()
+    st.run(cycles, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": cycles * st.k_act / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
+            "sample": f"{L_BENCH}^3, d={D_BENCH}, hot start seed {SEED_BENCH}, cycles 0..{cycles - 1} "
+                      f"(one visit of each colour), OpenMP over active domains, {dt:.2f} s"}
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    cores = os.cpu_count() or 1
+    st = oracle.State(L_BENCH, D_BENCH, 1.0, 0.0, 4.5115, SEED_BENCH)
+    for _ in range(args.warmup):
+        st.run(1, threads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st.run(1, threads=cores)
+    dt = time.perf_counter() - t0
+    value = args.steps * st.k_act / dt
+    line = {
+        "impl": "reference", "metric": "spin-flip events/s (incl. null) at 1024^3",
+        "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u1 spins, int32 counts, f64 clock",
+        "data": "synthetic (hot start from Philox)",
+        "config": {"workload": "spkmc-1024^3-d16", "L": L_BENCH, "domain_edge": D_BENCH, "J": 1.0,
+                   "H": 0.0, "T": 4.5115, "seed": SEED_BENCH, "cycles_per_step": 1,
+                   "impl": "CPU oracle (plain C, FP64), OpenMP over active domains"},
+        "cpu_baseline": {"value": value, "unit": "events/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} cycles of the {L_BENCH}^3 lattice after "
+                                   f"{args.warmup} warm-up cycles"},
+        "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args, world, rank, local, pg):
+    import numpy as np
+    import torch
+
+    import paper_1005_4713_gb300 as sp
+
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(device)
+    cfg = sp.torch_config()
+    seed = SEED_BENCH + rank
+    lat = sp.Lattice(L_BENCH, D_BENCH, 1.0, 0.0, 4.5115, seed, config=cfg)
+    kact = lat.K_act
+    cps = args.cycles_per_step
+
+    def step():
+        lat.run(cps)
+        return lat.observables()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(device)
+    barrier(pg, device)
+    torch.cuda.synchronize(device)
+
+    sampler = ClockSampler(local).start()
+    k0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    k1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    t_host0 = time.perf_counter()
+    e0.record(stream)
+    for i in range(args.steps):
+        k0[i].record(stream)
+        lat.run(cps)
+        k1[i].record(stream)
+        lat.observables()
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    t_host1 = time.perf_counter()
+    barrier(pg, device)
+    sampler.stop()
+    ms = e0.elapsed_time(e1)
+    kernel_ms = sum(a.elapsed_time(b) for a, b in zip(k0, k1)) / args.steps
+    ms_max = max_over_ranks(ms, pg, device)
+    events = world * args.steps * cps * kact
+    value = events / (ms_max / 1e3)
+    lat_info = lat.info()
+
+    # end to end through the C ABI with host buffers: upload the start
+    # lattice from pinned memory, run the steps with observables, read the
+    # final lattice back
+    e2e = None
+    if not args.no_e2e:
+        n = L_BENCH ** 3
+        host = torch.empty(n, dtype=torch.int8, pin_memory=True).numpy()
+        lat.spins()  # warm the read path
+        host[:] = lat.spins()
+        out = torch.empty(n, dtype=torch.int8, pin_memory=True).numpy()
+        lat2 = sp.Lattice(L_BENCH, D_BENCH, 1.0, 0.0, 4.5115, seed, cold=True, config=cfg)
+        lat2.set_spins(host)
+        lat2.run(cps)
+        lat2.observables()
+        barrier(pg, device)
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        lat2.set_spins(host)
+        for _ in range(args.steps):
+            lat2.run(cps)
+            lat2.observables()
+        sp.spkmc_get_spins(lat2.h, out)
+        t1 = time.perf_counter()
+        barrier(pg, device)
+        e2e_s = max_over_ranks(t1 - t0, pg, device)
+        obs_bytes = ctypes.sizeof(sp.spkmc_obs)
+        e2e = {"value": events / e2e_s, "unit": "events/s",
+               "h2d_bytes_per_step": n // args.steps,
+               "d2h_bytes_per_step": n // args.steps + obs_bytes}
+        lat2.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(rank, world)
+
+    if rank == 0:
+        peak, peak_kind = measured_peak()
+        bpe = bytes_per_event(D_BENCH)
+        per_launch = cps * kact * bpe
+        achieved = per_launch / (kernel_ms / 1e3) / 1e9
+        clocks = sampler.summary(t_host0, t_host1)
+        line = {
+            "metric": "spin-flip events/s (incl. null) at 1024^3",
+            "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "u1 spins (bit-packed), int32 counts, f64 rates and clock",
+            "data": "synthetic (hot start from Philox, seed 3 + rank)",
+            "config": {"workload": "spkmc-1024^3-d16", "L": L_BENCH, "domain_edge": D_BENCH,
+                       "J": 1.0, "H": 0.0, "T": 4.5115, "seed": SEED_BENCH,
+                       "cycles_per_step": cps, "events_per_cycle": kact,
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "l2": "working set %.0f MB > 126 MB L2, no flush" % (lat_info.device_bytes / 1e6),
+                       "grid_ctas": lat_info.grid_ctas, "threads_per_cta": lat_info.threads_per_cta},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": ncu_traffic("spkmc-1024^3-d16"),
+                         "peak_kind": peak_kind, "kernel": "spkmc_cycles_kernel",
+                         "bytes_per_event": bpe, "kernel_ms_per_launch": kernel_ms,
+                         "int8_equivalent_GBps": cps * kact * int8_bytes_per_event(D_BENCH) / (kernel_ms / 1e3) / 1e9},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 2 * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    lat.close()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--cycles-per-step", type=int, default=CYCLES_PER_STEP)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local, pg = dist_setup(args.gpus)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, world, rank)
+        return run_gpu(args, world, rank, local, pg)
+    finally:
+        if pg is not None:
+            pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,224 @@
+/*
+ * spkmc.h -- C ABI of the GB300 spkMC library (libspkmc.so).
+ *
+ * The library runs the synchronous parallel kinetic Monte Carlo (spkMC) cycle
+ * of Martinez, Monasterio and Marian, arXiv:1005.4713, Sec. 3.1 (steps 1-6)
+ * with the chessboard sublattice of Sec. 3.2, on periodic simple-cubic 3D
+ * Ising lattices (Eq. 1) with Glauber rates (Eq. 3), on one CUDA GPU.
+ *
+ * Conventions shared by every entry point:
+ *   - lattice edge L, domain edge d, nd = L/d domains per axis; L % (2d) == 0
+ *     (nd even, so the 8 colours tile the lattice) and d in {2, 4, 8, 16};
+ *   - site (X,Y,Z), global index g = X + L*(Y + L*Z) (x fastest); spins are
+ *     exchanged with the host as int8 +1/-1 in that order;
+ *   - domain (dx,dy,dz), index k = dx + nd*(dy + nd*dz); local site
+ *     l = x + d*(y + d*z); colour = (dx&1) | (dy&1)<<1 | (dz&1)<<2; cycle t
+ *     works on colour t % 8 (Sec. 3.2 step 4a, deterministic rotation);
+ *   - class of a site = 7*[sigma = +1] + (number of up neighbours), 0..13;
+ *     rate r = 1/(1 + exp(2 sigma (J S + H) / T)), S = sum of the 6
+ *     neighbour spins, lambda = 1, k_B = 1 (Eq. 3 read as Glauber dynamics);
+ *   - random numbers: Philox4x64-10 keyed by (seed, 0); counter (t, k, 1, 0)
+ *     for the event of domain k in cycle t, (t, 0, 2, 0) for the clock,
+ *     (g/256, 0, 3, 0) for the hot start.
+ *
+ * Ownership: the library owns all device memory it allocates (through the
+ * optional allocator callbacks of spkmc_config, else stream-ordered
+ * cudaMallocAsync) and runs all work on the configured stream.  Host buffers
+ * passed in belong to the caller and are not retained after the call returns.
+ *
+ * Errors: every int-returning entry point returns SPKMC_OK (0) or one of the
+ * codes below; spkmc_last_error() gives a thread-local message.  A handle is
+ * never left partially constructed: a failed create returns no handle.
+ * Work is asynchronous on the stream: errors raised inside a kernel (a grid
+ * barrier that timed out, an internal inconsistency) are reported by the next
+ * entry point that synchronises (spkmc_synchronize, spkmc_observables,
+ * spkmc_get_*), after which the handle refuses to run until spkmc_set_state.
+ */
+#ifndef SPKMC_H
+#define SPKMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPKMC_OK 0
+#define SPKMC_EINVAL 1    /* invalid argument (message says which) */
+#define SPKMC_ENOMEM 2    /* device or host allocation failed */
+#define SPKMC_ECUDA 3     /* a CUDA runtime call failed */
+#define SPKMC_ETIMEOUT 4  /* a grid barrier gave up after its time limit */
+#define SPKMC_EBUSY 5     /* no free slot, or the budget does not allow it */
+#define SPKMC_EINTERNAL 6 /* the device found its class counts inconsistent */
+
+#define SPKMC_INIT_HOT 0  /* uniform +-1 spins from Philox (g/256, 0, 3, 0) */
+#define SPKMC_INIT_COLD 1 /* all spins +1 (the relaxation start of Sec. 6) */
+
+typedef struct spkmc_engine spkmc_t;
+typedef struct spkmc_batch spkmc_batch_t;
+
+/* Allocator callbacks: alloc returns device memory of at least `bytes` bytes
+ * usable on `stream` (NULL on failure); free releases it.  `ctx` is passed
+ * through unchanged. */
+typedef void *(*spkmc_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*spkmc_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+
+/* Physics and start state of one lattice (Eq. 1, Eq. 3). */
+typedef struct spkmc_params {
+    int32_t L;                  /* lattice edge */
+    int32_t domain_edge;        /* d in {2,4,8,16}; 0 = pick by a fixed rule */
+    double J;                   /* coupling (finite) */
+    double H;                   /* field (finite) */
+    double T;                   /* temperature in J/k_B units (> 0, finite) */
+    uint64_t seed;              /* Philox key word 0 */
+    int32_t init;               /* SPKMC_INIT_HOT or SPKMC_INIT_COLD */
+    int32_t reserved0;
+    int64_t event_log_capacity; /* events kept (see spkmc_event); 0 = off */
+} spkmc_params;
+
+/* Engine runtime: stream, allocator and launch geometry. */
+typedef struct spkmc_config {
+    void *stream;               /* cudaStream_t; NULL = a stream of the library's own */
+    spkmc_alloc_fn alloc;       /* NULL = cudaMallocAsync on the stream */
+    spkmc_free_fn free;
+    void *alloc_ctx;
+    int32_t device;             /* CUDA device ordinal; -1 = current device */
+    int32_t ctas_per_sm;        /* persistent grid: CTAs per SM; 0 = occupancy limit */
+    int32_t max_ctas;           /* cap on the grid; 0 = no cap */
+    int32_t items_per_cta;      /* target active domains per CTA; 0 = 64 */
+    int64_t barrier_timeout_ns; /* grid-barrier time limit; 0 = 2 s */
+    int32_t debug_skip_arrival_cta; /* fault test: that CTA never arrives; -1 = off */
+    int32_t reserved1;
+} spkmc_config;
+
+/* Observables (Eq. 1, Eq. 4, Eq. 7 moments and the Eq. 10 counters). */
+typedef struct spkmc_obs {
+    int64_t cycle;              /* cycles done */
+    double clock;               /* sum of dt = -ln(xi)/R_max (Sec. 3.1 step 5) */
+    int64_t M;                  /* sum of spins */
+    int64_t B;                  /* sum over sites of sigma_i (sigma_{+x}+sigma_{+y}+sigma_{+z}) */
+    double E;                   /* -J*B - H*M */
+    double m;                   /* M / N */
+    double m2;                  /* m^2 */
+    double m4;                  /* m^4 */
+    int64_t n_flip;             /* flip events so far */
+    int64_t n_null;             /* null events so far */
+    double sum_null_rate;       /* sum over cycles and active domains of R_max - R_k */
+    uint64_t sum_null_rate_fx[2]; /* the same, exact: sum of floor((R_max-R_k) 2^64), lo, hi */
+    int32_t L;
+    int32_t domain_edge;
+} spkmc_obs;
+
+/* One event of one active domain in one cycle (debug and parity log). */
+typedef struct spkmc_event {
+    int64_t cycle;              /* lattice-local cycle t */
+    int32_t domain;             /* k */
+    int32_t cls;                /* chosen class 0..13, or -1 for the null event */
+    int32_t site;               /* local site l of the flipped spin, or -1 */
+    int32_t reserved;
+} spkmc_event;
+
+/* Checkpoint scalars; spins are saved with spkmc_get_spins. */
+typedef struct spkmc_state {
+    int64_t cycle;
+    double clock;
+    int64_t n_flip;
+    int64_t n_null;
+    uint64_t sum_null_rate_fx[2];
+} spkmc_state;
+
+/* Sizes of a created lattice. */
+typedef struct spkmc_info {
+    int32_t L, domain_edge, nd, reserved;
+    int64_t K;                  /* domains */
+    int64_t K_act;              /* active domains (events) per cycle = K/8 */
+    int64_t device_bytes;       /* device memory held for this lattice */
+    int32_t grid_ctas;          /* CTAs of the persistent launch */
+    int32_t threads_per_cta;
+} spkmc_info;
+
+/* ---- defaults ---------------------------------------------------------- */
+void spkmc_params_init(spkmc_params *p);   /* L=16, d=4, J=1, H=0, T=4.5115, seed=1, hot */
+void spkmc_config_init(spkmc_config *c);   /* all defaults (NULL stream, own allocator) */
+
+/* Host-side rate table r[14] of Eq. 3 (read as Glauber), class order above,
+ * evaluated in FP64 with the C library's exp.  Returns EINVAL unless T > 0
+ * and J, H, T are finite. */
+int spkmc_rate_table(double J, double H, double T, double out[14]);
+
+/* Domain edge used for L when domain_edge = 0: the largest d in {16,8,4,2}
+ * with L % (2d) == 0, or 0 if none. */
+int32_t spkmc_resolve_domain_edge(int32_t L);
+
+/* Device bytes one lattice of these parameters holds (0 if invalid). */
+int64_t spkmc_bytes_required(const spkmc_params *p);
+
+/* ---- single lattice ---------------------------------------------------- */
+/* Create a lattice with a hot start (Sec. 3.1, the system to be partitioned).
+ * EINVAL unless L % (2d) == 0, d in {2,4,8,16} (or 0), T > 0 and all finite. */
+int spkmc_create(int32_t L, int32_t domain_edge, double J, double H, double T,
+                 uint64_t seed, spkmc_t **out);
+/* Same with every parameter; cfg may be NULL for defaults. */
+int spkmc_create_ex(const spkmc_params *p, const spkmc_config *cfg, spkmc_t **out);
+/* Release everything; NULL-safe.  Synchronises the stream first. */
+void spkmc_destroy(spkmc_t *h);
+/* Enqueue ncycles spkMC cycles (Sec. 3.1 steps 1-6, one colour per cycle) as
+ * one persistent cooperative launch; ncycles >= 0 (0 is a no-op). */
+int spkmc_run_cycles(spkmc_t *h, int64_t ncycles);
+/* Wait for the stream and report kernel-side errors (ETIMEOUT, EINTERNAL). */
+int spkmc_synchronize(spkmc_t *h);
+/* Synchronise and compute the observables on the device. */
+int spkmc_observables(spkmc_t *h, spkmc_obs *out);
+/* Copy spins to/from a host int8 buffer of n = L^3 entries in global order.
+ * set_spins recomputes the face mirrors and class counts on the device. */
+int spkmc_get_spins(spkmc_t *h, int8_t *host_buf, size_t n);
+int spkmc_set_spins(spkmc_t *h, const int8_t *host_buf, size_t n);
+/* Copy up to cap logged events (cycle-major, ascending k within a cycle);
+ * n_out receives the number copied.  The log holds the first
+ * event_log_capacity events after create or spkmc_clear_event_log. */
+int spkmc_get_event_log(spkmc_t *h, spkmc_event *buf, size_t cap, size_t *n_out);
+int spkmc_clear_event_log(spkmc_t *h);
+/* Checkpoint scalars (with get/set_spins the state is complete: the random
+ * numbers are counter-based, so a resumed run is bit-identical). */
+int spkmc_get_state(spkmc_t *h, spkmc_state *out);
+int spkmc_set_state(spkmc_t *h, const spkmc_state *in);
+/* Maintained class counts, n = 14*K int32 in domain order. */
+int spkmc_class_counts(spkmc_t *h, int32_t *host_counts, size_t n);
+/* Recount every domain from the spins on the device and report how many
+ * domains differ from the maintained counts (0 when consistent). */
+int spkmc_check_counts(spkmc_t *h, int64_t *mismatched_domains);
+int spkmc_info_get(spkmc_t *h, spkmc_info *out);
+
+/* ---- batched and served ensembles --------------------------------------- */
+/* A batch holds up to `capacity` independent lattices (slots) that advance
+ * together in one persistent launch over a flat table of their active
+ * domains; each lattice keeps its own R_max, clock, cycle counter and
+ * random streams, so its trajectory is bit-identical to a solo run. */
+int spkmc_batch_create(int32_t capacity, const spkmc_config *cfg, spkmc_batch_t **out);
+void spkmc_batch_destroy(spkmc_batch_t *b);
+/* Admit a lattice into a free slot with a budget of `cycles` cycles
+ * (< 0: unlimited).  EBUSY when no slot is free. */
+int spkmc_batch_admit(spkmc_batch_t *b, const spkmc_params *p, int64_t cycles, int32_t *slot);
+/* Run up to `cycles` cycles; each lattice stops at its own budget. */
+int spkmc_batch_run(spkmc_batch_t *b, int64_t cycles);
+/* Synchronise and list slots whose budget is spent and that were not listed
+ * before (at most cap); n receives the count. */
+int spkmc_batch_poll(spkmc_batch_t *b, int32_t *done_slots, int32_t cap, int32_t *n);
+/* Free a slot's device memory; the slot may be admitted again. */
+int spkmc_batch_retire(spkmc_batch_t *b, int32_t slot);
+int spkmc_batch_synchronize(spkmc_batch_t *b);
+int spkmc_batch_observables(spkmc_batch_t *b, int32_t slot, spkmc_obs *out);
+int spkmc_batch_get_spins(spkmc_batch_t *b, int32_t slot, int8_t *host_buf, size_t n);
+int spkmc_batch_get_event_log(spkmc_batch_t *b, int32_t slot, spkmc_event *buf, size_t cap,
+                              size_t *n_out);
+/* Number of admitted (not retired) slots and device bytes they hold. */
+int spkmc_batch_usage(spkmc_batch_t *b, int32_t *live_slots, int64_t *device_bytes);
+
+/* Thread-local description of the last error of this thread. */
+const char *spkmc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPKMC_H */

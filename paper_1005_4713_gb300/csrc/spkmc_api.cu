@@ -1,0 +1,945 @@
+// spkmc_api.cu -- host runtime behind the C ABI declared in include/spkmc.h.
+//
+// A batch owns up to `capacity` lattices (slots).  Each slot holds its device
+// arrays (rows, mirrors, counts, scratch, optional event log) and one entry
+// of the device descriptor and state tables.  A run enqueues one persistent
+// cooperative launch over the flat table of the running lattices' active
+// domains (segments sorted by slot).  A single-lattice handle is a batch of
+// capacity one.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "spkmc_internal.h"
+
+using namespace spkmc;
+
+namespace {
+
+thread_local std::string g_last_error = "no error";
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(SPKMC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(expr, what)                                                                       \
+    do {                                                                                           \
+        cudaError_t e_ = (expr);                                                                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);                                         \
+    } while (0)
+
+bool valid_edge(int d)
+{
+    return d == 2 || d == 4 || d == 8 || d == 16;
+}
+
+// Rate table of Eq. 3 read as Glauber dynamics: r = 1/(1 + exp(2 sigma (J S + H)/T)),
+// class c = 7*[sigma=+1] + u, S = 2u - 6; FP64 with the C library's exp and
+// no contraction (the host compiler runs with -ffp-contract=off).
+void host_rates(double J, double H, double T, double r[kClasses])
+{
+    for (int c = 0; c < kClasses; ++c) {
+        const double sigma = c >= 7 ? 1.0 : -1.0;
+        const double S = (double)(2 * (c % 7) - 6);
+        double field = J * S;
+        field = field + H;
+        const double dE = 2.0 * sigma * field;
+        const double x = dE / T;
+        r[c] = 1.0 / (1.0 + std::exp(x));
+    }
+}
+
+int check_params(const spkmc_params *p, int *d_out)
+{
+    if (!p) return fail(SPKMC_EINVAL, "params is NULL");
+    if (!std::isfinite(p->J) || !std::isfinite(p->H)) return fail(SPKMC_EINVAL, "J and H must be finite");
+    if (!(p->T > 0.0) || !std::isfinite(p->T)) return fail(SPKMC_EINVAL, "T must be finite and > 0");
+    if (p->L <= 0) return fail(SPKMC_EINVAL, "L must be positive (got %d)", p->L);
+    int d = p->domain_edge;
+    if (d == 0) d = spkmc_resolve_domain_edge(p->L);
+    if (!valid_edge(d))
+        return fail(SPKMC_EINVAL, "domain edge must be 2, 4, 8 or 16 (got %d for L=%d)",
+                    p->domain_edge, p->L);
+    if (p->L % (2 * d) != 0)
+        return fail(SPKMC_EINVAL, "L %% (2d) must be 0 so the 8 colours tile the lattice (L=%d, d=%d)",
+                    p->L, d);
+    if (p->init != SPKMC_INIT_HOT && p->init != SPKMC_INIT_COLD)
+        return fail(SPKMC_EINVAL, "init must be SPKMC_INIT_HOT or SPKMC_INIT_COLD");
+    if (p->event_log_capacity < 0) return fail(SPKMC_EINVAL, "event_log_capacity must be >= 0");
+    const long long nd = p->L / d;
+    if (nd * nd * nd > (1LL << 31) - 1) return fail(SPKMC_EINVAL, "too many domains (L/d)^3 for int32 ids");
+    *d_out = d;
+    return SPKMC_OK;
+}
+
+struct Sizes {
+    long long K, Kact, rows_b, mirrors_b, counts_b, scratch_b, log_b;
+    long long total() const { return rows_b + mirrors_b + counts_b + scratch_b + log_b; }
+};
+
+Sizes sizes_of(int L, int d, long long log_cap)
+{
+    Sizes s;
+    const long long nd = L / d;
+    s.K = nd * nd * nd;
+    s.Kact = s.K / 8;
+    auto up = [](long long b) { return (b + 255) & ~255LL; };
+    s.rows_b = up(s.K * d * d * 2);
+    s.mirrors_b = up(s.K * 4 * d * 2);
+    s.counts_b = up(s.K * kCountStride * 4);
+    s.scratch_b = up(s.Kact * kScratchStride * 8);
+    s.log_b = up(log_cap * (long long)sizeof(spkmc_event));
+    return s;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (dev < 0) return;
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+            cudaSetDevice(dev);
+            changed = true;
+        }
+    }
+    ~DeviceGuard()
+    {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+} // namespace
+
+struct Slot {
+    bool live = false;
+    bool done_reported = false;
+    spkmc_params params{};
+    int d = 0;
+    Sizes sz{};
+    LatticeDesc desc{};   // host copy of the device descriptor
+    long long t = 0;      // host mirror of the cycle counter
+    long long budget = -1;
+    void *blocks[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    size_t block_bytes[5] = {0, 0, 0, 0, 0};
+};
+
+struct spkmc_batch {
+    spkmc_config cfg{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int capacity = 0;
+    std::vector<Slot> slots;
+    LatticeDesc *d_desc = nullptr;
+    LatticeState *d_state = nullptr;
+    Segment *d_seg = nullptr;
+    unsigned *d_bar = nullptr;
+    int *d_err = nullptr;
+    long long *d_MB = nullptr;
+    unsigned long long *d_mismatch = nullptr;
+    // pinned host staging
+    LatticeDesc *h_desc = nullptr;
+    LatticeState *h_state = nullptr;
+    Segment *h_seg = nullptr;
+    int *h_err = nullptr;
+    long long *h_MB = nullptr;
+    int sm_count = 0;
+    int max_blocks_per_sm = 0;
+    int last_grid = 0;
+    int sticky_error = SPKMC_OK;
+    std::vector<Segment> uploaded_seg; // segment table currently on the device
+    long long live_bytes = 0;
+
+    void *dev_alloc(size_t bytes)
+    {
+        if (bytes == 0) bytes = 256;
+        if (cfg.alloc) return cfg.alloc(bytes, (void *)stream, cfg.alloc_ctx);
+        void *p = nullptr;
+        if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return p;
+    }
+    void dev_free(void *p, size_t bytes)
+    {
+        if (!p) return;
+        if (cfg.free) cfg.free(p, bytes, (void *)stream, cfg.alloc_ctx);
+        else cudaFreeAsync(p, stream);
+    }
+};
+
+struct spkmc_engine {
+    spkmc_batch *b = nullptr;
+    int slot = 0;
+};
+
+namespace {
+
+void free_slot_memory(spkmc_batch *b, Slot &s)
+{
+    for (int i = 0; i < 5; ++i) {
+        b->dev_free(s.blocks[i], s.block_bytes[i]);
+        s.blocks[i] = nullptr;
+        s.block_bytes[i] = 0;
+    }
+}
+
+void release_batch(spkmc_batch *b)
+{
+    if (!b) return;
+    DeviceGuard g(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (auto &s : b->slots)
+        if (s.live) free_slot_memory(b, s);
+    cudaFree(b->d_desc);
+    cudaFree(b->d_state);
+    cudaFree(b->d_seg);
+    cudaFree(b->d_bar);
+    cudaFree(b->d_err);
+    cudaFree(b->d_MB);
+    cudaFree(b->d_mismatch);
+    cudaFreeHost(b->h_desc);
+    cudaFreeHost(b->h_state);
+    cudaFreeHost(b->h_seg);
+    cudaFreeHost(b->h_err);
+    cudaFreeHost(b->h_MB);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+int batch_new(int capacity, const spkmc_config *cfg, spkmc_batch **out)
+{
+    if (!out) return fail(SPKMC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (capacity < 1) return fail(SPKMC_EINVAL, "capacity must be >= 1");
+    spkmc_batch *b = new (std::nothrow) spkmc_batch();
+    if (!b) return fail(SPKMC_ENOMEM, "host allocation failed");
+    if (cfg) b->cfg = *cfg;
+    else spkmc_config_init(&b->cfg);
+    if (b->cfg.device >= 0) {
+        b->device = b->cfg.device;
+    } else if (cudaGetDevice(&b->device) != cudaSuccess) {
+        delete b;
+        return fail(SPKMC_ECUDA, "no CUDA device");
+    }
+    DeviceGuard g(b->device);
+    auto bail = [&](int code) {
+        release_batch(b);
+        return code;
+    };
+    if (b->cfg.stream) {
+        b->stream = (cudaStream_t)b->cfg.stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreate"));
+        b->own_stream = true;
+    }
+    b->capacity = capacity;
+    b->slots.resize(capacity);
+    cudaError_t e = cudaSuccess;
+    if ((e = cudaMalloc(&b->d_desc, sizeof(LatticeDesc) * capacity)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_state, sizeof(LatticeState) * capacity)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_seg, sizeof(Segment) * capacity)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_bar, 256)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_err, 256)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_MB, 256)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_mismatch, 256)) != cudaSuccess ||
+        (e = cudaMallocHost(&b->h_desc, sizeof(LatticeDesc) * capacity)) != cudaSuccess ||
+        (e = cudaMallocHost(&b->h_state, sizeof(LatticeState) * capacity)) != cudaSuccess ||
+        (e = cudaMallocHost(&b->h_seg, sizeof(Segment) * capacity)) != cudaSuccess ||
+        (e = cudaMallocHost(&b->h_err, 256)) != cudaSuccess ||
+        (e = cudaMallocHost(&b->h_MB, 256)) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(e == cudaErrorMemoryAllocation ? fail(SPKMC_ENOMEM, "batch tables: out of memory")
+                                                   : cuda_fail(e, "batch tables"));
+    }
+    std::memset(b->h_desc, 0, sizeof(LatticeDesc) * capacity);
+    std::memset(b->h_state, 0, sizeof(LatticeState) * capacity);
+    if ((e = cudaMemsetAsync(b->d_desc, 0, sizeof(LatticeDesc) * capacity, b->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(b->d_state, 0, sizeof(LatticeState) * capacity, b->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(b->d_err, 0, 256, b->stream)) != cudaSuccess)
+        return bail(cuda_fail(e, "batch init"));
+    if ((e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device)) !=
+        cudaSuccess)
+        return bail(cuda_fail(e, "device attributes"));
+    b->max_blocks_per_sm = cycle_kernel_max_blocks_per_sm(b->device);
+    if (b->max_blocks_per_sm < 1) return bail(fail(SPKMC_ECUDA, "cycle kernel cannot be resident"));
+    *out = b;
+    return SPKMC_OK;
+}
+
+// Report and latch a device-side error; ETIMEOUT / EINTERNAL make the batch
+// refuse further runs.
+int sync_and_check(spkmc_batch *b)
+{
+    if (b->sticky_error) return fail(b->sticky_error, "batch stopped after an earlier device error (%d)",
+                                     b->sticky_error);
+    CUDA_TRY(cudaMemcpyAsync(b->h_err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream),
+             "read error flag");
+    CUDA_TRY(cudaStreamSynchronize(b->stream), "stream synchronize");
+    if (*b->h_err != 0) {
+        b->sticky_error = *b->h_err;
+        if (*b->h_err == SPKMC_ETIMEOUT)
+            return fail(SPKMC_ETIMEOUT, "a grid barrier timed out on the device");
+        return fail(*b->h_err, "device reported inconsistent class counts");
+    }
+    return SPKMC_OK;
+}
+
+int upload_slot(spkmc_batch *b, int slot)
+{
+    b->h_desc[slot] = b->slots[slot].desc;
+    CUDA_TRY(cudaMemcpyAsync(b->d_desc + slot, b->h_desc + slot, sizeof(LatticeDesc),
+                             cudaMemcpyHostToDevice, b->stream),
+             "upload descriptor");
+    CUDA_TRY(cudaMemcpyAsync(b->d_state + slot, b->h_state + slot, sizeof(LatticeState),
+                             cudaMemcpyHostToDevice, b->stream),
+             "upload state");
+    // the pinned staging entries are rewritten only after a synchronisation
+    CUDA_TRY(cudaStreamSynchronize(b->stream), "stream synchronize");
+    return SPKMC_OK;
+}
+
+int refresh_derived(spkmc_batch *b, const LatticeDesc &d)
+{
+    int rc;
+    if ((rc = launch_build_mirrors(d, b->stream)) != SPKMC_OK) return cuda_fail(cudaGetLastError(), "mirrors");
+    if ((rc = launch_count_classes(d, 0, nullptr, b->stream)) != SPKMC_OK)
+        return cuda_fail(cudaGetLastError(), "class counts");
+    return SPKMC_OK;
+}
+
+int admit(spkmc_batch *b, const spkmc_params *p, long long cycles, int slot_hint, int *slot_out)
+{
+    int d = 0;
+    int rc = check_params(p, &d);
+    if (rc) return rc;
+    if (b->sticky_error) return fail(b->sticky_error, "batch stopped after an earlier device error");
+    int slot = slot_hint;
+    if (slot < 0) {
+        for (int i = 0; i < b->capacity; ++i)
+            if (!b->slots[i].live) {
+                slot = i;
+                break;
+            }
+    }
+    if (slot < 0 || slot >= b->capacity || b->slots[slot].live) return fail(SPKMC_EBUSY, "no free slot");
+    DeviceGuard g(b->device);
+    CUDA_TRY(cudaStreamSynchronize(b->stream), "stream synchronize");
+    Slot &s = b->slots[slot];
+    s = Slot();
+    s.params = *p;
+    s.params.domain_edge = d;
+    s.d = d;
+    s.sz = sizes_of(p->L, d, p->event_log_capacity);
+    const long long bytes[5] = {s.sz.rows_b, s.sz.mirrors_b, s.sz.counts_b, s.sz.scratch_b, s.sz.log_b};
+    for (int i = 0; i < 5; ++i) {
+        if (bytes[i] == 0) continue;
+        s.blocks[i] = b->dev_alloc((size_t)bytes[i]);
+        s.block_bytes[i] = (size_t)bytes[i];
+        if (!s.blocks[i]) {
+            free_slot_memory(b, s);
+            cudaGetLastError();
+            return fail(SPKMC_ENOMEM, "device allocation of %lld bytes failed", bytes[i]);
+        }
+    }
+    LatticeDesc &D = s.desc;
+    D.rows = (uint16_t *)s.blocks[0];
+    D.mirrors = (uint16_t *)s.blocks[1];
+    D.counts = (int32_t *)s.blocks[2];
+    D.scratch = (double *)s.blocks[3];
+    D.log = p->event_log_capacity > 0 ? (spkmc_event *)s.blocks[4] : nullptr;
+    D.log_cap = p->event_log_capacity;
+    D.log_t0 = 0;
+    host_rates(p->J, p->H, p->T, D.rate);
+    D.seed = p->seed;
+    D.L = p->L;
+    D.d = d;
+    D.nd = p->L / d;
+    D.half = D.nd / 2;
+    D.K = s.sz.K;
+    D.Kact = s.sz.Kact;
+    std::memset(&b->h_state[slot], 0, sizeof(LatticeState));
+    b->h_state[slot].budget = cycles;
+    s.t = 0;
+    s.budget = cycles;
+    rc = upload_slot(b, slot);
+    if (!rc) rc = launch_init_rows(D, p->init, b->stream);
+    if (!rc) rc = refresh_derived(b, D);
+    if (rc) {
+        free_slot_memory(b, s);
+        s.live = false;
+        return rc == SPKMC_ECUDA ? rc : fail(rc, "lattice initialisation failed");
+    }
+    s.live = true;
+    b->live_bytes += s.sz.total();
+    b->uploaded_seg.clear();
+    *slot_out = slot;
+    return SPKMC_OK;
+}
+
+// One persistent launch (or several, in chunks) over the running lattices.
+int run(spkmc_batch *b, long long cycles)
+{
+    if (cycles < 0) return fail(SPKMC_EINVAL, "ncycles must be >= 0");
+    if (b->sticky_error) return fail(b->sticky_error, "batch stopped after an earlier device error");
+    DeviceGuard g(b->device);
+    const long long kChunk = 1LL << 18;
+    while (cycles > 0) {
+        const long long n = std::min(cycles, kChunk);
+        // segments of the lattices that still have cycles to run
+        std::vector<Segment> segs;
+        long long Q = 0;
+        int parity = -2;
+        for (int i = 0; i < b->capacity; ++i) {
+            Slot &s = b->slots[i];
+            if (!s.live || s.budget == 0) continue;
+            Segment sg;
+            sg.base = Q;
+            sg.slot = i;
+            sg.pad = 0;
+            segs.push_back(sg);
+            Q += s.sz.Kact;
+            const int par = (int)(s.t & 1);
+            parity = parity == -2 ? par : (parity == par ? parity : -1);
+        }
+        const int nseg = (int)segs.size();
+        if (nseg == 0) return SPKMC_OK;
+        bool same = segs.size() == b->uploaded_seg.size();
+        for (size_t i = 0; same && i < segs.size(); ++i)
+            same = segs[i].base == b->uploaded_seg[i].base && segs[i].slot == b->uploaded_seg[i].slot;
+        if (!same) {
+            CUDA_TRY(cudaStreamSynchronize(b->stream), "stream synchronize"); // pinned staging reuse
+            std::memcpy(b->h_seg, segs.data(), sizeof(Segment) * nseg);
+            CUDA_TRY(cudaMemcpyAsync(b->d_seg, b->h_seg, sizeof(Segment) * nseg, cudaMemcpyHostToDevice,
+                                     b->stream),
+                     "upload segments");
+            b->uploaded_seg = segs;
+        }
+        // grid: enough CTAs for ~items_per_cta active domains each, within co-residency
+        const int per_sm = b->cfg.ctas_per_sm > 0 ? std::min(b->cfg.ctas_per_sm, b->max_blocks_per_sm)
+                                                  : b->max_blocks_per_sm;
+        long long gmax = (long long)per_sm * b->sm_count;
+        if (b->cfg.max_ctas > 0) gmax = std::min<long long>(gmax, b->cfg.max_ctas);
+        const long long ipc = b->cfg.items_per_cta > 0 ? b->cfg.items_per_cta : 64;
+        long long grid = std::max(1LL, std::min(gmax, (Q + ipc - 1) / ipc));
+        // every CTA must see at most kMaxSegPerCta lattices
+        for (;;) {
+            int worst = 0;
+            int si = 0;
+            for (long long c = 0; c < grid; ++c) {
+                const long long lo = Q * c / grid, hi = Q * (c + 1) / grid;
+                while (si + 1 < nseg && segs[si + 1].base <= lo) ++si;
+                int sj = si, cnt = 0;
+                while (sj < nseg && segs[sj].base < hi) {
+                    ++cnt;
+                    ++sj;
+                }
+                worst = std::max(worst, cnt);
+            }
+            if (worst <= kMaxSegPerCta) break;
+            if (grid >= gmax) return fail(SPKMC_EINVAL, "too many small lattices for one launch");
+            grid = std::min(gmax, grid * 2);
+        }
+        CUDA_TRY(cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned), b->stream), "reset barrier");
+        LaunchParams P{};
+        P.desc = b->d_desc;
+        P.state = b->d_state;
+        P.seg = b->d_seg;
+        P.nseg = nseg;
+        P.parity0 = parity < 0 ? -1 : parity;
+        P.Q = Q;
+        P.ncycles = n;
+        P.bar = b->d_bar;
+        P.err = b->d_err;
+        P.timeout_ns = b->cfg.barrier_timeout_ns > 0 ? b->cfg.barrier_timeout_ns : 2000000000LL;
+        P.skip_cta = b->cfg.debug_skip_arrival_cta;
+        int rc = launch_cycles(P, (int)grid, b->stream, grid > 1);
+        if (rc) return cuda_fail(cudaGetLastError(), "persistent cycle launch");
+        b->last_grid = (int)grid;
+        for (int i = 0; i < nseg; ++i) {
+            Slot &s = b->slots[segs[i].slot];
+            const long long part = s.budget < 0 ? n : std::min(n, s.budget);
+            s.t += part;
+            if (s.budget >= 0) s.budget -= part;
+        }
+        cycles -= n;
+    }
+    return SPKMC_OK;
+}
+
+int slot_check(spkmc_batch *b, int slot)
+{
+    if (!b) return fail(SPKMC_EINVAL, "handle is NULL");
+    if (slot < 0 || slot >= b->capacity || !b->slots[slot].live)
+        return fail(SPKMC_EINVAL, "slot %d is not live", slot);
+    return SPKMC_OK;
+}
+
+int read_state(spkmc_batch *b, int slot, LatticeState *st)
+{
+    CUDA_TRY(cudaMemcpyAsync(&b->h_state[slot], b->d_state + slot, sizeof(LatticeState),
+                             cudaMemcpyDeviceToHost, b->stream),
+             "read state");
+    int rc = sync_and_check(b);
+    if (rc) return rc;
+    *st = b->h_state[slot];
+    return SPKMC_OK;
+}
+
+int observables(spkmc_batch *b, int slot, spkmc_obs *out)
+{
+    int rc = slot_check(b, slot);
+    if (rc) return rc;
+    if (!out) return fail(SPKMC_EINVAL, "out is NULL");
+    DeviceGuard g(b->device);
+    const Slot &s = b->slots[slot];
+    CUDA_TRY(cudaMemsetAsync(b->d_MB, 0, 2 * sizeof(long long), b->stream), "clear observables");
+    if ((rc = launch_observables(s.desc, b->d_MB, b->stream)) != SPKMC_OK)
+        return cuda_fail(cudaGetLastError(), "observables kernel");
+    CUDA_TRY(cudaMemcpyAsync(b->h_MB, b->d_MB, 2 * sizeof(long long), cudaMemcpyDeviceToHost, b->stream),
+             "read observables");
+    LatticeState st;
+    if ((rc = read_state(b, slot, &st)) != SPKMC_OK) return rc;
+    const double N = (double)s.params.L * s.params.L * s.params.L;
+    std::memset(out, 0, sizeof(*out));
+    out->cycle = st.t;
+    out->clock = st.clock;
+    out->M = b->h_MB[0];
+    out->B = b->h_MB[1];
+    out->E = -s.params.J * (double)out->B - s.params.H * (double)out->M;
+    out->m = (double)out->M / N;
+    out->m2 = out->m * out->m;
+    out->m4 = out->m2 * out->m2;
+    out->n_flip = (int64_t)st.n_flip;
+    out->n_null = (int64_t)st.n_null;
+    out->sum_null_rate_fx[0] = st.null_fx_lo;
+    out->sum_null_rate_fx[1] = st.null_fx_hi;
+    out->sum_null_rate = std::ldexp((double)st.null_fx_hi, 0) + std::ldexp((double)st.null_fx_lo, -64);
+    out->L = s.params.L;
+    out->domain_edge = s.d;
+    return SPKMC_OK;
+}
+
+int get_spins(spkmc_batch *b, int slot, int8_t *host, size_t n)
+{
+    int rc = slot_check(b, slot);
+    if (rc) return rc;
+    const Slot &s = b->slots[slot];
+    const size_t N = (size_t)s.params.L * s.params.L * s.params.L;
+    if (!host || n != N) return fail(SPKMC_EINVAL, "host buffer must hold L^3 = %zu int8", N);
+    DeviceGuard g(b->device);
+    if ((rc = sync_and_check(b)) != SPKMC_OK) return rc;
+    int8_t *tmp = (int8_t *)b->dev_alloc(N);
+    if (!tmp) return fail(SPKMC_ENOMEM, "device allocation of %zu bytes failed", N);
+    rc = launch_unpack_rows(s.desc, tmp, b->stream);
+    cudaError_t e = rc ? cudaGetLastError()
+                       : cudaMemcpyAsync(host, tmp, N, cudaMemcpyDeviceToHost, b->stream);
+    cudaError_t e2 = cudaStreamSynchronize(b->stream);
+    b->dev_free(tmp, N);
+    if (e != cudaSuccess) return cuda_fail(e, "read spins");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "read spins");
+    return SPKMC_OK;
+}
+
+int set_spins(spkmc_batch *b, int slot, const int8_t *host, size_t n)
+{
+    int rc = slot_check(b, slot);
+    if (rc) return rc;
+    const Slot &s = b->slots[slot];
+    const size_t N = (size_t)s.params.L * s.params.L * s.params.L;
+    if (!host || n != N) return fail(SPKMC_EINVAL, "host buffer must hold L^3 = %zu int8", N);
+    DeviceGuard g(b->device);
+    if ((rc = sync_and_check(b)) != SPKMC_OK) return rc;
+    int8_t *tmp = (int8_t *)b->dev_alloc(N);
+    if (!tmp) return fail(SPKMC_ENOMEM, "device allocation of %zu bytes failed", N);
+    cudaError_t e = cudaMemcpyAsync(tmp, host, N, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) {
+        rc = launch_pack_rows(s.desc, tmp, b->stream);
+        if (!rc) rc = refresh_derived(b, s.desc);
+        if (rc) e = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaStreamSynchronize(b->stream);
+    b->dev_free(tmp, N);
+    if (e != cudaSuccess) return cuda_fail(e, "write spins");
+    if (rc) return rc;
+    if (e2 != cudaSuccess) return cuda_fail(e2, "write spins");
+    return SPKMC_OK;
+}
+
+int get_event_log(spkmc_batch *b, int slot, spkmc_event *buf, size_t cap, size_t *n_out)
+{
+    int rc = slot_check(b, slot);
+    if (rc) return rc;
+    if (!n_out) return fail(SPKMC_EINVAL, "n_out is NULL");
+    *n_out = 0;
+    const Slot &s = b->slots[slot];
+    DeviceGuard g(b->device);
+    if ((rc = sync_and_check(b)) != SPKMC_OK) return rc;
+    if (!s.desc.log) return SPKMC_OK;
+    const long long logged = std::min<long long>(s.desc.log_cap, (s.t - s.desc.log_t0) * s.desc.Kact);
+    const size_t n = (size_t)std::max<long long>(0, std::min<long long>(logged, (long long)cap));
+    if (n == 0) return SPKMC_OK;
+    if (!buf) return fail(SPKMC_EINVAL, "buf is NULL");
+    CUDA_TRY(cudaMemcpyAsync(buf, s.desc.log, n * sizeof(spkmc_event), cudaMemcpyDeviceToHost, b->stream),
+             "read event log");
+    CUDA_TRY(cudaStreamSynchronize(b->stream), "stream synchronize");
+    *n_out = n;
+    return SPKMC_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+void spkmc_params_init(spkmc_params *p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->L = 16;
+    p->domain_edge = 4;
+    p->J = 1.0;
+    p->H = 0.0;
+    p->T = 4.5115;
+    p->seed = 1;
+    p->init = SPKMC_INIT_HOT;
+}
+
+void spkmc_config_init(spkmc_config *c)
+{
+    if (!c) return;
+    std::memset(c, 0, sizeof(*c));
+    c->device = -1;
+    c->debug_skip_arrival_cta = -1;
+}
+
+int spkmc_rate_table(double J, double H, double T, double out[14])
+{
+    if (!out) return fail(SPKMC_EINVAL, "out is NULL");
+    if (!std::isfinite(J) || !std::isfinite(H) || !std::isfinite(T) || !(T > 0.0))
+        return fail(SPKMC_EINVAL, "J, H, T must be finite and T > 0");
+    host_rates(J, H, T, out);
+    return SPKMC_OK;
+}
+
+int32_t spkmc_resolve_domain_edge(int32_t L)
+{
+    const int cand[4] = {16, 8, 4, 2};
+    for (int d : cand)
+        if (L > 0 && L % (2 * d) == 0) return d;
+    return 0;
+}
+
+int64_t spkmc_bytes_required(const spkmc_params *p)
+{
+    int d = 0;
+    if (check_params(p, &d) != SPKMC_OK) return 0;
+    return sizes_of(p->L, d, p->event_log_capacity).total();
+}
+
+int spkmc_create(int32_t L, int32_t domain_edge, double J, double H, double T, uint64_t seed,
+                 spkmc_t **out)
+{
+    spkmc_params p;
+    spkmc_params_init(&p);
+    p.L = L;
+    p.domain_edge = domain_edge;
+    p.J = J;
+    p.H = H;
+    p.T = T;
+    p.seed = seed;
+    return spkmc_create_ex(&p, nullptr, out);
+}
+
+int spkmc_create_ex(const spkmc_params *p, const spkmc_config *cfg, spkmc_t **out)
+{
+    if (!out) return fail(SPKMC_EINVAL, "out is NULL");
+    *out = nullptr;
+    int d = 0;
+    int rc = check_params(p, &d);
+    if (rc) return rc;
+    spkmc_batch *b = nullptr;
+    if ((rc = batch_new(1, cfg, &b)) != SPKMC_OK) return rc;
+    int slot = -1;
+    if ((rc = admit(b, p, -1, 0, &slot)) != SPKMC_OK) {
+        std::string msg = g_last_error;
+        release_batch(b);
+        g_last_error = msg;
+        return rc;
+    }
+    spkmc_engine *h = new (std::nothrow) spkmc_engine();
+    if (!h) {
+        release_batch(b);
+        return fail(SPKMC_ENOMEM, "host allocation failed");
+    }
+    h->b = b;
+    h->slot = slot;
+    *out = h;
+    return SPKMC_OK;
+}
+
+void spkmc_destroy(spkmc_t *h)
+{
+    if (!h) return;
+    release_batch(h->b);
+    delete h;
+}
+
+int spkmc_run_cycles(spkmc_t *h, int64_t ncycles)
+{
+    if (!h) return fail(SPKMC_EINVAL, "handle is NULL");
+    return run(h->b, ncycles);
+}
+
+int spkmc_synchronize(spkmc_t *h)
+{
+    if (!h) return fail(SPKMC_EINVAL, "handle is NULL");
+    DeviceGuard g(h->b->device);
+    return sync_and_check(h->b);
+}
+
+int spkmc_observables(spkmc_t *h, spkmc_obs *out)
+{
+    if (!h) return fail(SPKMC_EINVAL, "handle is NULL");
+    return observables(h->b, h->slot, out);
+}
+
+int spkmc_get_spins(spkmc_t *h, int8_t *host_buf, size_t n)
+{
+    if (!h) return fail(SPKMC_EINVAL, "handle is NULL");
+    return get_spins(h->b, h->slot, host_buf, n);
+}
+
+int spkmc_set_spins(spkmc_t *h, const int8_t *host_buf, size_t n)
+{
+    if (!h) return fail(SPKMC_EINVAL, "handle is NULL");
+    return set_spins(h->b, h->slot, host_buf, n);
+}
+
+int spkmc_get_event_log(spkmc_t *h, spkmc_event *buf, size_t cap, size_t *n_out)
+{
+    if (!h) return fail(SPKMC_EINVAL, "handle is NULL");
+    return get_event_log(h->b, h->slot, buf, cap, n_out);
+}
+
+int spkmc_clear_event_log(spkmc_t *h)
+{
+    if (!h) return fail(SPKMC_EINVAL, "handle is NULL");
+    spkmc_batch *b = h->b;
+    DeviceGuard g(b->device);
+    int rc = sync_and_check(b);
+    if (rc) return rc;
+    Slot &s = b->slots[h->slot];
+    s.desc.log_t0 = s.t;
+    return upload_slot(b, h->slot);
+}
+
+int spkmc_get_state(spkmc_t *h, spkmc_state *out)
+{
+    if (!h || !out) return fail(SPKMC_EINVAL, "NULL argument");
+    DeviceGuard g(h->b->device);
+    LatticeState st;
+    int rc = read_state(h->b, h->slot, &st);
+    if (rc) return rc;
+    out->cycle = st.t;
+    out->clock = st.clock;
+    out->n_flip = (int64_t)st.n_flip;
+    out->n_null = (int64_t)st.n_null;
+    out->sum_null_rate_fx[0] = st.null_fx_lo;
+    out->sum_null_rate_fx[1] = st.null_fx_hi;
+    return SPKMC_OK;
+}
+
+int spkmc_set_state(spkmc_t *h, const spkmc_state *in)
+{
+    if (!h || !in) return fail(SPKMC_EINVAL, "NULL argument");
+    if (in->cycle < 0 || in->n_flip < 0 || in->n_null < 0)
+        return fail(SPKMC_EINVAL, "state counters must be >= 0");
+    spkmc_batch *b = h->b;
+    DeviceGuard g(b->device);
+    CUDA_TRY(cudaStreamSynchronize(b->stream), "stream synchronize");
+    LatticeState &st = b->h_state[h->slot];
+    std::memset(&st, 0, sizeof(st));
+    st.t = in->cycle;
+    st.clock = in->clock;
+    st.n_flip = (unsigned long long)in->n_flip;
+    st.n_null = (unsigned long long)in->n_null;
+    st.null_fx_lo = in->sum_null_rate_fx[0];
+    st.null_fx_hi = in->sum_null_rate_fx[1];
+    Slot &s = b->slots[h->slot];
+    st.budget = s.budget;
+    s.t = in->cycle;
+    s.desc.log_t0 = in->cycle;
+    b->sticky_error = SPKMC_OK;
+    CUDA_TRY(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream), "clear error flag");
+    return upload_slot(b, h->slot);
+}
+
+int spkmc_class_counts(spkmc_t *h, int32_t *host_counts, size_t n)
+{
+    if (!h) return fail(SPKMC_EINVAL, "handle is NULL");
+    spkmc_batch *b = h->b;
+    const Slot &s = b->slots[h->slot];
+    if (!host_counts || n != (size_t)(s.desc.K * kClasses))
+        return fail(SPKMC_EINVAL, "buffer must hold 14*K = %lld int32", (long long)(s.desc.K * kClasses));
+    DeviceGuard g(b->device);
+    int rc = sync_and_check(b);
+    if (rc) return rc;
+    std::vector<int32_t> tmp((size_t)(s.desc.K * kCountStride));
+    CUDA_TRY(cudaMemcpyAsync(tmp.data(), s.desc.counts, tmp.size() * 4, cudaMemcpyDeviceToHost, b->stream),
+             "read counts");
+    CUDA_TRY(cudaStreamSynchronize(b->stream), "stream synchronize");
+    for (long long k = 0; k < s.desc.K; ++k)
+        std::memcpy(host_counts + k * kClasses, tmp.data() + k * kCountStride, kClasses * 4);
+    return SPKMC_OK;
+}
+
+int spkmc_check_counts(spkmc_t *h, int64_t *mismatched)
+{
+    if (!h || !mismatched) return fail(SPKMC_EINVAL, "NULL argument");
+    spkmc_batch *b = h->b;
+    DeviceGuard g(b->device);
+    int rc = sync_and_check(b);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemsetAsync(b->d_mismatch, 0, 8, b->stream), "clear");
+    if ((rc = launch_count_classes(b->slots[h->slot].desc, 1, b->d_mismatch, b->stream)) != SPKMC_OK)
+        return cuda_fail(cudaGetLastError(), "recount");
+    CUDA_TRY(cudaMemcpyAsync(b->h_MB, b->d_mismatch, 8, cudaMemcpyDeviceToHost, b->stream), "read");
+    CUDA_TRY(cudaStreamSynchronize(b->stream), "stream synchronize");
+    *mismatched = b->h_MB[0];
+    return SPKMC_OK;
+}
+
+int spkmc_info_get(spkmc_t *h, spkmc_info *out)
+{
+    if (!h || !out) return fail(SPKMC_EINVAL, "NULL argument");
+    const Slot &s = h->b->slots[h->slot];
+    std::memset(out, 0, sizeof(*out));
+    out->L = s.params.L;
+    out->domain_edge = s.d;
+    out->nd = s.desc.nd;
+    out->K = s.desc.K;
+    out->K_act = s.desc.Kact;
+    out->device_bytes = s.sz.total();
+    out->grid_ctas = h->b->last_grid;
+    out->threads_per_cta = cycle_kernel_shape().threads;
+    return SPKMC_OK;
+}
+
+int spkmc_batch_create(int32_t capacity, const spkmc_config *cfg, spkmc_batch_t **out)
+{
+    return batch_new(capacity, cfg, out);
+}
+
+void spkmc_batch_destroy(spkmc_batch_t *b)
+{
+    release_batch(b);
+}
+
+int spkmc_batch_admit(spkmc_batch_t *b, const spkmc_params *p, int64_t cycles, int32_t *slot)
+{
+    if (!b || !slot) return fail(SPKMC_EINVAL, "NULL argument");
+    int s = -1;
+    int rc = admit(b, p, cycles, -1, &s);
+    if (rc == SPKMC_OK) *slot = s;
+    return rc;
+}
+
+int spkmc_batch_run(spkmc_batch_t *b, int64_t cycles)
+{
+    if (!b) return fail(SPKMC_EINVAL, "handle is NULL");
+    return run(b, cycles);
+}
+
+int spkmc_batch_poll(spkmc_batch_t *b, int32_t *done_slots, int32_t cap, int32_t *n)
+{
+    if (!b || !n || (cap > 0 && !done_slots)) return fail(SPKMC_EINVAL, "NULL argument");
+    *n = 0;
+    DeviceGuard g(b->device);
+    int rc = sync_and_check(b);
+    if (rc) return rc;
+    for (int i = 0; i < b->capacity && *n < cap; ++i) {
+        Slot &s = b->slots[i];
+        if (s.live && s.budget == 0 && !s.done_reported) {
+            s.done_reported = true;
+            done_slots[(*n)++] = i;
+        }
+    }
+    return SPKMC_OK;
+}
+
+int spkmc_batch_retire(spkmc_batch_t *b, int32_t slot)
+{
+    int rc = slot_check(b, slot);
+    if (rc) return rc;
+    DeviceGuard g(b->device);
+    CUDA_TRY(cudaStreamSynchronize(b->stream), "stream synchronize");
+    Slot &s = b->slots[slot];
+    free_slot_memory(b, s);
+    b->live_bytes -= s.sz.total();
+    s = Slot();
+    b->uploaded_seg.clear();
+    return SPKMC_OK;
+}
+
+int spkmc_batch_synchronize(spkmc_batch_t *b)
+{
+    if (!b) return fail(SPKMC_EINVAL, "handle is NULL");
+    DeviceGuard g(b->device);
+    return sync_and_check(b);
+}
+
+int spkmc_batch_observables(spkmc_batch_t *b, int32_t slot, spkmc_obs *out)
+{
+    return observables(b, slot, out);
+}
+
+int spkmc_batch_get_spins(spkmc_batch_t *b, int32_t slot, int8_t *host_buf, size_t n)
+{
+    return get_spins(b, slot, host_buf, n);
+}
+
+int spkmc_batch_get_event_log(spkmc_batch_t *b, int32_t slot, spkmc_event *buf, size_t cap,
+                              size_t *n_out)
+{
+    return get_event_log(b, slot, buf, cap, n_out);
+}
+
+int spkmc_batch_usage(spkmc_batch_t *b, int32_t *live_slots, int64_t *device_bytes)
+{
+    if (!b) return fail(SPKMC_EINVAL, "handle is NULL");
+    int live = 0;
+    for (const auto &s : b->slots) live += s.live ? 1 : 0;
+    if (live_slots) *live_slots = live;
+    if (device_bytes) *device_bytes = b->live_bytes;
+    return SPKMC_OK;
+}
+
+const char *spkmc_last_error(void)
+{
+    return g_last_error.c_str();
+}
+
+} // extern "C"

@@ -1,0 +1,96 @@
+// Internal types shared by the kernels (spkmc_kernels.cu) and the host
+// runtime (spkmc_api.cu).  Device data layout of one lattice, for domain edge d:
+//
+//   rows    [K][d*d]  uint16: bit x of slot (y + d*z) is 1 when spin (x,y,z)
+//                     of the domain is +1 (a row of d spins along x);
+//   mirrors [K][4][d] uint16: copies of the domain's faces so a neighbour reads
+//                     its halo as whole 2d-byte lines: face 0 = x=0 and face
+//                     1 = x=d-1 (bit y, index z), face 2 = y=0 and face
+//                     3 = y=d-1 (bit x, index z);  z faces are rows already;
+//   counts  [K][16]   int32: number of sites of each of the 14 classes;
+//   scratch [K/8][16] double: per active domain of the running cycle, the
+//                     cumulative frequency line cum[0..13], u01 and w1.
+#pragma once
+
+#include <cstdint>
+
+#include "../../include/spkmc.h"
+
+namespace spkmc {
+
+constexpr int kClasses = 14;
+constexpr int kCountStride = 16;   // int32 per domain in counts
+constexpr int kScratchStride = 16; // doubles per active domain in scratch
+constexpr int kMaxEdge = 16;
+constexpr int kPadRow = kMaxEdge + 2;           // padded rows per axis
+constexpr int kPadWords = kPadRow * kPadRow;    // words of one padded domain
+constexpr int kMaxSegPerCta = 64;               // lattices one CTA may touch
+
+struct LatticeDesc {
+    uint16_t *rows;
+    uint16_t *mirrors;
+    int32_t *counts;
+    double *scratch;
+    spkmc_event *log;
+    int64_t log_cap;
+    int64_t log_t0;
+    double rate[kClasses];
+    uint64_t seed;
+    int32_t L, d, nd, half;
+    int64_t K, Kact;
+};
+
+// Per-lattice state written by the persistent kernel.
+struct LatticeState {
+    int64_t t;                      // cycles done
+    double clock;
+    unsigned long long n_flip;
+    unsigned long long n_null;
+    unsigned long long null_fx_lo;  // sum of floor(r_0k * 2^64), 128-bit
+    unsigned long long null_fx_hi;
+    int64_t budget;                 // cycles left; < 0 = unlimited
+    unsigned long long rmax[3];     // R_max bit patterns, slot t % 3
+};
+
+// One lattice's run of active domains in the flat work table.
+struct Segment {
+    int64_t base; // first flat item
+    int32_t slot; // index into desc/state
+    int32_t pad;
+};
+
+struct LaunchParams {
+    const LatticeDesc *desc;
+    LatticeState *state;
+    const Segment *seg;   // nseg entries, sorted by base
+    int32_t nseg;
+    int32_t parity0;      // t % 2 shared by all running lattices at launch, -1 if mixed
+    int64_t Q;            // total items
+    int64_t ncycles;      // grid cycles of this launch
+    unsigned *bar;        // grid-barrier arrival counter (zero at launch)
+    int *err;             // first error code raised on the device
+    long long timeout_ns; // barrier time limit
+    int skip_cta;         // debug: CTA that never arrives (-1 = none)
+    int pad;
+};
+
+// Host-side launch helpers implemented in spkmc_kernels.cu.
+struct KernelShape {
+    int threads;
+    int smem_bytes;
+};
+KernelShape cycle_kernel_shape();
+int cycle_kernel_max_blocks_per_sm(int device);
+int launch_cycles(const LaunchParams &p, int grid, void *stream, bool cooperative);
+int launch_init_rows(const LatticeDesc &d, int init, void *stream);
+int launch_pack_rows(const LatticeDesc &d, const int8_t *dev_spins, void *stream);
+int launch_unpack_rows(const LatticeDesc &d, int8_t *dev_spins, void *stream);
+int launch_build_mirrors(const LatticeDesc &d, void *stream);
+// mode 0: write counts; mode 1: compare with the stored counts and add the
+// number of mismatching domains to *mismatch (device int64).
+int launch_count_classes(const LatticeDesc &d, int mode, unsigned long long *mismatch,
+                         void *stream);
+// M and B (device int64 pair, accumulated).
+int launch_observables(const LatticeDesc &d, long long *MB, void *stream);
+
+} // namespace spkmc

@@ -1,0 +1,974 @@
+// spkmc_kernels.cu -- sm_103a kernels of the spkMC cycle (arXiv:1005.4713,
+// Sec. 3.1 steps 1-6 with the chessboard sublattice of Sec. 3.2).
+//
+// One persistent cooperative launch runs many cycles.  Per cycle:
+//   phase A (step 1)   one lane per active domain reads the domain's 14 class
+//                      counts, builds the cumulative frequency line in FP64
+//                      (class order, no fused multiply-add), draws its Philox
+//                      block and keeps the line in scratch; partial maxima go
+//                      to shared memory, then one atomicMax per CTA and lattice;
+//   grid barrier       (step 2: R_max is known everywhere);
+//   phase B (steps 3-6) one lane per domain finds the event on the line padded
+//                      by the null rate R_max - R_k; one warp per non-null
+//                      domain stages the domain and its 1-site halo (bit
+//                      packed) into shared memory, classifies its rows with a
+//                      bit-sliced adder, finds the j-th site of the chosen class
+//                      with popc + warp scan, flips it and moves the class
+//                      counts of the site and its 6 neighbours;
+//   grid barrier       (step 6: the flips are visible) -- skipped after an odd
+//                      cycle, whose flips never touch the counts that the next
+//                      colour reads.
+// The clock (step 5) is advanced once per cycle by the lane that owns the
+// lattice's first active domain.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "spkmc_internal.h"
+
+namespace spkmc {
+
+namespace {
+
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11), the counter-based
+// generator that gives each domain its own stream (Sec. 3.1, step 4).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x64_10(unsigned long long c0, unsigned long long c1,
+                                              unsigned long long c2, unsigned long long c3,
+                                              unsigned long long k0, unsigned long long k1,
+                                              unsigned long long out[4])
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const unsigned long long m0 = 0xD2E7470EE14C6C93ULL, m1 = 0xCA5A826395121157ULL;
+        unsigned long long hi0 = __umul64hi(m0, c0), lo0 = m0 * c0;
+        unsigned long long hi1 = __umul64hi(m1, c2), lo1 = m1 * c2;
+        unsigned long long n0 = hi1 ^ c1 ^ k0;
+        unsigned long long n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B97F4A7C15ULL;
+        k1 += 0xBB67AE8584CAA73BULL;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+// ---------------------------------------------------------------------------
+// Memory helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ long long global_timer_ns()
+{
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int ld_volatile_int(const int *p)
+{
+    return *reinterpret_cast<const volatile int *>(p);
+}
+
+__device__ __forceinline__ uint32_t ld_row(const uint16_t *p)
+{
+    return (uint32_t)__ldcg(reinterpret_cast<const unsigned short *>(p));
+}
+
+// XOR into one 16-bit slot through the 32-bit word that holds it.
+__device__ __forceinline__ void xor_u16(uint16_t *p, uint32_t bits)
+{
+    uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    uint32_t *w = reinterpret_cast<uint32_t *>(a & ~uintptr_t(3));
+    atomicXor(w, bits << ((a & 2) ? 16 : 0));
+}
+
+__device__ __forceinline__ void raise_error(int *err, int code)
+{
+    atomicCAS(err, 0, code);
+}
+
+// floor(x * 2^64) for finite x >= 0 as a 128-bit integer (lo, hi).
+__device__ __forceinline__ void fixed64(double x, unsigned long long &lo, unsigned long long &hi)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    int e = (int)((b >> 52) & 0x7ff);
+    lo = 0;
+    hi = 0;
+    if (e == 0) return; // zero or subnormal: far below 2^-64
+    unsigned long long m = (b & ((1ULL << 52) - 1)) | (1ULL << 52);
+    int sh = e - 1011; // x * 2^64 = m * 2^(e - 1075 + 64)
+    if (sh >= 64) {
+        hi = m << (sh - 64);
+    } else if (sh > 0) {
+        lo = m << sh;
+        hi = m >> (64 - sh);
+    } else if (sh == 0) {
+        lo = m;
+    } else if (sh > -64) {
+        lo = m >> (-sh);
+    }
+}
+
+// 128-bit add into (lo, hi) held in memory, exact and order-independent.
+__device__ __forceinline__ void atomic_add_u128(unsigned long long *lo_p, unsigned long long *hi_p,
+                                                unsigned long long lo, unsigned long long hi)
+{
+    if (lo == 0 && hi == 0) return;
+    unsigned long long old = atomicAdd(lo_p, lo);
+    unsigned long long carry = (old + lo < old) ? 1ULL : 0ULL;
+    if (hi + carry) atomicAdd(hi_p, hi + carry);
+}
+
+// ---------------------------------------------------------------------------
+// Geometry
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void active_domain(int half, long long a, int colour, int &dx, int &dy,
+                                              int &dz)
+{
+    dx = 2 * (int)(a % half) + (colour & 1);
+    dy = 2 * (int)((a / half) % half) + ((colour >> 1) & 1);
+    dz = 2 * (int)(a / ((long long)half * half)) + ((colour >> 2) & 1);
+}
+
+__device__ __forceinline__ long long domain_index(int nd, int dx, int dy, int dz)
+{
+    return (long long)dx + (long long)nd * ((long long)dy + (long long)nd * dz);
+}
+
+__device__ __forceinline__ int wrap_coord(int a, int n)
+{
+    return a < 0 ? a + n : (a >= n ? a - n : a);
+}
+
+// Spin bit (1 = up) of global site (X, Y, Z), coordinates taken modulo L.
+template <int D>
+__device__ __forceinline__ int spin_at(const LatticeDesc &Ld, int X, int Y, int Z)
+{
+    X = wrap_coord(X, Ld.L);
+    Y = wrap_coord(Y, Ld.L);
+    Z = wrap_coord(Z, Ld.L);
+    long long k = domain_index(Ld.nd, X / D, Y / D, Z / D);
+    uint32_t row = ld_row(Ld.rows + k * (D * D) + (Y % D) + D * (Z % D));
+    return (int)((row >> (X % D)) & 1u);
+}
+
+// Padded copy of one domain in shared memory: word (y+1) + (D+2)*(z+1) holds
+// the row (y, z) with spin x in bit x+1, x in [-1, D]; the six face halos come
+// from the neighbours' mirrors (x, y faces) and rows (z faces).
+template <int D>
+__device__ __forceinline__ void stage_padded(const LatticeDesc &Ld, long long k, int dx, int dy,
+                                             int dz, uint32_t *Pw, int lane)
+{
+    const int nd = Ld.nd;
+    const uint16_t *rows = Ld.rows + k * (D * D);
+    const long long kxm = domain_index(nd, wrap_coord(dx - 1, nd), dy, dz);
+    const long long kxp = domain_index(nd, wrap_coord(dx + 1, nd), dy, dz);
+    const long long kym = domain_index(nd, dx, wrap_coord(dy - 1, nd), dz);
+    const long long kyp = domain_index(nd, dx, wrap_coord(dy + 1, nd), dz);
+    const long long kzm = domain_index(nd, dx, dy, wrap_coord(dz - 1, nd));
+    const long long kzp = domain_index(nd, dx, dy, wrap_coord(dz + 1, nd));
+    const uint16_t *fxm = Ld.mirrors + kxm * (4 * D) + 1 * D; // x = D-1 face of the -x neighbour
+    const uint16_t *fxp = Ld.mirrors + kxp * (4 * D) + 0 * D; // x = 0 face of the +x neighbour
+    const uint16_t *fym = Ld.mirrors + kym * (4 * D) + 3 * D; // y = D-1 face of the -y neighbour
+    const uint16_t *fyp = Ld.mirrors + kyp * (4 * D) + 2 * D; // y = 0 face of the +y neighbour
+    const uint16_t *rzm = Ld.rows + kzm * (D * D) + D * (D - 1);
+    const uint16_t *rzp = Ld.rows + kzp * (D * D);
+    for (int r = lane; r < D * D; r += 32) {
+        const int y = r % D, z = r / D;
+        uint32_t v = ld_row(rows + r) << 1;
+        v |= (ld_row(fxm + z) >> y) & 1u;
+        v |= ((ld_row(fxp + z) >> y) & 1u) << (D + 1);
+        Pw[(y + 1) + (D + 2) * (z + 1)] = v;
+    }
+    for (int i = lane; i < D; i += 32) {
+        Pw[(D + 2) * (i + 1)] = ld_row(fym + i) << 1;
+        Pw[(D + 1) + (D + 2) * (i + 1)] = ld_row(fyp + i) << 1;
+        Pw[i + 1] = ld_row(rzm + i) << 1;
+        Pw[(i + 1) + (D + 2) * (D + 1)] = ld_row(rzp + i) << 1;
+    }
+    __syncwarp();
+}
+
+// Bit-sliced count of up neighbours for the D sites of row (y, z): u = u0 +
+// 2 u1 + 4 u2 per bit position (bits 1..D are the sites).
+struct RowPlanes {
+    uint32_t s, u0, u1, u2;
+};
+
+template <int D>
+__device__ __forceinline__ RowPlanes classify_row(const uint32_t *Pw, int y, int z)
+{
+    const int base = (y + 1) + (D + 2) * (z + 1);
+    const uint32_t s = Pw[base];
+    const uint32_t a = s << 1, b = s >> 1;
+    const uint32_t c = Pw[base - 1], d = Pw[base + 1];
+    const uint32_t e = Pw[base - (D + 2)], f = Pw[base + (D + 2)];
+    const uint32_t s1 = a ^ b ^ c, c1 = (a & b) | (c & (a ^ b));
+    const uint32_t s2 = d ^ e ^ f, c2 = (d & e) | (f & (d ^ e));
+    const uint32_t k2 = s1 & s2;
+    RowPlanes p;
+    p.s = s;
+    p.u0 = s1 ^ s2;
+    p.u1 = c1 ^ c2 ^ k2;
+    p.u2 = (c1 & c2) | (k2 & (c1 ^ c2));
+    return p;
+}
+
+template <int D>
+__device__ __forceinline__ uint32_t class_mask(const RowPlanes &p, int cls)
+{
+    constexpr uint32_t V = ((1u << D) - 1u) << 1;
+    const int sig = cls >= 7, u = cls - 7 * sig;
+    uint32_t m = V & (sig ? p.s : ~p.s);
+    m &= (u & 1) ? p.u0 : ~p.u0;
+    m &= (u & 2) ? p.u1 : ~p.u1;
+    m &= (u & 4) ? p.u2 : ~p.u2;
+    return m;
+}
+
+template <int D>
+__device__ __forceinline__ int pad_bit(const uint32_t *Pw, int x, int y, int z)
+{
+    return (int)((Pw[(y + 1) + (D + 2) * (z + 1)] >> (x + 1)) & 1u);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent cycle kernel
+// ---------------------------------------------------------------------------
+struct __align__(16) WorkItem {
+    int ls;  // local segment
+    int a;   // active index within the lattice
+    int cls; // chosen class
+    int j;   // rank of the site within the class
+};
+
+struct CtaShared {
+    long long seg_base[kMaxSegPerCta + 1];
+    long long seg_t0[kMaxSegPerCta];
+    long long seg_part[kMaxSegPerCta];
+    unsigned long long seg_rmax[kMaxSegPerCta];
+    unsigned long long seg_nflip[kMaxSegPerCta];
+    unsigned long long seg_nnull[kMaxSegPerCta];
+    unsigned long long seg_fxlo[kMaxSegPerCta];
+    unsigned long long seg_fxhi[kMaxSegPerCta];
+    int seg_slot[kMaxSegPerCta];
+    int nsegc;
+    int nwork;
+    int ok;
+    WorkItem work[kThreads];
+    uint32_t P[kWarps][kPadWords];
+};
+
+__device__ __forceinline__ int find_segment(const CtaShared &S, long long q)
+{
+    int lo = 0, hi = S.nsegc - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (S.seg_base[mid] <= q) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Grid-wide barrier on a monotone arrival counter.  Waits at most
+// timeout_ns (and a fixed number of polls); on timeout or when another CTA
+// has raised an error it returns false and the caller leaves the kernel.
+__device__ bool grid_barrier(const LaunchParams &P, CtaShared &S, unsigned &epoch)
+{
+    ++epoch;
+    __syncthreads();
+    if (gridDim.x == 1) return ld_volatile_int(P.err) == 0;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        if ((int)blockIdx.x != P.skip_cta) red_release_add_u32(P.bar, 1u);
+        const unsigned target = epoch * gridDim.x;
+        const long long t0 = global_timer_ns();
+        unsigned polls = 0;
+        while (ld_acquire_u32(P.bar) < target) {
+            ++polls;
+            if ((polls & 15u) == 0) {
+                if (ld_volatile_int(P.err) != 0) {
+                    ok = 0;
+                    break;
+                }
+                if (global_timer_ns() - t0 > P.timeout_ns || polls > (1u << 28)) {
+                    raise_error(P.err, SPKMC_ETIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+            __nanosleep(20);
+        }
+        __threadfence();
+        S.ok = ok;
+    }
+    __syncthreads();
+    return *reinterpret_cast<volatile int *>(&S.ok) != 0;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        unsigned long long o = __shfl_xor_sync(kFull, v, off);
+        v = o > v ? o : v;
+    }
+    return v;
+}
+
+__device__ __forceinline__ void warp_sum_u128(unsigned long long &lo, unsigned long long &hi)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        unsigned long long ol = __shfl_xor_sync(kFull, lo, off);
+        unsigned long long oh = __shfl_xor_sync(kFull, hi, off);
+        unsigned long long nl = lo + ol;
+        hi = hi + oh + (nl < lo ? 1ULL : 0ULL);
+        lo = nl;
+    }
+}
+
+// Step 1: frequency line of every active domain of the CTA's item range.
+__device__ void phase_a(const LaunchParams &P, CtaShared &S, long long g, long long lo, long long hi)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (long long base = lo + warp * 32; base < hi; base += kThreads) {
+        const long long q = base + lane;
+        int ls = -1;
+        unsigned long long rbits = 0;
+        if (q < hi) {
+            ls = find_segment(S, q);
+            if (g < S.seg_part[ls]) {
+                const LatticeDesc &Ld = P.desc[S.seg_slot[ls]];
+                const long long a = q - S.seg_base[ls];
+                const long long t = S.seg_t0[ls] + g;
+                int dx, dy, dz;
+                active_domain(Ld.half, a, (int)(t & 7), dx, dy, dz);
+                const long long k = domain_index(Ld.nd, dx, dy, dz);
+                const int4 *cp = reinterpret_cast<const int4 *>(Ld.counts + k * kCountStride);
+                const int4 n0 = __ldcg(cp), n1 = __ldcg(cp + 1), n2 = __ldcg(cp + 2),
+                           n3 = __ldcg(cp + 3);
+                const int n[kClasses] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z,
+                                         n1.w, n2.x, n2.y, n2.z, n2.w, n3.x, n3.y};
+                double cum[kClasses];
+                double acc = __dmul_rn((double)n[0], __ldg(&Ld.rate[0]));
+                cum[0] = acc;
+#pragma unroll
+                for (int c = 1; c < kClasses; ++c) {
+                    acc = __dadd_rn(acc, __dmul_rn((double)n[c], __ldg(&Ld.rate[c])));
+                    cum[c] = acc;
+                }
+                unsigned long long w[4];
+                philox4x64_10((unsigned long long)t, (unsigned long long)k, 1ULL, 0ULL, Ld.seed, 0ULL,
+                              w);
+                const double u01 = __ull2double_rn(w[0] >> 11) * 0x1p-53;
+                double2 *sp = reinterpret_cast<double2 *>(Ld.scratch + a * kScratchStride);
+#pragma unroll
+                for (int c = 0; c < kClasses; c += 2) __stcg(sp + c / 2, make_double2(cum[c], cum[c + 1]));
+                __stcg(sp + 7, make_double2(u01, __longlong_as_double((long long)w[1])));
+                rbits = (unsigned long long)__double_as_longlong(acc);
+            } else {
+                ls = -1;
+            }
+        }
+        const int ls0 = __shfl_sync(kFull, ls, 0);
+        if (__all_sync(kFull, ls == ls0) && ls0 >= 0) {
+            const unsigned long long m = warp_max_u64(rbits);
+            if (lane == 0) atomicMax(&S.seg_rmax[ls0], m);
+        } else if (ls >= 0) {
+            atomicMax(&S.seg_rmax[ls], rbits);
+        }
+    }
+}
+
+template <int D>
+__device__ void select_and_flip(const LaunchParams &P, CtaShared &S, const WorkItem wi, long long g,
+                                int warp, int lane)
+{
+    const int slot = S.seg_slot[wi.ls];
+    const LatticeDesc &Ld = P.desc[slot];
+    const long long t = S.seg_t0[wi.ls] + g;
+    int dx, dy, dz;
+    active_domain(Ld.half, wi.a, (int)(t & 7), dx, dy, dz);
+    const long long k = domain_index(Ld.nd, dx, dy, dz);
+    uint32_t *Pw = S.P[warp];
+    stage_padded<D>(Ld, k, dx, dy, dz, Pw, lane);
+
+    constexpr int kRows = D * D;
+    constexpr int kRpl = kRows >= 32 ? kRows / 32 : 1; // rows per lane, contiguous
+    const bool on = (kRows >= 32) || (lane < kRows);
+    uint32_t m[kRpl];
+    int tot = 0;
+#pragma unroll
+    for (int i = 0; i < kRpl; ++i) {
+        m[i] = 0;
+        if (on) {
+            const int r = lane * kRpl + i;
+            m[i] = class_mask<D>(classify_row<D>(Pw, r % D, r / D), wi.cls);
+            tot += __popc(m[i]);
+        }
+    }
+    int incl = tot;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, off);
+        if (lane >= off) incl += v;
+    }
+    const int excl = incl - tot;
+    const bool mine = wi.j >= excl && wi.j < incl;
+    const unsigned who = __ballot_sync(kFull, mine);
+    if (who == 0) {
+        if (lane == 0) raise_error(P.err, SPKMC_EINTERNAL);
+        return;
+    }
+    int pos = 0;
+    if (mine) {
+        int jj = wi.j - excl;
+#pragma unroll
+        for (int i = 0; i < kRpl; ++i) {
+            const int pc = __popc(m[i]);
+            if (jj >= 0 && jj < pc) {
+                uint32_t bits = m[i];
+                for (int q = 0; q < jj; ++q) bits &= bits - 1;
+                pos = (lane * kRpl + i) * 32 + (__ffs(bits) - 1);
+            }
+            jj -= pc;
+        }
+    }
+    pos = __shfl_sync(kFull, pos, __ffs(who) - 1);
+    const int r = pos >> 5, x = (pos & 31) - 1, y = r % D, z = r / D;
+    const int sig = wi.cls >= 7, us = wi.cls - 7 * sig;
+    const int delta = sig ? -1 : 1; // change of the neighbours' up count
+
+    // Class moves of the flipped site (lane 6) and of its 6 neighbours
+    // (lanes 0..5), read from the pre-flip state.
+    if (lane < 7) {
+        long long kj = k;
+        int cold, cnew;
+        if (lane == 6) {
+            cold = wi.cls;
+            cnew = 7 * (1 - sig) + us;
+        } else {
+            const int jx = x + (lane == 0 ? -1 : lane == 1 ? 1 : 0);
+            const int jy = y + (lane == 2 ? -1 : lane == 3 ? 1 : 0);
+            const int jz = z + (lane == 4 ? -1 : lane == 5 ? 1 : 0);
+            const int sj = pad_bit<D>(Pw, jx, jy, jz);
+            int uj;
+            if (jx >= 0 && jx < D && jy >= 0 && jy < D && jz >= 0 && jz < D) {
+                uj = pad_bit<D>(Pw, jx - 1, jy, jz) + pad_bit<D>(Pw, jx + 1, jy, jz) +
+                     pad_bit<D>(Pw, jx, jy - 1, jz) + pad_bit<D>(Pw, jx, jy + 1, jz) +
+                     pad_bit<D>(Pw, jx, jy, jz - 1) + pad_bit<D>(Pw, jx, jy, jz + 1);
+            } else {
+                const int X = dx * D + jx, Y = dy * D + jy, Z = dz * D + jz;
+                uj = spin_at<D>(Ld, X - 1, Y, Z) + spin_at<D>(Ld, X + 1, Y, Z) +
+                     spin_at<D>(Ld, X, Y - 1, Z) + spin_at<D>(Ld, X, Y + 1, Z) +
+                     spin_at<D>(Ld, X, Y, Z - 1) + spin_at<D>(Ld, X, Y, Z + 1);
+                kj = domain_index(Ld.nd, wrap_coord(X, Ld.L) / D, wrap_coord(Y, Ld.L) / D,
+                                  wrap_coord(Z, Ld.L) / D);
+            }
+            cold = 7 * sj + uj;
+            cnew = cold + delta;
+        }
+        if (cold >= 0 && cold < kClasses && cnew >= 0 && cnew < kClasses) {
+            atomicAdd(Ld.counts + kj * kCountStride + cold, -1);
+            atomicAdd(Ld.counts + kj * kCountStride + cnew, 1);
+        } else {
+            raise_error(P.err, SPKMC_EINTERNAL);
+        }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        xor_u16(Ld.rows + k * (D * D) + r, 1u << x);
+        uint16_t *mir = Ld.mirrors + k * (4 * D);
+        if (x == 0) xor_u16(mir + 0 * D + z, 1u << y);
+        if (x == D - 1) xor_u16(mir + 1 * D + z, 1u << y);
+        if (y == 0) xor_u16(mir + 2 * D + z, 1u << x);
+        if (y == D - 1) xor_u16(mir + 3 * D + z, 1u << x);
+        if (Ld.log) {
+            const long long idx = (t - Ld.log_t0) * Ld.Kact + wi.a;
+            if (idx >= 0 && idx < Ld.log_cap) {
+                spkmc_event ev;
+                ev.cycle = t;
+                ev.domain = (int32_t)k;
+                ev.cls = wi.cls;
+                ev.site = x + D * (y + D * z);
+                ev.reserved = 0;
+                Ld.log[idx] = ev;
+            }
+        }
+        atomicAdd(&S.seg_nflip[wi.ls], 1ULL);
+    }
+    __syncwarp();
+}
+
+// Steps 3, 4/4b, 5, 6 for the CTA's item range.
+__device__ void phase_b(const LaunchParams &P, CtaShared &S, long long g, long long lo, long long hi)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (long long rbase = lo; rbase < hi; rbase += kThreads) {
+        if (threadIdx.x == 0) S.nwork = 0;
+        __syncthreads();
+        const long long q = rbase + threadIdx.x;
+        int ls = -1;
+        unsigned long long fxlo = 0, fxhi = 0;
+        if (q < hi) {
+            ls = find_segment(S, q);
+            if (g < S.seg_part[ls]) {
+                const int slot = S.seg_slot[ls];
+                const LatticeDesc &Ld = P.desc[slot];
+                const long long a = q - S.seg_base[ls];
+                const long long t = S.seg_t0[ls] + g;
+                const double Rmax = __longlong_as_double(
+                    (long long)__ldcg(&P.state[slot].rmax[t % 3]));
+                const double2 *sp = reinterpret_cast<const double2 *>(Ld.scratch + a * kScratchStride);
+                double cum[kClasses];
+#pragma unroll
+                for (int c = 0; c < kClasses; c += 2) {
+                    const double2 v = __ldcg(sp + c / 2);
+                    cum[c] = v.x;
+                    cum[c + 1] = v.y;
+                }
+                const double2 uw = __ldcg(sp + 7);
+                const unsigned long long w1 = (unsigned long long)__double_as_longlong(uw.y);
+                // target on the frequency line padded to R_max (steps 3-4):
+                // the first class whose cumulative rate exceeds it, else null.
+                const double target = __dmul_rn(uw.x, Rmax);
+                const unsigned long long tb = (unsigned long long)__double_as_longlong(target);
+                int cls = -1;
+#pragma unroll
+                for (int c = kClasses - 1; c >= 0; --c)
+                    if (tb < (unsigned long long)__double_as_longlong(cum[c])) cls = c;
+                fixed64(__dadd_rn(Rmax, -cum[kClasses - 1]), fxlo, fxhi);
+                int dx, dy, dz;
+                active_domain(Ld.half, a, (int)(t & 7), dx, dy, dz);
+                const long long k = domain_index(Ld.nd, dx, dy, dz);
+                if (cls < 0) {
+                    atomicAdd(&S.seg_nnull[ls], 1ULL);
+                    if (Ld.log) {
+                        const long long idx = (t - Ld.log_t0) * Ld.Kact + a;
+                        if (idx >= 0 && idx < Ld.log_cap) {
+                            spkmc_event ev;
+                            ev.cycle = t;
+                            ev.domain = (int32_t)k;
+                            ev.cls = -1;
+                            ev.site = -1;
+                            ev.reserved = 0;
+                            Ld.log[idx] = ev;
+                        }
+                    }
+                } else {
+                    const unsigned long long nc =
+                        (unsigned long long)__ldcg(Ld.counts + k * kCountStride + cls);
+                    WorkItem wi;
+                    wi.ls = ls;
+                    wi.a = (int)a;
+                    wi.cls = cls;
+                    wi.j = (int)__umul64hi(w1, nc);
+                    S.work[atomicAdd(&S.nwork, 1)] = wi;
+                }
+                if (a == 0) {
+                    // Step 5: one global time increment per cycle.
+                    unsigned long long wc[4];
+                    philox4x64_10((unsigned long long)t, 0ULL, 2ULL, 0ULL, Ld.seed, 0ULL, wc);
+                    const double xi = __ull2double_rn(2ULL * (wc[0] >> 12) + 1ULL) * 0x1p-53;
+                    const double dt = __ddiv_rn(-log(xi), Rmax);
+                    LatticeState &st = P.state[slot];
+                    st.clock = __dadd_rn(st.clock, dt);
+                    st.rmax[(t + 2) % 3] = 0ULL;
+                }
+            } else {
+                ls = -1;
+            }
+        }
+        const int ls0 = __shfl_sync(kFull, ls, 0);
+        if (__all_sync(kFull, ls == ls0) && ls0 >= 0) {
+            warp_sum_u128(fxlo, fxhi);
+            if (lane == 0) atomic_add_u128(&S.seg_fxlo[ls0], &S.seg_fxhi[ls0], fxlo, fxhi);
+        } else if (ls >= 0) {
+            atomic_add_u128(&S.seg_fxlo[ls], &S.seg_fxhi[ls], fxlo, fxhi);
+        }
+        __syncthreads();
+        const int nwork = S.nwork;
+        for (int i = warp; i < nwork; i += kWarps) {
+            const WorkItem wi = S.work[i];
+            switch (P.desc[S.seg_slot[wi.ls]].d) {
+            case 2: select_and_flip<2>(P, S, wi, g, warp, lane); break;
+            case 4: select_and_flip<4>(P, S, wi, g, warp, lane); break;
+            case 8: select_and_flip<8>(P, S, wi, g, warp, lane); break;
+            default: select_and_flip<16>(P, S, wi, g, warp, lane); break;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams P)
+{
+    __shared__ CtaShared S;
+    const long long G = gridDim.x;
+    const long long lo = (P.Q * (long long)blockIdx.x) / G;
+    const long long hi = (P.Q * ((long long)blockIdx.x + 1)) / G;
+
+    if (threadIdx.x == 0) {
+        // segments overlapping [lo, hi): the last one with base <= lo, onwards
+        int first = 0, top = P.nseg - 1;
+        while (first < top) {
+            int mid = (first + top + 1) >> 1;
+            if (P.seg[mid].base <= lo) first = mid;
+            else top = mid - 1;
+        }
+        int n = 0, i = first;
+        S.ok = 1;
+        for (; i < P.nseg && P.seg[i].base < hi; ++i) {
+            if (n == kMaxSegPerCta) {
+                raise_error(P.err, SPKMC_EINTERNAL);
+                S.ok = 0;
+                break;
+            }
+            S.seg_base[n] = P.seg[i].base;
+            S.seg_slot[n] = P.seg[i].slot;
+            ++n;
+        }
+        S.seg_base[n] = (i < P.nseg) ? P.seg[i].base : P.Q;
+        S.nsegc = n;
+    }
+    __syncthreads();
+    if (!S.ok) return; // the host sizes the grid so that this cannot happen
+    for (int i = threadIdx.x; i < S.nsegc; i += blockDim.x) {
+        const LatticeState &st = P.state[S.seg_slot[i]];
+        const long long budget = st.budget;
+        S.seg_t0[i] = st.t;
+        S.seg_part[i] = budget < 0 ? P.ncycles : (budget < P.ncycles ? budget : P.ncycles);
+        S.seg_rmax[i] = 0;
+        S.seg_nflip[i] = 0;
+        S.seg_nnull[i] = 0;
+        S.seg_fxlo[i] = 0;
+        S.seg_fxhi[i] = 0;
+    }
+    __syncthreads();
+    if (ld_volatile_int(P.err) != 0) return;
+
+    unsigned epoch = 0;
+    for (long long g = 0; g < P.ncycles; ++g) {
+        phase_a(P, S, g, lo, hi);
+        __syncthreads();
+        for (int i = threadIdx.x; i < S.nsegc; i += blockDim.x) {
+            if (g < S.seg_part[i]) {
+                const long long t = S.seg_t0[i] + g;
+                atomicMax(&P.state[S.seg_slot[i]].rmax[t % 3], S.seg_rmax[i]);
+            }
+            S.seg_rmax[i] = 0;
+        }
+        if (!grid_barrier(P, S, epoch)) return;
+        phase_b(P, S, g, lo, hi);
+        if (g + 1 < P.ncycles) {
+            const bool odd = P.parity0 >= 0 && (((long long)P.parity0 + g) & 1LL) == 1LL;
+            if (odd) {
+                __syncthreads();
+            } else if (!grid_barrier(P, S, epoch)) {
+                return;
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < S.nsegc; i += blockDim.x) {
+        LatticeState &st = P.state[S.seg_slot[i]];
+        if (S.seg_nflip[i]) atomicAdd(&st.n_flip, S.seg_nflip[i]);
+        if (S.seg_nnull[i]) atomicAdd(&st.n_null, S.seg_nnull[i]);
+        atomic_add_u128(&st.null_fx_lo, &st.null_fx_hi, S.seg_fxlo[i], S.seg_fxhi[i]);
+        if (S.seg_base[i] >= lo) { // this CTA owns the lattice's first active domain
+            st.t = S.seg_t0[i] + S.seg_part[i];
+            if (st.budget >= 0) st.budget -= S.seg_part[i];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Set-up and read-out kernels (one thread per row, or one warp per domain)
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void init_rows_kernel(LatticeDesc Ld, int init)
+{
+    const long long nrows = Ld.K * (D * D);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nrows;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long k = i / (D * D);
+        const int r = (int)(i % (D * D));
+        const int dx = (int)(k % Ld.nd), dy = (int)((k / Ld.nd) % Ld.nd),
+                  dz = (int)(k / ((long long)Ld.nd * Ld.nd));
+        uint32_t row = (1u << D) - 1u;
+        if (init == SPKMC_INIT_HOT) {
+            const long long X0 = (long long)dx * D, Y = (long long)dy * D + r % D,
+                            Z = (long long)dz * D + r / D;
+            const long long g0 = X0 + (long long)Ld.L * (Y + (long long)Ld.L * Z);
+            unsigned long long w[4];
+            philox4x64_10((unsigned long long)(g0 >> 8), 0ULL, 3ULL, 0ULL, Ld.seed, 0ULL, w);
+            const int off = (int)(g0 & 255);
+            row = (uint32_t)((w[off >> 6] >> (off & 63)) & ((1ULL << D) - 1ULL));
+        }
+        Ld.rows[i] = (uint16_t)row;
+    }
+}
+
+template <int D>
+__global__ void pack_rows_kernel(LatticeDesc Ld, const int8_t *s8)
+{
+    const long long nrows = Ld.K * (D * D);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nrows;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long k = i / (D * D);
+        const int r = (int)(i % (D * D));
+        const int dx = (int)(k % Ld.nd), dy = (int)((k / Ld.nd) % Ld.nd),
+                  dz = (int)(k / ((long long)Ld.nd * Ld.nd));
+        const long long g0 = (long long)dx * D +
+                             (long long)Ld.L * ((long long)dy * D + r % D +
+                                                (long long)Ld.L * ((long long)dz * D + r / D));
+        uint32_t row = 0;
+        for (int x = 0; x < D; ++x) row |= (s8[g0 + x] > 0 ? 1u : 0u) << x;
+        Ld.rows[i] = (uint16_t)row;
+    }
+}
+
+template <int D>
+__global__ void unpack_rows_kernel(LatticeDesc Ld, int8_t *s8)
+{
+    const long long nrows = Ld.K * (D * D);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nrows;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long k = i / (D * D);
+        const int r = (int)(i % (D * D));
+        const int dx = (int)(k % Ld.nd), dy = (int)((k / Ld.nd) % Ld.nd),
+                  dz = (int)(k / ((long long)Ld.nd * Ld.nd));
+        const long long g0 = (long long)dx * D +
+                             (long long)Ld.L * ((long long)dy * D + r % D +
+                                                (long long)Ld.L * ((long long)dz * D + r / D));
+        const uint32_t row = Ld.rows[i];
+        for (int x = 0; x < D; ++x) s8[g0 + x] = ((row >> x) & 1u) ? int8_t(1) : int8_t(-1);
+    }
+}
+
+template <int D>
+__global__ void build_mirrors_kernel(LatticeDesc Ld)
+{
+    const long long n = Ld.K * D;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long k = i / D;
+        const int z = (int)(i % D);
+        const uint16_t *rows = Ld.rows + k * (D * D) + D * z;
+        uint32_t x0 = 0, x1 = 0;
+        for (int y = 0; y < D; ++y) {
+            const uint32_t row = rows[y];
+            x0 |= (row & 1u) << y;
+            x1 |= ((row >> (D - 1)) & 1u) << y;
+        }
+        uint16_t *mir = Ld.mirrors + k * (4 * D);
+        mir[0 * D + z] = (uint16_t)x0;
+        mir[1 * D + z] = (uint16_t)x1;
+        mir[2 * D + z] = rows[0];
+        mir[3 * D + z] = rows[D - 1];
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) count_classes_kernel(LatticeDesc Ld, int mode,
+                                                            unsigned long long *mismatch)
+{
+    __shared__ uint32_t Pbuf[8][kPadWords];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *Pw = Pbuf[warp];
+    constexpr uint32_t V = ((1u << D) - 1u) << 1;
+    unsigned long long bad = 0;
+    for (long long k = blockIdx.x * 8LL + warp; k < Ld.K; k += gridDim.x * 8LL) {
+        const int dx = (int)(k % Ld.nd), dy = (int)((k / Ld.nd) % Ld.nd),
+                  dz = (int)(k / ((long long)Ld.nd * Ld.nd));
+        stage_padded<D>(Ld, k, dx, dy, dz, Pw, lane);
+        int cnt[kClasses];
+#pragma unroll
+        for (int c = 0; c < kClasses; ++c) cnt[c] = 0;
+        for (int r = lane; r < D * D; r += 32) {
+            const RowPlanes p = classify_row<D>(Pw, r % D, r / D);
+#pragma unroll
+            for (int u = 0; u < 7; ++u) {
+                uint32_t e = V;
+                e &= (u & 1) ? p.u0 : ~p.u0;
+                e &= (u & 2) ? p.u1 : ~p.u1;
+                e &= (u & 4) ? p.u2 : ~p.u2;
+                cnt[7 + u] += __popc(e & p.s);
+                cnt[u] += __popc(e & ~p.s);
+            }
+        }
+        int differs = 0;
+#pragma unroll
+        for (int c = 0; c < kClasses; ++c) {
+            const int v = __reduce_add_sync(kFull, cnt[c]);
+            if (lane == c) {
+                if (mode == 0) Ld.counts[k * kCountStride + c] = v;
+                else differs = Ld.counts[k * kCountStride + c] != v;
+            }
+        }
+        if (mode == 0 && lane >= kClasses && lane < kCountStride) Ld.counts[k * kCountStride + lane] = 0;
+        if (__any_sync(kFull, differs) && lane == 0) ++bad;
+        __syncwarp();
+    }
+    if (mode == 1 && lane == 0 && bad) atomicAdd(mismatch, bad);
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) observables_kernel(LatticeDesc Ld, long long *MB)
+{
+    __shared__ uint32_t Pbuf[8][kPadWords];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *Pw = Pbuf[warp];
+    constexpr uint32_t V = ((1u << D) - 1u) << 1;
+    long long M = 0, B = 0;
+    for (long long k = blockIdx.x * 8LL + warp; k < Ld.K; k += gridDim.x * 8LL) {
+        const int dx = (int)(k % Ld.nd), dy = (int)((k / Ld.nd) % Ld.nd),
+                  dz = (int)(k / ((long long)Ld.nd * Ld.nd));
+        stage_padded<D>(Ld, k, dx, dy, dz, Pw, lane);
+        int m = 0, b = 0;
+        for (int r = lane; r < D * D; r += 32) {
+            const int y = r % D, z = r / D;
+            const int base = (y + 1) + (D + 2) * (z + 1);
+            const uint32_t s = Pw[base];
+            m += 2 * __popc(s & V) - D;
+            b += 2 * __popc(~(s ^ (s >> 1)) & V) - D;
+            b += 2 * __popc(~(s ^ Pw[base + 1]) & V) - D;
+            b += 2 * __popc(~(s ^ Pw[base + (D + 2)]) & V) - D;
+        }
+        m = __reduce_add_sync(kFull, m);
+        b = __reduce_add_sync(kFull, b);
+        M += m;
+        B += b;
+        __syncwarp();
+    }
+    if (lane == 0 && (M || B)) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(MB), (unsigned long long)M);
+        atomicAdd(reinterpret_cast<unsigned long long *>(MB + 1), (unsigned long long)B);
+    }
+}
+
+inline int to_status(cudaError_t e)
+{
+    return e == cudaSuccess ? SPKMC_OK : SPKMC_ECUDA;
+}
+
+inline int simple_grid(long long n, int threads)
+{
+    long long b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 65535LL * 16) b = 65535LL * 16;
+    return (int)b;
+}
+
+} // namespace
+
+KernelShape cycle_kernel_shape()
+{
+    KernelShape s;
+    s.threads = kThreads;
+    s.smem_bytes = 0; // all static
+    return s;
+}
+
+int cycle_kernel_max_blocks_per_sm(int device)
+{
+    (void)device;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, spkmc_cycles_kernel, kThreads, 0) !=
+        cudaSuccess)
+        return 0;
+    return n;
+}
+
+int launch_cycles(const LaunchParams &p, int grid, void *stream, bool cooperative)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = (cudaStream_t)stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = cooperative ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return to_status(cudaLaunchKernelEx(&cfg, spkmc_cycles_kernel, p));
+}
+
+#define SPKMC_DISPATCH_D(dval, KERNEL, GRID, BLOCK, STREAM, ...)                                  \
+    do {                                                                                          \
+        switch (dval) {                                                                           \
+        case 2: KERNEL<2><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;                        \
+        case 4: KERNEL<4><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;                        \
+        case 8: KERNEL<8><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;                        \
+        case 16: KERNEL<16><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;                      \
+        default: return SPKMC_EINVAL;                                                             \
+        }                                                                                         \
+    } while (0)
+
+int launch_init_rows(const LatticeDesc &d, int init, void *stream)
+{
+    const int grid = simple_grid(d.K * d.d * d.d, 256);
+    SPKMC_DISPATCH_D(d.d, init_rows_kernel, grid, 256, (cudaStream_t)stream, d, init);
+    return to_status(cudaGetLastError());
+}
+
+int launch_pack_rows(const LatticeDesc &d, const int8_t *dev_spins, void *stream)
+{
+    const int grid = simple_grid(d.K * d.d * d.d, 256);
+    SPKMC_DISPATCH_D(d.d, pack_rows_kernel, grid, 256, (cudaStream_t)stream, d, dev_spins);
+    return to_status(cudaGetLastError());
+}
+
+int launch_unpack_rows(const LatticeDesc &d, int8_t *dev_spins, void *stream)
+{
+    const int grid = simple_grid(d.K * d.d * d.d, 256);
+    SPKMC_DISPATCH_D(d.d, unpack_rows_kernel, grid, 256, (cudaStream_t)stream, d, dev_spins);
+    return to_status(cudaGetLastError());
+}
+
+int launch_build_mirrors(const LatticeDesc &d, void *stream)
+{
+    const int grid = simple_grid(d.K * d.d, 256);
+    SPKMC_DISPATCH_D(d.d, build_mirrors_kernel, grid, 256, (cudaStream_t)stream, d);
+    return to_status(cudaGetLastError());
+}
+
+int launch_count_classes(const LatticeDesc &d, int mode, unsigned long long *mismatch, void *stream)
+{
+    const int grid = simple_grid(d.K, 8);
+    SPKMC_DISPATCH_D(d.d, count_classes_kernel, grid, 256, (cudaStream_t)stream, d, mode, mismatch);
+    return to_status(cudaGetLastError());
+}
+
+int launch_observables(const LatticeDesc &d, long long *MB, void *stream)
+{
+    const int grid = simple_grid(d.K, 8);
+    SPKMC_DISPATCH_D(d.d, observables_kernel, grid, 256, (cudaStream_t)stream, d, MB);
+    return to_status(cudaGetLastError());
+}
+
+} // namespace spkmc

@@ -1,0 +1,256 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, element
+by element, on the same seeded inputs.  Spins, event logs, counters and the
+exact null-rate sum must be bit-identical; the clock (the only value that goes
+through a transcendental function on the device) must agree to 1e-12
+relative, the tolerance stated for the clock."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1005_4713_gb300 as sp
+from paper_1005_4713_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+CLOCK_RTOL = 1e-12
+THREADS = max(1, min(16, os.cpu_count() or 1))
+
+
+def oracle_state(spec, **kw):
+    return oracle.State(spec.L, spec.d, spec.J, spec.H, spec.T, spec.seed, cold=spec.cold, **kw)
+
+
+def gpu_lattice(spec, log=0, config=None):
+    return sp.Lattice(spec.L, spec.d, spec.J, spec.H, spec.T, spec.seed, cold=spec.cold,
+                      event_log_capacity=log, config=config)
+
+
+def same_clock(a, b):
+    if math.isinf(a) or math.isinf(b):
+        return a == b
+    return a == pytest.approx(b, rel=CLOCK_RTOL, abs=0.0)
+
+
+def assert_same(lat, st, spins=True):
+    o = lat.observables()
+    assert o.cycle == st.cycle
+    assert (o.n_flip, o.n_null) == (st.n_flip, st.n_null)
+    assert int(o.sum_null_rate_fx[0]) | (int(o.sum_null_rate_fx[1]) << 64) == st.null_fx
+    assert same_clock(o.clock, st.clock), (o.clock, st.clock)
+    if spins:
+        s = lat.spins()
+        assert np.array_equal(s, st.spins), int(np.sum(s != st.spins))
+        assert (o.M, o.B) == st.observables()
+
+
+def log_as_array(ev):
+    return np.stack([ev["domain"], ev["cls"], ev["site"]], axis=-1).astype(np.int32)
+
+
+@pytest.mark.parametrize("spec", [
+    wl.LatticeSpec(L=16, d=4, seed=1), wl.LatticeSpec(L=16, d=4, seed=1, cold=True),
+    wl.LatticeSpec(L=32, d=2, seed=7), wl.LatticeSpec(L=64, d=8, seed=9),
+    wl.LatticeSpec(L=96, d=16, seed=11), wl.LatticeSpec(L=24, d=4, seed=5),
+])
+def test_initial_state_and_counts_match_oracle(spec):
+    with gpu_lattice(spec) as lat:
+        st = oracle_state(spec)
+        assert np.array_equal(lat.spins(), st.spins)
+        assert np.array_equal(lat.class_counts(), oracle.class_counts(spec.L, spec.d, st.spins))
+        o = lat.observables()
+        assert (o.M, o.B) == st.observables()
+        assert lat.check_counts() == 0
+
+
+def test_config_16_ten_thousand_cycles_with_event_log():
+    """16^3, 4^3-site domains, hot start seed 1: 10^4 cycles, spins, clock and
+    counters compared every 100 cycles, the whole event log compared."""
+    spec = wl.CONFIG_16
+    st = oracle_state(spec)
+    kact = st.k_act
+    with gpu_lattice(spec, log=wl.CYCLES_16 * kact) as lat:
+        logs = []
+        for _ in range(wl.CYCLES_16 // 100):
+            lat.run(100)
+            logs.append(st.run(100, log=True))
+            assert_same(lat, st)
+        ev = lat.event_log()
+        assert len(ev) == wl.CYCLES_16 * kact
+        ref = np.concatenate(logs).reshape(-1, 3)
+        assert np.array_equal(log_as_array(ev), ref)
+        assert np.array_equal(ev["cycle"], np.repeat(np.arange(wl.CYCLES_16), kact))
+        assert lat.check_counts() == 0
+
+
+@pytest.mark.parametrize("spec", [wl.CONFIG_128_COLD, wl.CONFIG_128_HOT])
+def test_config_128_against_oracle(spec):
+    """128^3, 8^3-site domains, cold and hot start: 800 cycles (100 visits per
+    colour) compared every 100 cycles, event log of the first 200 cycles."""
+    st = oracle_state(spec)
+    with gpu_lattice(spec, log=200 * st.k_act) as lat:
+        ref_log = []
+        for i in range(8):
+            lat.run(100)
+            ev = st.run(100, log=i < 2, threads=THREADS)
+            if ev is not None:
+                ref_log.append(ev)
+            assert_same(lat, st)
+        assert np.array_equal(log_as_array(lat.event_log()), np.concatenate(ref_log).reshape(-1, 3))
+        assert np.array_equal(lat.class_counts(), oracle.class_counts(spec.L, spec.d, st.spins))
+
+
+def test_config_1024_first_eight_cycles():
+    """1024^3 with 16^3-site domains (32768 events per cycle) in the launch
+    configuration the benchmark times: one visit of every colour, compared
+    in full with the oracle."""
+    spec = wl.CONFIG_1024
+    st = oracle_state(spec)
+    with gpu_lattice(spec) as lat:
+        lat.run(8)
+        st.run(8, threads=THREADS)
+        assert_same(lat, st)
+        o = lat.observables()
+        assert o.n_flip + o.n_null == 8 * st.k_act
+
+
+@pytest.mark.parametrize("spec", [
+    wl.LatticeSpec(L=4, d=2, seed=3),                    # nd = 2: both x neighbours are one domain
+    wl.LatticeSpec(L=8, d=4, seed=4, H=0.3),
+    wl.LatticeSpec(L=16, d=8, seed=5, J=-0.7, H=0.1, T=2.0),
+    wl.LatticeSpec(L=32, d=16, seed=6, cold=True),
+    wl.LatticeSpec(L=64, d=16, seed=7, T=3.0),
+    wl.LatticeSpec(L=24, d=4, seed=8, H=0.01, T=4.45),  # nd = 6
+    wl.LatticeSpec(L=40, d=2, seed=9, T=6.0),           # nd = 20
+    wl.LatticeSpec(L=48, d=8, seed=10, T=1.5, H=-0.2),
+])
+def test_geometries_and_fields(spec):
+    st = oracle_state(spec)
+    n = 64
+    with gpu_lattice(spec, log=n * st.k_act) as lat:
+        lat.run(n)
+        ev = st.run(n, log=True, threads=THREADS)
+        assert_same(lat, st)
+        assert np.array_equal(log_as_array(lat.event_log()), ev.reshape(-1, 3))
+        assert lat.check_counts() == 0
+
+
+def test_frozen_lattice_has_infinite_clock_and_only_nulls():
+    """Cold start at T -> 0: every rate underflows to 0, so R_max = 0, every
+    event is null and dt = -ln(xi)/0 = +inf (the degenerate case of step 5)."""
+    spec = wl.LatticeSpec(L=16, d=4, T=0.01, cold=True)
+    st = oracle_state(spec)
+    with gpu_lattice(spec) as lat:
+        lat.run(3)
+        st.run(3)
+        o = lat.observables()
+        assert o.n_flip == 0 and o.n_null == 3 * st.k_act
+        assert math.isinf(o.clock) and math.isinf(st.clock)
+        assert_same(lat, st)
+
+
+def test_zero_cycles_is_a_noop():
+    spec = wl.CONFIG_16
+    with gpu_lattice(spec) as lat:
+        s0 = lat.spins()
+        lat.run(0)
+        o = lat.observables()
+        assert o.cycle == 0 and o.clock == 0.0
+        assert np.array_equal(lat.spins(), s0)
+
+
+def test_event_log_capacity_truncates():
+    spec = wl.CONFIG_16
+    st = oracle_state(spec)
+    with gpu_lattice(spec, log=20) as lat:
+        lat.run(10)
+        ev = lat.event_log()
+        assert len(ev) == 20
+        ref = st.run(10, log=True).reshape(-1, 3)[:20]
+        assert np.array_equal(log_as_array(ev), ref)
+
+
+def test_chunked_runs_equal_one_run():
+    spec = wl.LatticeSpec(L=32, d=4, seed=21)
+    with gpu_lattice(spec) as a, gpu_lattice(spec) as b:
+        a.run(5)
+        a.run(7)
+        a.run(1)
+        b.run(13)
+        assert np.array_equal(a.spins(), b.spins())
+        oa, ob = a.observables(), b.observables()
+        assert (oa.clock, oa.n_flip, oa.n_null) == (ob.clock, ob.n_flip, ob.n_null)
+
+
+@pytest.mark.parametrize("kw", [dict(max_ctas=1), dict(items_per_cta=1), dict(items_per_cta=7),
+                                dict(items_per_cta=1000), dict(ctas_per_sm=1)])
+def test_launch_geometry_does_not_change_the_trajectory(kw):
+    spec = wl.LatticeSpec(L=64, d=4, seed=22)
+    st = oracle_state(spec)
+    st.run(40, threads=THREADS)
+    with gpu_lattice(spec, config=sp.make_config(**kw)) as lat:
+        lat.run(40)
+        assert_same(lat, st)
+
+
+def test_checkpoint_resume_is_bit_exact():
+    spec = wl.LatticeSpec(L=64, d=8, seed=23)
+    with gpu_lattice(spec) as a:
+        a.run(30)
+        state, spins = a.state(), a.spins()
+        a.run(30)
+        with gpu_lattice(wl.LatticeSpec(L=64, d=8, seed=23, cold=True)) as b:
+            b.set_spins(spins)
+            b.set_state(state)
+            assert b.check_counts() == 0
+            b.run(30)
+            assert np.array_equal(a.spins(), b.spins())
+            oa, ob = a.observables(), b.observables()
+            assert (oa.cycle, oa.clock, oa.n_flip, oa.n_null) == (ob.cycle, ob.clock, ob.n_flip, ob.n_null)
+            assert list(oa.sum_null_rate_fx) == list(ob.sum_null_rate_fx)
+
+
+def test_set_spins_roundtrip_and_recount():
+    spec = wl.LatticeSpec(L=32, d=8, seed=24)
+    rng = np.random.default_rng(0)
+    s = rng.choice(np.array([-1, 1], dtype=np.int8), size=32 ** 3)
+    with gpu_lattice(spec) as lat:
+        lat.set_spins(s)
+        assert np.array_equal(lat.spins(), s)
+        assert np.array_equal(lat.class_counts(), oracle.class_counts(32, 8, s))
+
+
+def test_torch_stream_and_caching_allocator():
+    torch = pytest.importorskip("torch")
+    spec = wl.LatticeSpec(L=32, d=4, seed=25)
+    st = oracle_state(spec)
+    st.run(16)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        cfg = sp.torch_config(caching_allocator=True)
+        with gpu_lattice(spec, config=cfg) as lat:
+            lat.run(16)
+            assert_same(lat, st)
+
+
+def test_barrier_timeout_is_reported_and_the_context_survives():
+    """Fault test without a GPU fault: one CTA never arrives at the grid
+    barrier, the others give up after 50 ms, the host reads ETIMEOUT, and a
+    fresh lattice on the same context still runs correctly."""
+    spec = wl.LatticeSpec(L=64, d=4, seed=26)
+    cfg = sp.make_config(barrier_timeout_ns=50_000_000, debug_skip_arrival_cta=0, items_per_cta=64)
+    lat = gpu_lattice(spec, config=cfg)
+    lat.run(2)
+    with pytest.raises(sp.SpkmcError) as e:
+        lat.synchronize()
+    assert e.value.code == sp.SPKMC_ETIMEOUT
+    with pytest.raises(sp.SpkmcError):
+        lat.run(1)
+    lat.close()
+    st = oracle_state(spec)
+    st.run(4)
+    with gpu_lattice(spec) as ok:
+        ok.run(4)
+        assert_same(ok, st)

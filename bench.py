@@ -274,7 +274,10 @@ def run_gpu(args, world, rank, local, pg):
 
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(device)
+    # a stream of our own (the legacy default stream has handle 0, which the
+    # library would replace by a private stream that these events cannot see)
+    stream = torch.cuda.Stream(device)
+    torch.cuda.set_stream(stream)
     cfg = sp.torch_config()
     seed = SEED_BENCH + rank
     lat = sp.Lattice(L_BENCH, D_BENCH, 1.0, 0.0, 4.5115, seed, config=cfg)
@@ -376,7 +379,7 @@ def run_gpu(args, world, rank, local, pg):
                          "int8_equivalent_GBps": cps * kact * int8_bytes_per_event(D_BENCH) / (kernel_ms / 1e3) / 1e9},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": args.steps,
             "clocks": clocks,
         }
         print(json.dumps(line))

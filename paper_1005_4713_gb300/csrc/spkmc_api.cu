@@ -331,6 +331,16 @@ int refresh_derived(spkmc_batch *b, const LatticeDesc &d)
     return SPKMC_OK;
 }
 
+// Exact M and B of a slot, recomputed from the spins into its device state.
+int recompute_MB(spkmc_batch *b, int slot)
+{
+    LatticeState *st = b->d_state + slot;
+    CUDA_TRY(cudaMemsetAsync(&st->M, 0, 2 * sizeof(long long), b->stream), "clear M, B");
+    if (launch_observables(b->slots[slot].desc, &st->M, b->stream) != SPKMC_OK)
+        return cuda_fail(cudaGetLastError(), "observables kernel");
+    return SPKMC_OK;
+}
+
 int admit(spkmc_batch *b, const spkmc_params *p, long long cycles, int slot_hint, int *slot_out)
 {
     int d = 0;
@@ -388,6 +398,7 @@ int admit(spkmc_batch *b, const spkmc_params *p, long long cycles, int slot_hint
     rc = upload_slot(b, slot);
     if (!rc) rc = launch_init_rows(D, p->init, b->stream);
     if (!rc) rc = refresh_derived(b, D);
+    if (!rc) rc = recompute_MB(b, slot);
     if (rc) {
         free_slot_memory(b, s);
         s.live = false;
@@ -476,6 +487,10 @@ int run(spkmc_batch *b, long long cycles)
         P.err = b->d_err;
         P.timeout_ns = b->cfg.barrier_timeout_ns > 0 ? b->cfg.barrier_timeout_ns : 2000000000LL;
         P.skip_cta = b->cfg.debug_skip_arrival_cta;
+        int dmax = 2;
+        for (const Segment &sg : segs) dmax = std::max(dmax, b->slots[sg.slot].d);
+        P.item_bytes = staged_bytes(dmax);
+        P.round_items = cycle_round_items(dmax);
         int rc = launch_cycles(P, (int)grid, b->stream, grid > 1);
         if (rc) return cuda_fail(cudaGetLastError(), "persistent cycle launch");
         b->last_grid = (int)grid;
@@ -516,19 +531,14 @@ int observables(spkmc_batch *b, int slot, spkmc_obs *out)
     if (!out) return fail(SPKMC_EINVAL, "out is NULL");
     DeviceGuard g(b->device);
     const Slot &s = b->slots[slot];
-    CUDA_TRY(cudaMemsetAsync(b->d_MB, 0, 2 * sizeof(long long), b->stream), "clear observables");
-    if ((rc = launch_observables(s.desc, b->d_MB, b->stream)) != SPKMC_OK)
-        return cuda_fail(cudaGetLastError(), "observables kernel");
-    CUDA_TRY(cudaMemcpyAsync(b->h_MB, b->d_MB, 2 * sizeof(long long), cudaMemcpyDeviceToHost, b->stream),
-             "read observables");
     LatticeState st;
     if ((rc = read_state(b, slot, &st)) != SPKMC_OK) return rc;
     const double N = (double)s.params.L * s.params.L * s.params.L;
     std::memset(out, 0, sizeof(*out));
     out->cycle = st.t;
     out->clock = st.clock;
-    out->M = b->h_MB[0];
-    out->B = b->h_MB[1];
+    out->M = st.M;
+    out->B = st.B;
     out->E = -s.params.J * (double)out->B - s.params.H * (double)out->M;
     out->m = (double)out->M / N;
     out->m2 = out->m * out->m;
@@ -579,6 +589,7 @@ int set_spins(spkmc_batch *b, int slot, const int8_t *host, size_t n)
     if (e == cudaSuccess) {
         rc = launch_pack_rows(s.desc, tmp, b->stream);
         if (!rc) rc = refresh_derived(b, s.desc);
+        if (!rc) rc = recompute_MB(b, slot);
         if (rc) e = cudaGetLastError();
     }
     cudaError_t e2 = cudaStreamSynchronize(b->stream);
@@ -794,7 +805,10 @@ int spkmc_set_state(spkmc_t *h, const spkmc_state *in)
     s.desc.log_t0 = in->cycle;
     b->sticky_error = SPKMC_OK;
     CUDA_TRY(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream), "clear error flag");
-    return upload_slot(b, h->slot);
+    int rc = upload_slot(b, h->slot);
+    if (!rc) rc = recompute_MB(b, h->slot);
+    if (!rc) CUDA_TRY(cudaStreamSynchronize(b->stream), "stream synchronize");
+    return rc;
 }
 
 int spkmc_class_counts(spkmc_t *h, int32_t *host_counts, size_t n)
@@ -824,11 +838,21 @@ int spkmc_check_counts(spkmc_t *h, int64_t *mismatched)
     int rc = sync_and_check(b);
     if (rc) return rc;
     CUDA_TRY(cudaMemsetAsync(b->d_mismatch, 0, 8, b->stream), "clear");
-    if ((rc = launch_count_classes(b->slots[h->slot].desc, 1, b->d_mismatch, b->stream)) != SPKMC_OK)
+    CUDA_TRY(cudaMemsetAsync(b->d_MB, 0, 2 * sizeof(long long), b->stream), "clear");
+    const LatticeDesc &D = b->slots[h->slot].desc;
+    if ((rc = launch_count_classes(D, 1, b->d_mismatch, b->stream)) != SPKMC_OK)
         return cuda_fail(cudaGetLastError(), "recount");
-    CUDA_TRY(cudaMemcpyAsync(b->h_MB, b->d_mismatch, 8, cudaMemcpyDeviceToHost, b->stream), "read");
+    if ((rc = launch_observables(D, b->d_MB, b->stream)) != SPKMC_OK)
+        return cuda_fail(cudaGetLastError(), "observables kernel");
+    CUDA_TRY(cudaMemcpyAsync(b->h_MB, b->d_MB, 2 * sizeof(long long), cudaMemcpyDeviceToHost, b->stream),
+             "read");
+    CUDA_TRY(cudaMemcpyAsync(&b->h_MB[2], b->d_mismatch, 8, cudaMemcpyDeviceToHost, b->stream), "read");
+    CUDA_TRY(cudaMemcpyAsync(&b->h_state[h->slot], b->d_state + h->slot, sizeof(LatticeState),
+                             cudaMemcpyDeviceToHost, b->stream),
+             "read state");
     CUDA_TRY(cudaStreamSynchronize(b->stream), "stream synchronize");
-    *mismatched = b->h_MB[0];
+    const LatticeState &st = b->h_state[h->slot];
+    *mismatched = b->h_MB[2] + ((b->h_MB[0] != st.M || b->h_MB[1] != st.B) ? 1 : 0);
     return SPKMC_OK;
 }
 

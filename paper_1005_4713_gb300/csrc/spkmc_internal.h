@@ -10,6 +10,11 @@
 //   counts  [K][16]   int32: number of sites of each of the 14 classes;
 //   scratch [K/8][16] double: per active domain of the running cycle, the
 //                     cumulative frequency line cum[0..13], u01 and w1.
+// Staged copy of one domain in shared memory (phase B), u16 words:
+//   rows[d*d] | fxm[d] | fxp[d] | fym[d] | fyp[d] | rzm[d] | rzp[d]
+// fxm = x = d-1 face of the -x neighbour, fxp = x = 0 face of the +x
+// neighbour, fym / fyp the same along y, rzm = rows (y, d-1) of the -z
+// neighbour, rzp = rows (y, 0) of the +z neighbour.
 #pragma once
 
 #include <cstdint>
@@ -50,6 +55,8 @@ struct LatticeState {
     unsigned long long null_fx_hi;
     int64_t budget;                 // cycles left; < 0 = unlimited
     unsigned long long rmax[3];     // R_max bit patterns, slot t % 3
+    long long M;                    // sum of spins, kept exact flip by flip
+    long long B;                    // forward bond sum, kept exact flip by flip
 };
 
 // One lattice's run of active domains in the flat work table.
@@ -71,8 +78,14 @@ struct LaunchParams {
     int *err;             // first error code raised on the device
     long long timeout_ns; // barrier time limit
     int skip_cta;         // debug: CTA that never arrives (-1 = none)
+    int round_items;      // active domains per phase-B round (staging capacity)
+    int item_bytes;       // staging bytes per domain (largest edge of the launch)
     int pad;
 };
+
+// Bytes of one staged domain: its rows and its six face halos.
+__host__ __device__ constexpr int staged_bytes(int d) { return 2 * d * d + 12 * d; }
+constexpr int kStageBytes = 88 * 1024; // phase-B staging area per CTA
 
 // Host-side launch helpers implemented in spkmc_kernels.cu.
 struct KernelShape {
@@ -92,5 +105,7 @@ int launch_count_classes(const LatticeDesc &d, int mode, unsigned long long *mis
                          void *stream);
 // M and B (device int64 pair, accumulated).
 int launch_observables(const LatticeDesc &d, long long *MB, void *stream);
+// Round size for a launch whose largest domain edge is d_max.
+int cycle_round_items(int d_max);
 
 } // namespace spkmc

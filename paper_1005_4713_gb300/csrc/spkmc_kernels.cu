@@ -256,11 +256,63 @@ __device__ __forceinline__ int pad_bit(const uint32_t *Pw, int x, int y, int z)
 // ---------------------------------------------------------------------------
 // Persistent cycle kernel
 // ---------------------------------------------------------------------------
+// Row planes of a staged domain: s = row (y, z) with spin x in bit x+1,
+// the x halo in bits 0 and D+1; the five other planes are the neighbour rows.
+template <int D>
+__device__ __forceinline__ RowPlanes classify_staged_row(const uint16_t *st, int y, int z)
+{
+    const uint16_t *rows = st, *fxm = st + D * D, *fxp = fxm + D, *fym = fxp + D, *fyp = fym + D,
+                   *rzm = fyp + D, *rzp = rzm + D;
+    const int r = y + D * z;
+    const uint32_t s = ((uint32_t)rows[r] << 1) | (((uint32_t)fxm[z] >> y) & 1u) |
+                       ((((uint32_t)fxp[z] >> y) & 1u) << (D + 1));
+    const uint32_t a = s << 1, b = s >> 1;
+    const uint32_t c = (uint32_t)(y > 0 ? rows[r - 1] : fym[z]) << 1;
+    const uint32_t d = (uint32_t)(y < D - 1 ? rows[r + 1] : fyp[z]) << 1;
+    const uint32_t e = (uint32_t)(z > 0 ? rows[r - D] : rzm[y]) << 1;
+    const uint32_t f = (uint32_t)(z < D - 1 ? rows[r + D] : rzp[y]) << 1;
+    const uint32_t s1 = a ^ b ^ c, c1 = (a & b) | (c & (a ^ b));
+    const uint32_t s2 = d ^ e ^ f, c2 = (d & e) | (f & (d ^ e));
+    const uint32_t k2 = s1 & s2;
+    RowPlanes p;
+    p.s = s;
+    p.u0 = s1 ^ s2;
+    p.u1 = c1 ^ c2 ^ k2;
+    p.u2 = (c1 & c2) | (k2 & (c1 ^ c2));
+    return p;
+}
+
+// Spin bit of local site (x, y, z) of a staged domain, one coordinate at most
+// one step outside [0, D) (the face halo).
+template <int D>
+__device__ __forceinline__ int staged_bit(const uint16_t *st, int x, int y, int z)
+{
+    const uint16_t *fxm = st + D * D, *fxp = fxm + D, *fym = fxp + D, *fyp = fym + D, *rzm = fyp + D,
+                   *rzp = rzm + D;
+    uint32_t w;
+    int b;
+    if (x < 0) { w = fxm[z]; b = y; }
+    else if (x >= D) { w = fxp[z]; b = y; }
+    else if (y < 0) { w = fym[z]; b = x; }
+    else if (y >= D) { w = fyp[z]; b = x; }
+    else if (z < 0) { w = rzm[y]; b = x; }
+    else if (z >= D) { w = rzp[y]; b = x; }
+    else { w = st[y + D * z]; b = x; }
+    return (int)((w >> b) & 1u);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent cycle kernel
+// ---------------------------------------------------------------------------
 struct __align__(16) WorkItem {
-    int ls;  // local segment
-    int a;   // active index within the lattice
-    int cls; // chosen class
-    int j;   // rank of the site within the class
+    long long k;  // domain index
+    int ls;       // local segment
+    int a;        // active index within the lattice
+    int cls;      // chosen class
+    int j;        // rank of the site within the class
+    int off;      // byte offset of the staged copy
+    int site;     // chosen local site (set by the classifier), -1 if none
+    short dx, dy, dz, d;
 };
 
 struct CtaShared {
@@ -272,12 +324,15 @@ struct CtaShared {
     unsigned long long seg_nnull[kMaxSegPerCta];
     unsigned long long seg_fxlo[kMaxSegPerCta];
     unsigned long long seg_fxhi[kMaxSegPerCta];
+    unsigned long long seg_dM[kMaxSegPerCta];
+    unsigned long long seg_dB[kMaxSegPerCta];
     int seg_slot[kMaxSegPerCta];
+    unsigned long long mbar;
     int nsegc;
     int nwork;
+    int bulk_bytes;
     int ok;
     WorkItem work[kThreads];
-    uint32_t P[kWarps][kPadWords];
 };
 
 __device__ __forceinline__ int find_segment(const CtaShared &S, long long q)
@@ -350,6 +405,62 @@ __device__ __forceinline__ void warp_sum_u128(unsigned long long &lo, unsigned l
     }
 }
 
+// --- shared-memory barrier (mbarrier) and bulk copies (TMA engine) ---------
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *m, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(m)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *m, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(m)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *m, unsigned parity)
+{
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done)
+                 : "r"(smem_addr(m)), "r"(parity)
+                 : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes,
+                                              unsigned long long *m)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(m))
+                 : "memory");
+}
+
+// Wait for the bulk copies of one round.  The first limit raises an error
+// (the copies must still land before the shared memory is released, so the
+// wait goes on, bounded again); returns false if they never completed.
+__device__ bool mbar_wait_bounded(const LaunchParams &P, unsigned long long *m, unsigned parity)
+{
+    const long long t0 = global_timer_ns();
+    bool raised = false;
+    for (unsigned polls = 0;; ++polls) {
+        if (mbar_try_wait(m, parity)) return true;
+        const long long dt = global_timer_ns() - t0;
+        if (!raised && (dt > P.timeout_ns || polls > (1u << 26))) {
+            raise_error(P.err, SPKMC_ETIMEOUT);
+            raised = true;
+        }
+        if (dt > 4 * P.timeout_ns || polls > (1u << 28)) return false;
+    }
+}
+
 // Step 1: frequency line of every active domain of the CTA's item range.
 __device__ void phase_a(const LaunchParams &P, CtaShared &S, long long g, long long lo, long long hi)
 {
@@ -403,137 +514,241 @@ __device__ void phase_a(const LaunchParams &P, CtaShared &S, long long g, long l
     }
 }
 
+// Stage one domain and its face halos into shared memory: bulk copies on the
+// TMA engine for D >= 8 (every piece is a multiple of 16 bytes), plain loads
+// for the small edges.
 template <int D>
-__device__ void select_and_flip(const LaunchParams &P, CtaShared &S, const WorkItem wi, long long g,
-                                int warp, int lane)
+__device__ __forceinline__ void stage_domain(const LatticeDesc &Ld, const WorkItem &w,
+                                             unsigned char *stage, unsigned long long *mbar)
 {
-    const int slot = S.seg_slot[wi.ls];
-    const LatticeDesc &Ld = P.desc[slot];
-    const long long t = S.seg_t0[wi.ls] + g;
-    int dx, dy, dz;
-    active_domain(Ld.half, wi.a, (int)(t & 7), dx, dy, dz);
-    const long long k = domain_index(Ld.nd, dx, dy, dz);
-    uint32_t *Pw = S.P[warp];
-    stage_padded<D>(Ld, k, dx, dy, dz, Pw, lane);
-
-    constexpr int kRows = D * D;
-    constexpr int kRpl = kRows >= 32 ? kRows / 32 : 1; // rows per lane, contiguous
-    const bool on = (kRows >= 32) || (lane < kRows);
-    uint32_t m[kRpl];
-    int tot = 0;
+    const int nd = Ld.nd;
+    const long long kxm = domain_index(nd, wrap_coord(w.dx - 1, nd), w.dy, w.dz);
+    const long long kxp = domain_index(nd, wrap_coord(w.dx + 1, nd), w.dy, w.dz);
+    const long long kym = domain_index(nd, w.dx, wrap_coord(w.dy - 1, nd), w.dz);
+    const long long kyp = domain_index(nd, w.dx, wrap_coord(w.dy + 1, nd), w.dz);
+    const long long kzm = domain_index(nd, w.dx, w.dy, wrap_coord(w.dz - 1, nd));
+    const long long kzp = domain_index(nd, w.dx, w.dy, wrap_coord(w.dz + 1, nd));
+    const uint16_t *src[7] = {Ld.rows + w.k * (D * D),
+                              Ld.mirrors + kxm * (4 * D) + 1 * D,
+                              Ld.mirrors + kxp * (4 * D) + 0 * D,
+                              Ld.mirrors + kym * (4 * D) + 3 * D,
+                              Ld.mirrors + kyp * (4 * D) + 2 * D,
+                              Ld.rows + kzm * (D * D) + D * (D - 1),
+                              Ld.rows + kzp * (D * D)};
+    uint16_t *dst = reinterpret_cast<uint16_t *>(stage + w.off);
+    if constexpr (D >= 8) {
+        bulk_copy_g2s(dst, src[0], 2 * D * D, mbar);
 #pragma unroll
-    for (int i = 0; i < kRpl; ++i) {
-        m[i] = 0;
-        if (on) {
-            const int r = lane * kRpl + i;
-            m[i] = class_mask<D>(classify_row<D>(Pw, r % D, r / D), wi.cls);
-            tot += __popc(m[i]);
-        }
-    }
-    int incl = tot;
+        for (int i = 1; i < 7; ++i) bulk_copy_g2s(dst + D * D + (i - 1) * D, src[i], 2 * D, mbar);
+    } else {
+        for (int r = 0; r < D * D; ++r) dst[r] = (uint16_t)ld_row(src[0] + r);
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int v = __shfl_up_sync(kFull, incl, off);
-        if (lane >= off) incl += v;
+        for (int i = 1; i < 7; ++i)
+            for (int r = 0; r < D; ++r) dst[D * D + (i - 1) * D + r] = (uint16_t)ld_row(src[i] + r);
     }
-    const int excl = incl - tot;
-    const bool mine = wi.j >= excl && wi.j < incl;
-    const unsigned who = __ballot_sync(kFull, mine);
-    if (who == 0) {
-        if (lane == 0) raise_error(P.err, SPKMC_EINTERNAL);
-        return;
-    }
-    int pos = 0;
-    if (mine) {
-        int jj = wi.j - excl;
-#pragma unroll
-        for (int i = 0; i < kRpl; ++i) {
-            const int pc = __popc(m[i]);
-            if (jj >= 0 && jj < pc) {
-                uint32_t bits = m[i];
-                for (int q = 0; q < jj; ++q) bits &= bits - 1;
-                pos = (lane * kRpl + i) * 32 + (__ffs(bits) - 1);
-            }
-            jj -= pc;
-        }
-    }
-    pos = __shfl_sync(kFull, pos, __ffs(who) - 1);
-    const int r = pos >> 5, x = (pos & 31) - 1, y = r % D, z = r / D;
-    const int sig = wi.cls >= 7, us = wi.cls - 7 * sig;
-    const int delta = sig ? -1 : 1; // change of the neighbours' up count
-
-    // Class moves of the flipped site (lane 6) and of its 6 neighbours
-    // (lanes 0..5), read from the pre-flip state.
-    if (lane < 7) {
-        long long kj = k;
-        int cold, cnew;
-        if (lane == 6) {
-            cold = wi.cls;
-            cnew = 7 * (1 - sig) + us;
-        } else {
-            const int jx = x + (lane == 0 ? -1 : lane == 1 ? 1 : 0);
-            const int jy = y + (lane == 2 ? -1 : lane == 3 ? 1 : 0);
-            const int jz = z + (lane == 4 ? -1 : lane == 5 ? 1 : 0);
-            const int sj = pad_bit<D>(Pw, jx, jy, jz);
-            int uj;
-            if (jx >= 0 && jx < D && jy >= 0 && jy < D && jz >= 0 && jz < D) {
-                uj = pad_bit<D>(Pw, jx - 1, jy, jz) + pad_bit<D>(Pw, jx + 1, jy, jz) +
-                     pad_bit<D>(Pw, jx, jy - 1, jz) + pad_bit<D>(Pw, jx, jy + 1, jz) +
-                     pad_bit<D>(Pw, jx, jy, jz - 1) + pad_bit<D>(Pw, jx, jy, jz + 1);
-            } else {
-                const int X = dx * D + jx, Y = dy * D + jy, Z = dz * D + jz;
-                uj = spin_at<D>(Ld, X - 1, Y, Z) + spin_at<D>(Ld, X + 1, Y, Z) +
-                     spin_at<D>(Ld, X, Y - 1, Z) + spin_at<D>(Ld, X, Y + 1, Z) +
-                     spin_at<D>(Ld, X, Y, Z - 1) + spin_at<D>(Ld, X, Y, Z + 1);
-                kj = domain_index(Ld.nd, wrap_coord(X, Ld.L) / D, wrap_coord(Y, Ld.L) / D,
-                                  wrap_coord(Z, Ld.L) / D);
-            }
-            cold = 7 * sj + uj;
-            cnew = cold + delta;
-        }
-        if (cold >= 0 && cold < kClasses && cnew >= 0 && cnew < kClasses) {
-            atomicAdd(Ld.counts + kj * kCountStride + cold, -1);
-            atomicAdd(Ld.counts + kj * kCountStride + cnew, 1);
-        } else {
-            raise_error(P.err, SPKMC_EINTERNAL);
-        }
-    }
-    __syncwarp();
-    if (lane == 0) {
-        xor_u16(Ld.rows + k * (D * D) + r, 1u << x);
-        uint16_t *mir = Ld.mirrors + k * (4 * D);
-        if (x == 0) xor_u16(mir + 0 * D + z, 1u << y);
-        if (x == D - 1) xor_u16(mir + 1 * D + z, 1u << y);
-        if (y == 0) xor_u16(mir + 2 * D + z, 1u << x);
-        if (y == D - 1) xor_u16(mir + 3 * D + z, 1u << x);
-        if (Ld.log) {
-            const long long idx = (t - Ld.log_t0) * Ld.Kact + wi.a;
-            if (idx >= 0 && idx < Ld.log_cap) {
-                spkmc_event ev;
-                ev.cycle = t;
-                ev.domain = (int32_t)k;
-                ev.cls = wi.cls;
-                ev.site = x + D * (y + D * z);
-                ev.reserved = 0;
-                Ld.log[idx] = ev;
-            }
-        }
-        atomicAdd(&S.seg_nflip[wi.ls], 1ULL);
-    }
-    __syncwarp();
 }
 
-// Steps 3, 4/4b, 5, 6 for the CTA's item range.
-__device__ void phase_b(const LaunchParams &P, CtaShared &S, long long g, long long lo, long long hi)
+// Rank the sites of class w.cls in ascending local index and return the
+// w.j-th (warp-cooperative, from the staged copy); -1 if the class is short.
+template <int D>
+__device__ int select_site(const WorkItem &w, const unsigned char *stage, int lane)
+{
+    const uint16_t *st = reinterpret_cast<const uint16_t *>(stage + w.off);
+    const int sig = w.cls >= 7, us = w.cls - 7 * sig;
+    if constexpr (D == 16) {
+        // lane l holds rows r0..r0+7 (z = l/2, y = 8(l&1)..+7) as four pairs of
+        // 16-bit rows per 32-bit word: bit b of pair p is site l = 16 (r0+2p) + b
+        const int z = lane >> 1, y0 = (lane & 1) * 8, r0 = lane * 8;
+        const uint16_t *fxm = st + 256, *fxp = fxm + 16, *fym = fxp + 16, *fyp = fym + 16,
+                       *rzm = fyp + 16, *rzp = rzm + 16;
+        const uint4 cur4 = *reinterpret_cast<const uint4 *>(st + r0);
+        const uint4 zm4 = *reinterpret_cast<const uint4 *>(z > 0 ? st + r0 - 16 : rzm + y0);
+        const uint4 zp4 = *reinterpret_cast<const uint4 *>(z < 15 ? st + r0 + 16 : rzp + y0);
+        const uint32_t cur[4] = {cur4.x, cur4.y, cur4.z, cur4.w};
+        const uint32_t zmv[4] = {zm4.x, zm4.y, zm4.z, zm4.w};
+        const uint32_t zpv[4] = {zp4.x, zp4.y, zp4.z, zp4.w};
+        const uint32_t below = (uint32_t)(y0 == 0 ? fym[z] : st[r0 - 1]); // row y0-1
+        const uint32_t above = (uint32_t)(y0 == 8 ? fyp[z] : st[r0 + 8]); // row y0+8
+        const uint32_t hxm = fxm[z], hxp = fxp[z];
+        uint32_t m[4];
+        int tot = 0;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const int y = y0 + 2 * p;
+            const uint32_t s = cur[p];
+            const uint32_t xm = ((s << 1) & 0xFFFEFFFEu) | ((hxm >> y) & 1u) | (((hxm >> (y + 1)) & 1u) << 16);
+            const uint32_t xp = ((s >> 1) & 0x7FFF7FFFu) | (((hxp >> y) & 1u) << 15) |
+                                (((hxp >> (y + 1)) & 1u) << 31);
+            const uint32_t ym = (s << 16) | (p > 0 ? (cur[p - 1] >> 16) : below);
+            const uint32_t yp = (s >> 16) | ((p < 3 ? (cur[p + 1] & 0xFFFFu) : above) << 16);
+            const uint32_t e = zmv[p], f = zpv[p];
+            const uint32_t s1 = xm ^ xp ^ ym, c1 = (xm & xp) | (ym & (xm ^ xp));
+            const uint32_t s2 = yp ^ e ^ f, c2 = (yp & e) | (f & (yp ^ e));
+            const uint32_t k2 = s1 & s2;
+            const uint32_t u0 = s1 ^ s2, u1 = c1 ^ c2 ^ k2, u2 = (c1 & c2) | (k2 & (c1 ^ c2));
+            uint32_t mm = sig ? s : ~s;
+            mm &= (us & 1) ? u0 : ~u0;
+            mm &= (us & 2) ? u1 : ~u1;
+            mm &= (us & 4) ? u2 : ~u2;
+            m[p] = mm;
+            tot += __popc(mm);
+        }
+        int incl = tot;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, off);
+            if (lane >= off) incl += v;
+        }
+        const int excl = incl - tot;
+        const bool mine = w.j >= excl && w.j < incl;
+        const unsigned who = __ballot_sync(kFull, mine);
+        if (who == 0) return -1;
+        int site = 0;
+        if (mine) {
+            int jj = w.j - excl;
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const int pc = __popc(m[p]);
+                if (jj >= 0 && jj < pc) {
+                    uint32_t bits = m[p];
+                    for (int q = 0; q < jj; ++q) bits &= bits - 1;
+                    site = 16 * (r0 + 2 * p) + (__ffs(bits) - 1);
+                }
+                jj -= pc;
+            }
+        }
+        return __shfl_sync(kFull, site, __ffs(who) - 1);
+    } else {
+        constexpr int kRows = D * D;
+        constexpr int kRpl = kRows >= 32 ? kRows / 32 : 1; // rows per lane, contiguous
+        const bool on = (kRows >= 32) || (lane < kRows);
+        uint32_t m[kRpl];
+        int tot = 0;
+#pragma unroll
+        for (int i = 0; i < kRpl; ++i) {
+            m[i] = 0;
+            if (on) {
+                const int r = lane * kRpl + i;
+                m[i] = class_mask<D>(classify_staged_row<D>(st, r % D, r / D), w.cls);
+                tot += __popc(m[i]);
+            }
+        }
+        int incl = tot;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, off);
+            if (lane >= off) incl += v;
+        }
+        const int excl = incl - tot;
+        const bool mine = w.j >= excl && w.j < incl;
+        const unsigned who = __ballot_sync(kFull, mine);
+        if (who == 0) return -1;
+        int site = 0;
+        if (mine) {
+            int jj = w.j - excl;
+#pragma unroll
+            for (int i = 0; i < kRpl; ++i) {
+                const int pc = __popc(m[i]);
+                if (jj >= 0 && jj < pc) {
+                    uint32_t bits = m[i];
+                    for (int q = 0; q < jj; ++q) bits &= bits - 1;
+                    site = D * (lane * kRpl + i) + (__ffs(bits) - 1) - 1;
+                }
+                jj -= pc;
+            }
+        }
+        return __shfl_sync(kFull, site, __ffs(who) - 1);
+    }
+}
+
+// Flip the chosen site (step 6) and move the class counts of the site and of
+// its 6 neighbours (one thread per domain; values read from the pre-flip
+// state: the staged copy inside, global spins for neighbours outside).
+template <int D>
+__device__ void apply_flip(const LaunchParams &P, CtaShared &S, const WorkItem &w,
+                           const unsigned char *stage, long long g)
+{
+    const LatticeDesc &Ld = P.desc[S.seg_slot[w.ls]];
+    const uint16_t *st = reinterpret_cast<const uint16_t *>(stage + w.off);
+    const int l = w.site;
+    const int x = l % D, y = (l / D) % D, z = l / (D * D);
+    const int sig = w.cls >= 7, us = w.cls - 7 * sig;
+    const int delta = sig ? -1 : 1; // change of the neighbours' up count
+    int32_t *cnt = Ld.counts;
+    bool ok = true;
+    atomicAdd(cnt + w.k * kCountStride + w.cls, -1);
+    atomicAdd(cnt + w.k * kCountStride + 7 * (1 - sig) + us, 1);
+#pragma unroll 1
+    for (int dir = 0; dir < 6; ++dir) {
+        const int jx = x + (dir == 0 ? -1 : dir == 1 ? 1 : 0);
+        const int jy = y + (dir == 2 ? -1 : dir == 3 ? 1 : 0);
+        const int jz = z + (dir == 4 ? -1 : dir == 5 ? 1 : 0);
+        const int sj = staged_bit<D>(st, jx, jy, jz);
+        int uj;
+        long long kj = w.k;
+        if (jx >= 0 && jx < D && jy >= 0 && jy < D && jz >= 0 && jz < D) {
+            uj = staged_bit<D>(st, jx - 1, jy, jz) + staged_bit<D>(st, jx + 1, jy, jz) +
+                 staged_bit<D>(st, jx, jy - 1, jz) + staged_bit<D>(st, jx, jy + 1, jz) +
+                 staged_bit<D>(st, jx, jy, jz - 1) + staged_bit<D>(st, jx, jy, jz + 1);
+        } else {
+            const int X = w.dx * D + jx, Y = w.dy * D + jy, Z = w.dz * D + jz;
+            uj = spin_at<D>(Ld, X - 1, Y, Z) + spin_at<D>(Ld, X + 1, Y, Z) + spin_at<D>(Ld, X, Y - 1, Z) +
+                 spin_at<D>(Ld, X, Y + 1, Z) + spin_at<D>(Ld, X, Y, Z - 1) + spin_at<D>(Ld, X, Y, Z + 1);
+            kj = domain_index(Ld.nd, wrap_coord(X, Ld.L) / D, wrap_coord(Y, Ld.L) / D,
+                              wrap_coord(Z, Ld.L) / D);
+        }
+        const int cold = 7 * sj + uj, cnew = cold + delta;
+        if (cold >= 0 && cold < kClasses && cnew >= 0 && cnew < kClasses) {
+            atomicAdd(cnt + kj * kCountStride + cold, -1);
+            atomicAdd(cnt + kj * kCountStride + cnew, 1);
+        } else {
+            ok = false;
+        }
+    }
+    if (!ok) raise_error(P.err, SPKMC_EINTERNAL);
+    xor_u16(Ld.rows + w.k * (D * D) + y + D * z, 1u << x);
+    uint16_t *mir = Ld.mirrors + w.k * (4 * D);
+    if (x == 0) xor_u16(mir + 0 * D + z, 1u << y);
+    if (x == D - 1) xor_u16(mir + 1 * D + z, 1u << y);
+    if (y == 0) xor_u16(mir + 2 * D + z, 1u << x);
+    if (y == D - 1) xor_u16(mir + 3 * D + z, 1u << x);
+    const long long t = S.seg_t0[w.ls] + g;
+    if (Ld.log) {
+        const long long idx = (t - Ld.log_t0) * Ld.Kact + w.a;
+        if (idx >= 0 && idx < Ld.log_cap) {
+            spkmc_event ev;
+            ev.cycle = t;
+            ev.domain = (int32_t)w.k;
+            ev.cls = w.cls;
+            ev.site = l;
+            ev.reserved = 0;
+            Ld.log[idx] = ev;
+        }
+    }
+    // M and B move by -2 sigma and -2 sigma S (Eq. 1 and Eq. 4, S = 2u - 6)
+    const long long sgn = sig ? 1 : -1;
+    atomicAdd(&S.seg_nflip[w.ls], 1ULL);
+    atomicAdd(&S.seg_dM[w.ls], (unsigned long long)(-2 * sgn));
+    atomicAdd(&S.seg_dB[w.ls], (unsigned long long)(-2 * sgn * (2 * us - 6)));
+}
+
+// Steps 3, 4/4b, 5 and 6 for the CTA's item range, in rounds that fit the
+// staging area.
+__device__ void phase_b(const LaunchParams &P, CtaShared &S, unsigned char *stage, long long g,
+                        long long lo, long long hi, unsigned &mbar_phase)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (long long rbase = lo; rbase < hi; rbase += kThreads) {
-        if (threadIdx.x == 0) S.nwork = 0;
+    const int R = P.round_items;
+    for (long long rbase = lo; rbase < hi; rbase += R) {
+        if (threadIdx.x == 0) {
+            S.nwork = 0;
+            S.bulk_bytes = 0;
+        }
         __syncthreads();
         const long long q = rbase + threadIdx.x;
         int ls = -1;
         unsigned long long fxlo = 0, fxhi = 0;
-        if (q < hi) {
+        if (threadIdx.x < R && q < hi) {
             ls = find_segment(S, q);
             if (g < S.seg_part[ls]) {
                 const int slot = S.seg_slot[ls];
@@ -581,12 +796,21 @@ __device__ void phase_b(const LaunchParams &P, CtaShared &S, long long g, long l
                 } else {
                     const unsigned long long nc =
                         (unsigned long long)__ldcg(Ld.counts + k * kCountStride + cls);
+                    const int idx = atomicAdd(&S.nwork, 1);
                     WorkItem wi;
+                    wi.k = k;
                     wi.ls = ls;
                     wi.a = (int)a;
                     wi.cls = cls;
                     wi.j = (int)__umul64hi(w1, nc);
-                    S.work[atomicAdd(&S.nwork, 1)] = wi;
+                    wi.off = idx * P.item_bytes;
+                    wi.site = -1;
+                    wi.dx = (short)dx;
+                    wi.dy = (short)dy;
+                    wi.dz = (short)dz;
+                    wi.d = (short)Ld.d;
+                    S.work[idx] = wi;
+                    if (Ld.d >= 8) atomicAdd(&S.bulk_bytes, staged_bytes(Ld.d));
                 }
                 if (a == 0) {
                     // Step 5: one global time increment per cycle.
@@ -611,13 +835,56 @@ __device__ void phase_b(const LaunchParams &P, CtaShared &S, long long g, long l
         }
         __syncthreads();
         const int nwork = S.nwork;
+        const int bulk = S.bulk_bytes;
+        if (nwork == 0) continue;
+        // stage every selected domain of the round at once
+        if (bulk > 0 && threadIdx.x == 0) mbar_expect_tx(&S.mbar, (unsigned)bulk);
+        __syncthreads();
+        if (threadIdx.x < nwork) {
+            const WorkItem w = S.work[threadIdx.x];
+            if (w.d >= 8) asm volatile("fence.proxy.async.global;" ::: "memory");
+            const LatticeDesc &Ld = P.desc[S.seg_slot[w.ls]];
+            switch (w.d) {
+            case 2: stage_domain<2>(Ld, w, stage, &S.mbar); break;
+            case 4: stage_domain<4>(Ld, w, stage, &S.mbar); break;
+            case 8: stage_domain<8>(Ld, w, stage, &S.mbar); break;
+            default: stage_domain<16>(Ld, w, stage, &S.mbar); break;
+            }
+        }
+        if (bulk > 0) {
+            if (!mbar_wait_bounded(P, &S.mbar, mbar_phase)) {
+                S.ok = 0; // copies never landed: leave without touching the area
+            }
+            mbar_phase ^= 1u;
+        }
+        __syncthreads();
+        if (!*reinterpret_cast<volatile int *>(&S.ok)) return;
+        // rank and pick the site, one warp per domain
         for (int i = warp; i < nwork; i += kWarps) {
-            const WorkItem wi = S.work[i];
-            switch (P.desc[S.seg_slot[wi.ls]].d) {
-            case 2: select_and_flip<2>(P, S, wi, g, warp, lane); break;
-            case 4: select_and_flip<4>(P, S, wi, g, warp, lane); break;
-            case 8: select_and_flip<8>(P, S, wi, g, warp, lane); break;
-            default: select_and_flip<16>(P, S, wi, g, warp, lane); break;
+            const WorkItem &w = S.work[i];
+            int site;
+            switch (w.d) {
+            case 2: site = select_site<2>(w, stage, lane); break;
+            case 4: site = select_site<4>(w, stage, lane); break;
+            case 8: site = select_site<8>(w, stage, lane); break;
+            default: site = select_site<16>(w, stage, lane); break;
+            }
+            if (lane == 0) {
+                S.work[i].site = site;
+                if (site < 0) raise_error(P.err, SPKMC_EINTERNAL);
+            }
+        }
+        __syncthreads();
+        // flips and class moves, one thread per domain
+        if (threadIdx.x < nwork) {
+            const WorkItem w = S.work[threadIdx.x];
+            if (w.site >= 0) {
+                switch (w.d) {
+                case 2: apply_flip<2>(P, S, w, stage, g); break;
+                case 4: apply_flip<4>(P, S, w, stage, g); break;
+                case 8: apply_flip<8>(P, S, w, stage, g); break;
+                default: apply_flip<16>(P, S, w, stage, g); break;
+                }
             }
         }
         __syncthreads();
@@ -627,6 +894,7 @@ __device__ void phase_b(const LaunchParams &P, CtaShared &S, long long g, long l
 __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams P)
 {
     __shared__ CtaShared S;
+    extern __shared__ __align__(128) unsigned char stage[];
     const long long G = gridDim.x;
     const long long lo = (P.Q * (long long)blockIdx.x) / G;
     const long long hi = (P.Q * ((long long)blockIdx.x + 1)) / G;
@@ -653,6 +921,7 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
         }
         S.seg_base[n] = (i < P.nseg) ? P.seg[i].base : P.Q;
         S.nsegc = n;
+        mbar_init(&S.mbar, 1);
     }
     __syncthreads();
     if (!S.ok) return; // the host sizes the grid so that this cannot happen
@@ -666,11 +935,13 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
         S.seg_nnull[i] = 0;
         S.seg_fxlo[i] = 0;
         S.seg_fxhi[i] = 0;
+        S.seg_dM[i] = 0;
+        S.seg_dB[i] = 0;
     }
     __syncthreads();
     if (ld_volatile_int(P.err) != 0) return;
 
-    unsigned epoch = 0;
+    unsigned epoch = 0, mbar_phase = 0;
     for (long long g = 0; g < P.ncycles; ++g) {
         phase_a(P, S, g, lo, hi);
         __syncthreads();
@@ -682,7 +953,8 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
             S.seg_rmax[i] = 0;
         }
         if (!grid_barrier(P, S, epoch)) return;
-        phase_b(P, S, g, lo, hi);
+        phase_b(P, S, stage, g, lo, hi, mbar_phase);
+        if (!*reinterpret_cast<volatile int *>(&S.ok)) return;
         if (g + 1 < P.ncycles) {
             const bool odd = P.parity0 >= 0 && (((long long)P.parity0 + g) & 1LL) == 1LL;
             if (odd) {
@@ -697,6 +969,8 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
         LatticeState &st = P.state[S.seg_slot[i]];
         if (S.seg_nflip[i]) atomicAdd(&st.n_flip, S.seg_nflip[i]);
         if (S.seg_nnull[i]) atomicAdd(&st.n_null, S.seg_nnull[i]);
+        if (S.seg_dM[i]) atomicAdd(reinterpret_cast<unsigned long long *>(&st.M), S.seg_dM[i]);
+        if (S.seg_dB[i]) atomicAdd(reinterpret_cast<unsigned long long *>(&st.B), S.seg_dB[i]);
         atomic_add_u128(&st.null_fx_lo, &st.null_fx_hi, S.seg_fxlo[i], S.seg_fxhi[i]);
         if (S.seg_base[i] >= lo) { // this CTA owns the lattice's first active domain
             st.t = S.seg_t0[i] + S.seg_part[i];
@@ -889,15 +1163,24 @@ KernelShape cycle_kernel_shape()
 {
     KernelShape s;
     s.threads = kThreads;
-    s.smem_bytes = 0; // all static
+    s.smem_bytes = kStageBytes;
     return s;
+}
+
+int cycle_round_items(int d_max)
+{
+    const int per = kStageBytes / staged_bytes(d_max);
+    return per < kThreads ? per : kThreads;
 }
 
 int cycle_kernel_max_blocks_per_sm(int device)
 {
     (void)device;
+    if (cudaFuncSetAttribute(spkmc_cycles_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kStageBytes) != cudaSuccess)
+        return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, spkmc_cycles_kernel, kThreads, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, spkmc_cycles_kernel, kThreads, kStageBytes) !=
         cudaSuccess)
         return 0;
     return n;
@@ -908,7 +1191,7 @@ int launch_cycles(const LaunchParams &p, int grid, void *stream, bool cooperativ
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = kStageBytes;
     cfg.stream = (cudaStream_t)stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;

@@ -171,7 +171,7 @@ int spkmc_synchronize(spkmc_t *h);
 /* Synchronise and compute the observables on the device. */
 int spkmc_observables(spkmc_t *h, spkmc_obs *out);
 /* Copy spins to/from a host int8 buffer of n = L^3 entries in global order.
- * set_spins recomputes the face mirrors and class counts on the device. */
+ * set_spins recomputes the ghost faces, class counts, M and B on the device. */
 int spkmc_get_spins(spkmc_t *h, int8_t *host_buf, size_t n);
 int spkmc_set_spins(spkmc_t *h, const int8_t *host_buf, size_t n);
 /* Copy up to cap logged events (cycle-major, ascending k within a cycle);

@@ -1,7 +1,7 @@
 // spkmc_api.cu -- host runtime behind the C ABI declared in include/spkmc.h.
 //
 // A batch owns up to `capacity` lattices (slots).  Each slot holds its device
-// arrays (rows, mirrors, counts, scratch, optional event log) and one entry
+// arrays (domain blocks, counts, scratch, optional event log) and one entry
 // of the device descriptor and state tables.  A run enqueues one persistent
 // cooperative launch over the flat table of the running lattices' active
 // domains (segments sorted by slot).  A single-lattice handle is a batch of
@@ -92,8 +92,8 @@ int check_params(const spkmc_params *p, int *d_out)
 }
 
 struct Sizes {
-    long long K, Kact, rows_b, mirrors_b, counts_b, scratch_b, log_b;
-    long long total() const { return rows_b + mirrors_b + counts_b + scratch_b + log_b; }
+    long long K, Kact, cells_b, counts_b, scratch_b, log_b;
+    long long total() const { return cells_b + counts_b + scratch_b + log_b; }
 };
 
 Sizes sizes_of(int L, int d, long long log_cap)
@@ -103,8 +103,7 @@ Sizes sizes_of(int L, int d, long long log_cap)
     s.K = nd * nd * nd;
     s.Kact = s.K / 8;
     auto up = [](long long b) { return (b + 255) & ~255LL; };
-    s.rows_b = up(s.K * d * d * 2);
-    s.mirrors_b = up(s.K * 4 * d * 2);
+    s.cells_b = up(s.K * staged_bytes(d));
     s.counts_b = up(s.K * kCountStride * 4);
     s.scratch_b = up(s.Kact * kScratchStride * 8);
     s.log_b = up(log_cap * (long long)sizeof(spkmc_event));
@@ -139,8 +138,8 @@ struct Slot {
     LatticeDesc desc{};   // host copy of the device descriptor
     long long t = 0;      // host mirror of the cycle counter
     long long budget = -1;
-    void *blocks[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    size_t block_bytes[5] = {0, 0, 0, 0, 0};
+    void *blocks[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t block_bytes[4] = {0, 0, 0, 0};
 };
 
 struct spkmc_batch {
@@ -198,7 +197,7 @@ namespace {
 
 void free_slot_memory(spkmc_batch *b, Slot &s)
 {
-    for (int i = 0; i < 5; ++i) {
+    for (int i = 0; i < 4; ++i) {
         b->dev_free(s.blocks[i], s.block_bytes[i]);
         s.blocks[i] = nullptr;
         s.block_bytes[i] = 0;
@@ -325,7 +324,7 @@ int upload_slot(spkmc_batch *b, int slot)
 int refresh_derived(spkmc_batch *b, const LatticeDesc &d)
 {
     int rc;
-    if ((rc = launch_build_mirrors(d, b->stream)) != SPKMC_OK) return cuda_fail(cudaGetLastError(), "mirrors");
+    if ((rc = launch_ghosts(d, 0, nullptr, b->stream)) != SPKMC_OK) return cuda_fail(cudaGetLastError(), "ghost faces");
     if ((rc = launch_count_classes(d, 0, nullptr, b->stream)) != SPKMC_OK)
         return cuda_fail(cudaGetLastError(), "class counts");
     return SPKMC_OK;
@@ -364,8 +363,8 @@ int admit(spkmc_batch *b, const spkmc_params *p, long long cycles, int slot_hint
     s.params.domain_edge = d;
     s.d = d;
     s.sz = sizes_of(p->L, d, p->event_log_capacity);
-    const long long bytes[5] = {s.sz.rows_b, s.sz.mirrors_b, s.sz.counts_b, s.sz.scratch_b, s.sz.log_b};
-    for (int i = 0; i < 5; ++i) {
+    const long long bytes[4] = {s.sz.cells_b, s.sz.counts_b, s.sz.scratch_b, s.sz.log_b};
+    for (int i = 0; i < 4; ++i) {
         if (bytes[i] == 0) continue;
         s.blocks[i] = b->dev_alloc((size_t)bytes[i]);
         s.block_bytes[i] = (size_t)bytes[i];
@@ -376,11 +375,10 @@ int admit(spkmc_batch *b, const spkmc_params *p, long long cycles, int slot_hint
         }
     }
     LatticeDesc &D = s.desc;
-    D.rows = (uint16_t *)s.blocks[0];
-    D.mirrors = (uint16_t *)s.blocks[1];
-    D.counts = (int32_t *)s.blocks[2];
-    D.scratch = (double *)s.blocks[3];
-    D.log = p->event_log_capacity > 0 ? (spkmc_event *)s.blocks[4] : nullptr;
+    D.cells = (uint16_t *)s.blocks[0];
+    D.counts = (int32_t *)s.blocks[1];
+    D.scratch = (double *)s.blocks[2];
+    D.log = p->event_log_capacity > 0 ? (spkmc_event *)s.blocks[3] : nullptr;
     D.log_cap = p->event_log_capacity;
     D.log_t0 = 0;
     host_rates(p->J, p->H, p->T, D.rate);
@@ -842,6 +840,8 @@ int spkmc_check_counts(spkmc_t *h, int64_t *mismatched)
     const LatticeDesc &D = b->slots[h->slot].desc;
     if ((rc = launch_count_classes(D, 1, b->d_mismatch, b->stream)) != SPKMC_OK)
         return cuda_fail(cudaGetLastError(), "recount");
+    if ((rc = launch_ghosts(D, 1, b->d_mismatch, b->stream)) != SPKMC_OK)
+        return cuda_fail(cudaGetLastError(), "ghost check");
     if ((rc = launch_observables(D, b->d_MB, b->stream)) != SPKMC_OK)
         return cuda_fail(cudaGetLastError(), "observables kernel");
     CUDA_TRY(cudaMemcpyAsync(b->h_MB, b->d_MB, 2 * sizeof(long long), cudaMemcpyDeviceToHost, b->stream),

@@ -1,20 +1,22 @@
 // Internal types shared by the kernels (spkmc_kernels.cu) and the host
 // runtime (spkmc_api.cu).  Device data layout of one lattice, for domain edge d:
 //
-//   rows    [K][d*d]  uint16: bit x of slot (y + d*z) is 1 when spin (x,y,z)
-//                     of the domain is +1 (a row of d spins along x);
-//   mirrors [K][4][d] uint16: copies of the domain's faces so a neighbour reads
-//                     its halo as whole 2d-byte lines: face 0 = x=0 and face
-//                     1 = x=d-1 (bit y, index z), face 2 = y=0 and face
-//                     3 = y=d-1 (bit x, index z);  z faces are rows already;
+//   cells   [K][d*d + 6*d] uint16, one contiguous block per domain:
+//           rows[d*d]  bit x of slot (y + d*z) is 1 when spin (x,y,z) is +1;
+//           ghosts[6][d]  copies of the neighbours' faces that touch the
+//           domain (the one-site halo), kept current by the neighbours' flips:
+//             0 gxm[z] bit y = spin (x=-1, y, z)   (x = d-1 face of the -x domain)
+//             1 gxp[z] bit y = spin (x=d, y, z)    (x = 0 face of the +x domain)
+//             2 gym[z] bit x = spin (x, y=-1, z)
+//             3 gyp[z] bit x = spin (x, y=d, z)
+//             4 gzm[y] bit x = spin (x, y, z=-1)
+//             5 gzp[y] bit x = spin (x, y, z=d)
+//           so a domain with its halo is 2d^2 + 12d bytes (704 for d = 16),
+//           read by one bulk copy;
 //   counts  [K][16]   int32: number of sites of each of the 14 classes;
-//   scratch [K/8][16] double: per active domain of the running cycle, the
-//                     cumulative frequency line cum[0..13], u01 and w1.
-// Staged copy of one domain in shared memory (phase B), u16 words:
-//   rows[d*d] | fxm[d] | fxp[d] | fym[d] | fyp[d] | rzm[d] | rzp[d]
-// fxm = x = d-1 face of the -x neighbour, fxp = x = 0 face of the +x
-// neighbour, fym / fyp the same along y, rzm = rows (y, d-1) of the -z
-// neighbour, rzp = rows (y, 0) of the +z neighbour.
+//   scratch [K/8][20] 8-byte words: per active domain of the running cycle,
+//           the cumulative frequency line cum[0..13], u01, w1 and the 14
+//           class counts as uint16.
 #pragma once
 
 #include <cstdint>
@@ -25,15 +27,14 @@ namespace spkmc {
 
 constexpr int kClasses = 14;
 constexpr int kCountStride = 16;   // int32 per domain in counts
-constexpr int kScratchStride = 16; // doubles per active domain in scratch
+constexpr int kScratchStride = 20; // 8-byte words per active domain in scratch
 constexpr int kMaxEdge = 16;
 constexpr int kPadRow = kMaxEdge + 2;           // padded rows per axis
 constexpr int kPadWords = kPadRow * kPadRow;    // words of one padded domain
 constexpr int kMaxSegPerCta = 64;               // lattices one CTA may touch
 
 struct LatticeDesc {
-    uint16_t *rows;
-    uint16_t *mirrors;
+    uint16_t *cells;
     int32_t *counts;
     double *scratch;
     spkmc_event *log;
@@ -83,8 +84,9 @@ struct LaunchParams {
     int pad;
 };
 
-// Bytes of one staged domain: its rows and its six face halos.
-__host__ __device__ constexpr int staged_bytes(int d) { return 2 * d * d + 12 * d; }
+// u16 words and bytes of one domain block (rows and ghost faces).
+__host__ __device__ constexpr int block_words(int d) { return d * d + 6 * d; }
+__host__ __device__ constexpr int staged_bytes(int d) { return 2 * block_words(d); }
 constexpr int kStageBytes = 88 * 1024; // phase-B staging area per CTA
 
 // Host-side launch helpers implemented in spkmc_kernels.cu.
@@ -98,7 +100,9 @@ int launch_cycles(const LaunchParams &p, int grid, void *stream, bool cooperativ
 int launch_init_rows(const LatticeDesc &d, int init, void *stream);
 int launch_pack_rows(const LatticeDesc &d, const int8_t *dev_spins, void *stream);
 int launch_unpack_rows(const LatticeDesc &d, int8_t *dev_spins, void *stream);
-int launch_build_mirrors(const LatticeDesc &d, void *stream);
+// mode 0: rebuild every domain's ghost faces from its neighbours' rows;
+// mode 1: compare and add the number of stale ghost words to *mismatch.
+int launch_ghosts(const LatticeDesc &d, int mode, unsigned long long *mismatch, void *stream);
 // mode 0: write counts; mode 1: compare with the stored counts and add the
 // number of mismatching domains to *mismatch (device int64).
 int launch_count_classes(const LatticeDesc &d, int mode, unsigned long long *mismatch,

@@ -2,22 +2,25 @@
 // Sec. 3.1 steps 1-6 with the chessboard sublattice of Sec. 3.2).
 //
 // One persistent cooperative launch runs many cycles.  Per cycle:
-//   phase A (step 1)   one lane per active domain reads the domain's 14 class
-//                      counts, builds the cumulative frequency line in FP64
-//                      (class order, no fused multiply-add), draws its Philox
-//                      block and keeps the line in scratch; partial maxima go
-//                      to shared memory, then one atomicMax per CTA and lattice;
-//   grid barrier       (step 2: R_max is known everywhere);
-//   phase B (steps 3-6) one lane per domain finds the event on the line padded
-//                      by the null rate R_max - R_k; one warp per non-null
-//                      domain stages the domain and its 1-site halo (bit
-//                      packed) into shared memory, classifies its rows with a
-//                      bit-sliced adder, finds the j-th site of the chosen class
-//                      with popc + warp scan, flips it and moves the class
-//                      counts of the site and its 6 neighbours;
-//   grid barrier       (step 6: the flips are visible) -- skipped after an odd
-//                      cycle, whose flips never touch the counts that the next
-//                      colour reads.
+//   phase A (step 1)    one lane per active domain reads the domain's 14 class
+//                       counts, builds the cumulative frequency line in FP64
+//                       (class order, no fused multiply-add), draws its Philox
+//                       block and keeps the line in scratch; partial maxima
+//                       go to shared memory, then one atomicMax per CTA and
+//                       lattice;
+//   grid barrier        (step 2: R_max is known everywhere);
+//   phase B (steps 3-6) one lane per domain finds its event on the line
+//                       padded by the null rate R_max - R_k; the blocks of the
+//                       domains that flip (rows and one-site halo, 704 bytes
+//                       at d = 16) are staged into shared memory by bulk
+//                       copies on the TMA engine; one warp per domain ranks
+//                       the sites of the chosen class with a bit-sliced adder,
+//                       popc and a warp scan; one thread per domain flips the
+//                       site, moves the class counts of the site and of its 6
+//                       neighbours and refreshes the neighbours' ghost faces;
+//   grid barrier        (step 6: the flips are visible) -- skipped after an
+//                       odd cycle, whose flips never touch the data that the
+//                       next colour reads.
 // The clock (step 5) is advanced once per cycle by the lane that owns the
 // lattice's first active domain.
 #include <cuda_runtime.h>
@@ -90,7 +93,7 @@ __device__ __forceinline__ int ld_volatile_int(const int *p)
     return *reinterpret_cast<const volatile int *>(p);
 }
 
-__device__ __forceinline__ uint32_t ld_row(const uint16_t *p)
+__device__ __forceinline__ uint32_t ld_u16(const uint16_t *p)
 {
     return (uint32_t)__ldcg(reinterpret_cast<const unsigned short *>(p));
 }
@@ -156,74 +159,74 @@ __device__ __forceinline__ long long domain_index(int nd, int dx, int dy, int dz
     return (long long)dx + (long long)nd * ((long long)dy + (long long)nd * dz);
 }
 
+__device__ __forceinline__ void domain_coords(const LatticeDesc &Ld, long long k, int &dx, int &dy, int &dz)
+{
+    dx = (int)(k % Ld.nd);
+    dy = (int)((k / Ld.nd) % Ld.nd);
+    dz = (int)(k / ((long long)Ld.nd * Ld.nd));
+}
+
 __device__ __forceinline__ int wrap_coord(int a, int n)
 {
     return a < 0 ? a + n : (a >= n ? a - n : a);
 }
 
-// Spin bit (1 = up) of global site (X, Y, Z), coordinates taken modulo L.
 template <int D>
-__device__ __forceinline__ int spin_at(const LatticeDesc &Ld, int X, int Y, int Z)
+__device__ __forceinline__ uint16_t *block_of(const LatticeDesc &Ld, long long k)
+{
+    return Ld.cells + k * block_words(D);
+}
+
+// Address of the row holding global site (X, Y, Z) (coordinates modulo L)
+// and the site's bit in it.
+template <int D>
+__device__ __forceinline__ const uint16_t *row_of_site(const LatticeDesc &Ld, int X, int Y, int Z, int &bit)
 {
     X = wrap_coord(X, Ld.L);
     Y = wrap_coord(Y, Ld.L);
     Z = wrap_coord(Z, Ld.L);
-    long long k = domain_index(Ld.nd, X / D, Y / D, Z / D);
-    uint32_t row = ld_row(Ld.rows + k * (D * D) + (Y % D) + D * (Z % D));
-    return (int)((row >> (X % D)) & 1u);
+    const long long k = domain_index(Ld.nd, X / D, Y / D, Z / D);
+    bit = X % D;
+    return block_of<D>(Ld, k) + (Y % D) + D * (Z % D);
 }
 
-// Padded copy of one domain in shared memory: word (y+1) + (D+2)*(z+1) holds
-// the row (y, z) with spin x in bit x+1, x in [-1, D]; the six face halos come
-// from the neighbours' mirrors (x, y faces) and rows (z faces).
+// Spin bit of local site (x, y, z) of a domain block (global or staged),
+// with at most one coordinate one step outside [0, D) (read from the ghosts).
 template <int D>
-__device__ __forceinline__ void stage_padded(const LatticeDesc &Ld, long long k, int dx, int dy,
-                                             int dz, uint32_t *Pw, int lane)
+__device__ __forceinline__ int block_bit(const uint16_t *blk, int x, int y, int z)
 {
-    const int nd = Ld.nd;
-    const uint16_t *rows = Ld.rows + k * (D * D);
-    const long long kxm = domain_index(nd, wrap_coord(dx - 1, nd), dy, dz);
-    const long long kxp = domain_index(nd, wrap_coord(dx + 1, nd), dy, dz);
-    const long long kym = domain_index(nd, dx, wrap_coord(dy - 1, nd), dz);
-    const long long kyp = domain_index(nd, dx, wrap_coord(dy + 1, nd), dz);
-    const long long kzm = domain_index(nd, dx, dy, wrap_coord(dz - 1, nd));
-    const long long kzp = domain_index(nd, dx, dy, wrap_coord(dz + 1, nd));
-    const uint16_t *fxm = Ld.mirrors + kxm * (4 * D) + 1 * D; // x = D-1 face of the -x neighbour
-    const uint16_t *fxp = Ld.mirrors + kxp * (4 * D) + 0 * D; // x = 0 face of the +x neighbour
-    const uint16_t *fym = Ld.mirrors + kym * (4 * D) + 3 * D; // y = D-1 face of the -y neighbour
-    const uint16_t *fyp = Ld.mirrors + kyp * (4 * D) + 2 * D; // y = 0 face of the +y neighbour
-    const uint16_t *rzm = Ld.rows + kzm * (D * D) + D * (D - 1);
-    const uint16_t *rzp = Ld.rows + kzp * (D * D);
-    for (int r = lane; r < D * D; r += 32) {
-        const int y = r % D, z = r / D;
-        uint32_t v = ld_row(rows + r) << 1;
-        v |= (ld_row(fxm + z) >> y) & 1u;
-        v |= ((ld_row(fxp + z) >> y) & 1u) << (D + 1);
-        Pw[(y + 1) + (D + 2) * (z + 1)] = v;
-    }
-    for (int i = lane; i < D; i += 32) {
-        Pw[(D + 2) * (i + 1)] = ld_row(fym + i) << 1;
-        Pw[(D + 1) + (D + 2) * (i + 1)] = ld_row(fyp + i) << 1;
-        Pw[i + 1] = ld_row(rzm + i) << 1;
-        Pw[(i + 1) + (D + 2) * (D + 1)] = ld_row(rzp + i) << 1;
-    }
-    __syncwarp();
+    const uint16_t *g = blk + D * D;
+    uint32_t w;
+    int b;
+    if (x < 0) { w = g[0 * D + z]; b = y; }
+    else if (x >= D) { w = g[1 * D + z]; b = y; }
+    else if (y < 0) { w = g[2 * D + z]; b = x; }
+    else if (y >= D) { w = g[3 * D + z]; b = x; }
+    else if (z < 0) { w = g[4 * D + y]; b = x; }
+    else if (z >= D) { w = g[5 * D + y]; b = x; }
+    else { w = blk[y + D * z]; b = x; }
+    return (int)((w >> b) & 1u);
 }
 
-// Bit-sliced count of up neighbours for the D sites of row (y, z): u = u0 +
-// 2 u1 + 4 u2 per bit position (bits 1..D are the sites).
+// Bit-sliced count of up neighbours for the D sites of row (y, z) of a
+// domain block: bit x+1 of s is spin x (x in [-1, D], halo from the ghosts)
+// and u = u0 + 2 u1 + 4 u2 per bit position.
 struct RowPlanes {
     uint32_t s, u0, u1, u2;
 };
 
 template <int D>
-__device__ __forceinline__ RowPlanes classify_row(const uint32_t *Pw, int y, int z)
+__device__ __forceinline__ RowPlanes classify_row(const uint16_t *blk, int y, int z)
 {
-    const int base = (y + 1) + (D + 2) * (z + 1);
-    const uint32_t s = Pw[base];
+    const uint16_t *rows = blk, *g = blk + D * D;
+    const int r = y + D * z;
+    const uint32_t s = ((uint32_t)rows[r] << 1) | (((uint32_t)g[0 * D + z] >> y) & 1u) |
+                       ((((uint32_t)g[1 * D + z] >> y) & 1u) << (D + 1));
     const uint32_t a = s << 1, b = s >> 1;
-    const uint32_t c = Pw[base - 1], d = Pw[base + 1];
-    const uint32_t e = Pw[base - (D + 2)], f = Pw[base + (D + 2)];
+    const uint32_t c = (uint32_t)(y > 0 ? rows[r - 1] : g[2 * D + z]) << 1;
+    const uint32_t d = (uint32_t)(y < D - 1 ? rows[r + 1] : g[3 * D + z]) << 1;
+    const uint32_t e = (uint32_t)(z > 0 ? rows[r - D] : g[4 * D + y]) << 1;
+    const uint32_t f = (uint32_t)(z < D - 1 ? rows[r + D] : g[5 * D + y]) << 1;
     const uint32_t s1 = a ^ b ^ c, c1 = (a & b) | (c & (a ^ b));
     const uint32_t s2 = d ^ e ^ f, c2 = (d & e) | (f & (d ^ e));
     const uint32_t k2 = s1 & s2;
@@ -247,60 +250,6 @@ __device__ __forceinline__ uint32_t class_mask(const RowPlanes &p, int cls)
     return m;
 }
 
-template <int D>
-__device__ __forceinline__ int pad_bit(const uint32_t *Pw, int x, int y, int z)
-{
-    return (int)((Pw[(y + 1) + (D + 2) * (z + 1)] >> (x + 1)) & 1u);
-}
-
-// ---------------------------------------------------------------------------
-// Persistent cycle kernel
-// ---------------------------------------------------------------------------
-// Row planes of a staged domain: s = row (y, z) with spin x in bit x+1,
-// the x halo in bits 0 and D+1; the five other planes are the neighbour rows.
-template <int D>
-__device__ __forceinline__ RowPlanes classify_staged_row(const uint16_t *st, int y, int z)
-{
-    const uint16_t *rows = st, *fxm = st + D * D, *fxp = fxm + D, *fym = fxp + D, *fyp = fym + D,
-                   *rzm = fyp + D, *rzp = rzm + D;
-    const int r = y + D * z;
-    const uint32_t s = ((uint32_t)rows[r] << 1) | (((uint32_t)fxm[z] >> y) & 1u) |
-                       ((((uint32_t)fxp[z] >> y) & 1u) << (D + 1));
-    const uint32_t a = s << 1, b = s >> 1;
-    const uint32_t c = (uint32_t)(y > 0 ? rows[r - 1] : fym[z]) << 1;
-    const uint32_t d = (uint32_t)(y < D - 1 ? rows[r + 1] : fyp[z]) << 1;
-    const uint32_t e = (uint32_t)(z > 0 ? rows[r - D] : rzm[y]) << 1;
-    const uint32_t f = (uint32_t)(z < D - 1 ? rows[r + D] : rzp[y]) << 1;
-    const uint32_t s1 = a ^ b ^ c, c1 = (a & b) | (c & (a ^ b));
-    const uint32_t s2 = d ^ e ^ f, c2 = (d & e) | (f & (d ^ e));
-    const uint32_t k2 = s1 & s2;
-    RowPlanes p;
-    p.s = s;
-    p.u0 = s1 ^ s2;
-    p.u1 = c1 ^ c2 ^ k2;
-    p.u2 = (c1 & c2) | (k2 & (c1 ^ c2));
-    return p;
-}
-
-// Spin bit of local site (x, y, z) of a staged domain, one coordinate at most
-// one step outside [0, D) (the face halo).
-template <int D>
-__device__ __forceinline__ int staged_bit(const uint16_t *st, int x, int y, int z)
-{
-    const uint16_t *fxm = st + D * D, *fxp = fxm + D, *fym = fxp + D, *fyp = fym + D, *rzm = fyp + D,
-                   *rzp = rzm + D;
-    uint32_t w;
-    int b;
-    if (x < 0) { w = fxm[z]; b = y; }
-    else if (x >= D) { w = fxp[z]; b = y; }
-    else if (y < 0) { w = fym[z]; b = x; }
-    else if (y >= D) { w = fyp[z]; b = x; }
-    else if (z < 0) { w = rzm[y]; b = x; }
-    else if (z >= D) { w = rzp[y]; b = x; }
-    else { w = st[y + D * z]; b = x; }
-    return (int)((w >> b) & 1u);
-}
-
 // ---------------------------------------------------------------------------
 // Persistent cycle kernel
 // ---------------------------------------------------------------------------
@@ -310,7 +259,7 @@ struct __align__(16) WorkItem {
     int a;        // active index within the lattice
     int cls;      // chosen class
     int j;        // rank of the site within the class
-    int off;      // byte offset of the staged copy
+    int off;      // byte offset of the staged block
     int site;     // chosen local site (set by the classifier), -1 if none
     short dx, dy, dz, d;
 };
@@ -326,6 +275,7 @@ struct CtaShared {
     unsigned long long seg_fxhi[kMaxSegPerCta];
     unsigned long long seg_dM[kMaxSegPerCta];
     unsigned long long seg_dB[kMaxSegPerCta];
+    double seg_nlogxi[kMaxSegPerCta]; // -ln(xi) of the running cycle
     int seg_slot[kMaxSegPerCta];
     unsigned long long mbar;
     int nsegc;
@@ -374,7 +324,7 @@ __device__ bool grid_barrier(const LaunchParams &P, CtaShared &S, unsigned &epoc
                     break;
                 }
             }
-            __nanosleep(20);
+            __nanosleep(32);
         }
         __threadfence();
         S.ok = ok;
@@ -499,7 +449,19 @@ __device__ void phase_a(const LaunchParams &P, CtaShared &S, long long g, long l
 #pragma unroll
                 for (int c = 0; c < kClasses; c += 2) __stcg(sp + c / 2, make_double2(cum[c], cum[c + 1]));
                 __stcg(sp + 7, make_double2(u01, __longlong_as_double((long long)w[1])));
+                uint4 *np = reinterpret_cast<uint4 *>(sp + 8);
+                __stcg(np, make_uint4((uint32_t)n[0] | ((uint32_t)n[1] << 16), (uint32_t)n[2] | ((uint32_t)n[3] << 16),
+                                      (uint32_t)n[4] | ((uint32_t)n[5] << 16), (uint32_t)n[6] | ((uint32_t)n[7] << 16)));
+                __stcg(np + 1, make_uint4((uint32_t)n[8] | ((uint32_t)n[9] << 16), (uint32_t)n[10] | ((uint32_t)n[11] << 16),
+                                          (uint32_t)n[12] | ((uint32_t)n[13] << 16), 0u));
                 rbits = (unsigned long long)__double_as_longlong(acc);
+                if (a == 0) {
+                    // -ln(xi) of this cycle's time step (step 5), drawn ahead
+                    unsigned long long wc[4];
+                    philox4x64_10((unsigned long long)t, 0ULL, 2ULL, 0ULL, Ld.seed, 0ULL, wc);
+                    const double xi = __ull2double_rn(2ULL * (wc[0] >> 12) + 1ULL) * 0x1p-53;
+                    S.seg_nlogxi[ls] = -log(xi);
+                }
             } else {
                 ls = -1;
             }
@@ -514,42 +476,8 @@ __device__ void phase_a(const LaunchParams &P, CtaShared &S, long long g, long l
     }
 }
 
-// Stage one domain and its face halos into shared memory: bulk copies on the
-// TMA engine for D >= 8 (every piece is a multiple of 16 bytes), plain loads
-// for the small edges.
-template <int D>
-__device__ __forceinline__ void stage_domain(const LatticeDesc &Ld, const WorkItem &w,
-                                             unsigned char *stage, unsigned long long *mbar)
-{
-    const int nd = Ld.nd;
-    const long long kxm = domain_index(nd, wrap_coord(w.dx - 1, nd), w.dy, w.dz);
-    const long long kxp = domain_index(nd, wrap_coord(w.dx + 1, nd), w.dy, w.dz);
-    const long long kym = domain_index(nd, w.dx, wrap_coord(w.dy - 1, nd), w.dz);
-    const long long kyp = domain_index(nd, w.dx, wrap_coord(w.dy + 1, nd), w.dz);
-    const long long kzm = domain_index(nd, w.dx, w.dy, wrap_coord(w.dz - 1, nd));
-    const long long kzp = domain_index(nd, w.dx, w.dy, wrap_coord(w.dz + 1, nd));
-    const uint16_t *src[7] = {Ld.rows + w.k * (D * D),
-                              Ld.mirrors + kxm * (4 * D) + 1 * D,
-                              Ld.mirrors + kxp * (4 * D) + 0 * D,
-                              Ld.mirrors + kym * (4 * D) + 3 * D,
-                              Ld.mirrors + kyp * (4 * D) + 2 * D,
-                              Ld.rows + kzm * (D * D) + D * (D - 1),
-                              Ld.rows + kzp * (D * D)};
-    uint16_t *dst = reinterpret_cast<uint16_t *>(stage + w.off);
-    if constexpr (D >= 8) {
-        bulk_copy_g2s(dst, src[0], 2 * D * D, mbar);
-#pragma unroll
-        for (int i = 1; i < 7; ++i) bulk_copy_g2s(dst + D * D + (i - 1) * D, src[i], 2 * D, mbar);
-    } else {
-        for (int r = 0; r < D * D; ++r) dst[r] = (uint16_t)ld_row(src[0] + r);
-#pragma unroll
-        for (int i = 1; i < 7; ++i)
-            for (int r = 0; r < D; ++r) dst[D * D + (i - 1) * D + r] = (uint16_t)ld_row(src[i] + r);
-    }
-}
-
 // Rank the sites of class w.cls in ascending local index and return the
-// w.j-th (warp-cooperative, from the staged copy); -1 if the class is short.
+// w.j-th (warp-cooperative, from the staged block); -1 if the class is short.
 template <int D>
 __device__ int select_site(const WorkItem &w, const unsigned char *stage, int lane)
 {
@@ -557,19 +485,18 @@ __device__ int select_site(const WorkItem &w, const unsigned char *stage, int la
     const int sig = w.cls >= 7, us = w.cls - 7 * sig;
     if constexpr (D == 16) {
         // lane l holds rows r0..r0+7 (z = l/2, y = 8(l&1)..+7) as four pairs of
-        // 16-bit rows per 32-bit word: bit b of pair p is site l = 16 (r0+2p) + b
+        // 16-bit rows per 32-bit word: bit b of pair p is site 16 (r0+2p) + b
         const int z = lane >> 1, y0 = (lane & 1) * 8, r0 = lane * 8;
-        const uint16_t *fxm = st + 256, *fxp = fxm + 16, *fym = fxp + 16, *fyp = fym + 16,
-                       *rzm = fyp + 16, *rzp = rzm + 16;
+        const uint16_t *g = st + 256;
         const uint4 cur4 = *reinterpret_cast<const uint4 *>(st + r0);
-        const uint4 zm4 = *reinterpret_cast<const uint4 *>(z > 0 ? st + r0 - 16 : rzm + y0);
-        const uint4 zp4 = *reinterpret_cast<const uint4 *>(z < 15 ? st + r0 + 16 : rzp + y0);
+        const uint4 zm4 = *reinterpret_cast<const uint4 *>(z > 0 ? st + r0 - 16 : g + 4 * 16 + y0);
+        const uint4 zp4 = *reinterpret_cast<const uint4 *>(z < 15 ? st + r0 + 16 : g + 5 * 16 + y0);
         const uint32_t cur[4] = {cur4.x, cur4.y, cur4.z, cur4.w};
         const uint32_t zmv[4] = {zm4.x, zm4.y, zm4.z, zm4.w};
         const uint32_t zpv[4] = {zp4.x, zp4.y, zp4.z, zp4.w};
-        const uint32_t below = (uint32_t)(y0 == 0 ? fym[z] : st[r0 - 1]); // row y0-1
-        const uint32_t above = (uint32_t)(y0 == 8 ? fyp[z] : st[r0 + 8]); // row y0+8
-        const uint32_t hxm = fxm[z], hxp = fxp[z];
+        const uint32_t below = (uint32_t)(y0 == 0 ? g[2 * 16 + z] : st[r0 - 1]); // row y0-1
+        const uint32_t above = (uint32_t)(y0 == 8 ? g[3 * 16 + z] : st[r0 + 8]); // row y0+8
+        const uint32_t hxm = g[0 * 16 + z], hxp = g[1 * 16 + z];
         uint32_t m[4];
         int tot = 0;
 #pragma unroll
@@ -629,7 +556,7 @@ __device__ int select_site(const WorkItem &w, const unsigned char *stage, int la
             m[i] = 0;
             if (on) {
                 const int r = lane * kRpl + i;
-                m[i] = class_mask<D>(classify_staged_row<D>(st, r % D, r / D), w.cls);
+                m[i] = class_mask<D>(classify_row<D>(st, r % D, r / D), w.cls);
                 tot += __popc(m[i]);
             }
         }
@@ -661,9 +588,36 @@ __device__ int select_site(const WorkItem &w, const unsigned char *stage, int la
     }
 }
 
-// Flip the chosen site (step 6) and move the class counts of the site and of
-// its 6 neighbours (one thread per domain; values read from the pre-flip
-// state: the staged copy inside, global spins for neighbours outside).
+// Up count of the neighbour (jx, jy, jz) of the flipped site, from the
+// pre-flip state: the staged block holds the one-site halo, global memory the
+// rest (the second layer and the edges of a neighbour face).  The global
+// loads of the six directions are independent of each other.
+template <int D>
+__device__ __forceinline__ int neighbour_up(const LatticeDesc &Ld, const WorkItem &w, const uint16_t *st,
+                                            int jx, int jy, int jz)
+{
+    int u = 0;
+#pragma unroll
+    for (int n = 0; n < 6; ++n) {
+        const int nx = jx + (n == 0 ? -1 : n == 1 ? 1 : 0);
+        const int ny = jy + (n == 2 ? -1 : n == 3 ? 1 : 0);
+        const int nz = jz + (n == 4 ? -1 : n == 5 ? 1 : 0);
+        const int outs = (nx < 0 || nx >= D) + (ny < 0 || ny >= D) + (nz < 0 || nz >= D);
+        const bool near = nx >= -1 && nx <= D && ny >= -1 && ny <= D && nz >= -1 && nz <= D && outs <= 1;
+        if (near) {
+            u += block_bit<D>(st, nx, ny, nz);
+        } else {
+            int bit;
+            const uint16_t *row = row_of_site<D>(Ld, w.dx * D + nx, w.dy * D + ny, w.dz * D + nz, bit);
+            u += (int)((ld_u16(row) >> bit) & 1u);
+        }
+    }
+    return u;
+}
+
+// Flip the chosen site (step 6), move the class counts of the site and of its
+// 6 neighbours, and refresh the ghost faces of the neighbour domains that see
+// the site (one thread per domain).
 template <int D>
 __device__ void apply_flip(const LaunchParams &P, CtaShared &S, const WorkItem &w,
                            const unsigned char *stage, long long g)
@@ -675,43 +629,42 @@ __device__ void apply_flip(const LaunchParams &P, CtaShared &S, const WorkItem &
     const int sig = w.cls >= 7, us = w.cls - 7 * sig;
     const int delta = sig ? -1 : 1; // change of the neighbours' up count
     int32_t *cnt = Ld.counts;
-    bool ok = true;
-    atomicAdd(cnt + w.k * kCountStride + w.cls, -1);
-    atomicAdd(cnt + w.k * kCountStride + 7 * (1 - sig) + us, 1);
-#pragma unroll 1
+    const int nd = Ld.nd;
+    int cold[6];
+    long long kj[6];
+#pragma unroll
     for (int dir = 0; dir < 6; ++dir) {
         const int jx = x + (dir == 0 ? -1 : dir == 1 ? 1 : 0);
         const int jy = y + (dir == 2 ? -1 : dir == 3 ? 1 : 0);
         const int jz = z + (dir == 4 ? -1 : dir == 5 ? 1 : 0);
-        const int sj = staged_bit<D>(st, jx, jy, jz);
-        int uj;
-        long long kj = w.k;
-        if (jx >= 0 && jx < D && jy >= 0 && jy < D && jz >= 0 && jz < D) {
-            uj = staged_bit<D>(st, jx - 1, jy, jz) + staged_bit<D>(st, jx + 1, jy, jz) +
-                 staged_bit<D>(st, jx, jy - 1, jz) + staged_bit<D>(st, jx, jy + 1, jz) +
-                 staged_bit<D>(st, jx, jy, jz - 1) + staged_bit<D>(st, jx, jy, jz + 1);
-        } else {
-            const int X = w.dx * D + jx, Y = w.dy * D + jy, Z = w.dz * D + jz;
-            uj = spin_at<D>(Ld, X - 1, Y, Z) + spin_at<D>(Ld, X + 1, Y, Z) + spin_at<D>(Ld, X, Y - 1, Z) +
-                 spin_at<D>(Ld, X, Y + 1, Z) + spin_at<D>(Ld, X, Y, Z - 1) + spin_at<D>(Ld, X, Y, Z + 1);
-            kj = domain_index(Ld.nd, wrap_coord(X, Ld.L) / D, wrap_coord(Y, Ld.L) / D,
-                              wrap_coord(Z, Ld.L) / D);
-        }
-        const int cold = 7 * sj + uj, cnew = cold + delta;
-        if (cold >= 0 && cold < kClasses && cnew >= 0 && cnew < kClasses) {
-            atomicAdd(cnt + kj * kCountStride + cold, -1);
-            atomicAdd(cnt + kj * kCountStride + cnew, 1);
+        cold[dir] = 7 * block_bit<D>(st, jx, jy, jz) + neighbour_up<D>(Ld, w, st, jx, jy, jz);
+        const int ndx = wrap_coord(w.dx + (jx < 0 ? -1 : jx >= D ? 1 : 0), nd);
+        const int ndy = wrap_coord(w.dy + (jy < 0 ? -1 : jy >= D ? 1 : 0), nd);
+        const int ndz = wrap_coord(w.dz + (jz < 0 ? -1 : jz >= D ? 1 : 0), nd);
+        kj[dir] = domain_index(nd, ndx, ndy, ndz); // w.k when the neighbour is inside
+    }
+    bool ok = true;
+    atomicAdd(cnt + w.k * kCountStride + w.cls, -1);
+    atomicAdd(cnt + w.k * kCountStride + 7 * (1 - sig) + us, 1);
+#pragma unroll
+    for (int dir = 0; dir < 6; ++dir) {
+        const int cn = cold[dir] + delta;
+        if (cold[dir] >= 0 && cold[dir] < kClasses && cn >= 0 && cn < kClasses) {
+            atomicAdd(cnt + kj[dir] * kCountStride + cold[dir], -1);
+            atomicAdd(cnt + kj[dir] * kCountStride + cn, 1);
         } else {
             ok = false;
         }
     }
     if (!ok) raise_error(P.err, SPKMC_EINTERNAL);
-    xor_u16(Ld.rows + w.k * (D * D) + y + D * z, 1u << x);
-    uint16_t *mir = Ld.mirrors + w.k * (4 * D);
-    if (x == 0) xor_u16(mir + 0 * D + z, 1u << y);
-    if (x == D - 1) xor_u16(mir + 1 * D + z, 1u << y);
-    if (y == 0) xor_u16(mir + 2 * D + z, 1u << x);
-    if (y == D - 1) xor_u16(mir + 3 * D + z, 1u << x);
+    // the flip, and the ghost faces of the neighbours that touch the site
+    xor_u16(block_of<D>(Ld, w.k) + y + D * z, 1u << x);
+    if (x == 0) xor_u16(block_of<D>(Ld, kj[0]) + D * D + 1 * D + z, 1u << y);
+    if (x == D - 1) xor_u16(block_of<D>(Ld, kj[1]) + D * D + 0 * D + z, 1u << y);
+    if (y == 0) xor_u16(block_of<D>(Ld, kj[2]) + D * D + 3 * D + z, 1u << x);
+    if (y == D - 1) xor_u16(block_of<D>(Ld, kj[3]) + D * D + 2 * D + z, 1u << x);
+    if (z == 0) xor_u16(block_of<D>(Ld, kj[4]) + D * D + 5 * D + y, 1u << x);
+    if (z == D - 1) xor_u16(block_of<D>(Ld, kj[5]) + D * D + 4 * D + y, 1u << x);
     const long long t = S.seg_t0[w.ls] + g;
     if (Ld.log) {
         const long long idx = (t - Ld.log_t0) * Ld.Kact + w.a;
@@ -766,6 +719,9 @@ __device__ void phase_b(const LaunchParams &P, CtaShared &S, unsigned char *stag
                     cum[c + 1] = v.y;
                 }
                 const double2 uw = __ldcg(sp + 7);
+                const uint4 n4a = __ldcg(reinterpret_cast<const uint4 *>(sp + 8));
+                const uint4 n4b = __ldcg(reinterpret_cast<const uint4 *>(sp + 9));
+                const uint32_t npk[7] = {n4a.x, n4a.y, n4a.z, n4a.w, n4b.x, n4b.y, n4b.z};
                 const unsigned long long w1 = (unsigned long long)__double_as_longlong(uw.y);
                 // target on the frequency line padded to R_max (steps 3-4):
                 // the first class whose cumulative rate exceeds it, else null.
@@ -794,8 +750,10 @@ __device__ void phase_b(const LaunchParams &P, CtaShared &S, unsigned char *stag
                         }
                     }
                 } else {
-                    const unsigned long long nc =
-                        (unsigned long long)__ldcg(Ld.counts + k * kCountStride + cls);
+                    unsigned long long nc = 0;
+#pragma unroll
+                    for (int c = 0; c < kClasses; ++c)
+                        if (c == cls) nc = (npk[c >> 1] >> (16 * (c & 1))) & 0xFFFFu;
                     const int idx = atomicAdd(&S.nwork, 1);
                     WorkItem wi;
                     wi.k = k;
@@ -810,14 +768,11 @@ __device__ void phase_b(const LaunchParams &P, CtaShared &S, unsigned char *stag
                     wi.dz = (short)dz;
                     wi.d = (short)Ld.d;
                     S.work[idx] = wi;
-                    if (Ld.d >= 8) atomicAdd(&S.bulk_bytes, staged_bytes(Ld.d));
+                    atomicAdd(&S.bulk_bytes, staged_bytes(Ld.d));
                 }
                 if (a == 0) {
                     // Step 5: one global time increment per cycle.
-                    unsigned long long wc[4];
-                    philox4x64_10((unsigned long long)t, 0ULL, 2ULL, 0ULL, Ld.seed, 0ULL, wc);
-                    const double xi = __ull2double_rn(2ULL * (wc[0] >> 12) + 1ULL) * 0x1p-53;
-                    const double dt = __ddiv_rn(-log(xi), Rmax);
+                    const double dt = __ddiv_rn(S.seg_nlogxi[ls], Rmax);
                     LatticeState &st = P.state[slot];
                     st.clock = __dadd_rn(st.clock, dt);
                     st.rmax[(t + 2) % 3] = 0ULL;
@@ -837,26 +792,18 @@ __device__ void phase_b(const LaunchParams &P, CtaShared &S, unsigned char *stag
         const int nwork = S.nwork;
         const int bulk = S.bulk_bytes;
         if (nwork == 0) continue;
-        // stage every selected domain of the round at once
-        if (bulk > 0 && threadIdx.x == 0) mbar_expect_tx(&S.mbar, (unsigned)bulk);
+        // stage the blocks of every domain that flips in this round at once
+        if (threadIdx.x == 0) mbar_expect_tx(&S.mbar, (unsigned)bulk);
         __syncthreads();
         if (threadIdx.x < nwork) {
-            const WorkItem w = S.work[threadIdx.x];
-            if (w.d >= 8) asm volatile("fence.proxy.async.global;" ::: "memory");
+            const WorkItem &w = S.work[threadIdx.x];
             const LatticeDesc &Ld = P.desc[S.seg_slot[w.ls]];
-            switch (w.d) {
-            case 2: stage_domain<2>(Ld, w, stage, &S.mbar); break;
-            case 4: stage_domain<4>(Ld, w, stage, &S.mbar); break;
-            case 8: stage_domain<8>(Ld, w, stage, &S.mbar); break;
-            default: stage_domain<16>(Ld, w, stage, &S.mbar); break;
-            }
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            bulk_copy_g2s(stage + w.off, Ld.cells + w.k * block_words(w.d), staged_bytes(w.d), &S.mbar);
         }
-        if (bulk > 0) {
-            if (!mbar_wait_bounded(P, &S.mbar, mbar_phase)) {
-                S.ok = 0; // copies never landed: leave without touching the area
-            }
-            mbar_phase ^= 1u;
-        }
+        if (threadIdx.x == 0 && !mbar_wait_bounded(P, &S.mbar, mbar_phase))
+            S.ok = 0; // copies never landed: leave without touching the area
+        mbar_phase ^= 1u;
         __syncthreads();
         if (!*reinterpret_cast<volatile int *>(&S.ok)) return;
         // rank and pick the site, one warp per domain
@@ -937,6 +884,7 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
         S.seg_fxhi[i] = 0;
         S.seg_dM[i] = 0;
         S.seg_dB[i] = 0;
+        S.seg_nlogxi[i] = 0.0;
     }
     __syncthreads();
     if (ld_volatile_int(P.err) != 0) return;
@@ -980,7 +928,7 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
 }
 
 // ---------------------------------------------------------------------------
-// Set-up and read-out kernels (one thread per row, or one warp per domain)
+// Set-up and read-out kernels
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void init_rows_kernel(LatticeDesc Ld, int init)
@@ -990,8 +938,8 @@ __global__ void init_rows_kernel(LatticeDesc Ld, int init)
          i += (long long)gridDim.x * blockDim.x) {
         const long long k = i / (D * D);
         const int r = (int)(i % (D * D));
-        const int dx = (int)(k % Ld.nd), dy = (int)((k / Ld.nd) % Ld.nd),
-                  dz = (int)(k / ((long long)Ld.nd * Ld.nd));
+        int dx, dy, dz;
+        domain_coords(Ld, k, dx, dy, dz);
         uint32_t row = (1u << D) - 1u;
         if (init == SPKMC_INIT_HOT) {
             const long long X0 = (long long)dx * D, Y = (long long)dy * D + r % D,
@@ -1002,8 +950,17 @@ __global__ void init_rows_kernel(LatticeDesc Ld, int init)
             const int off = (int)(g0 & 255);
             row = (uint32_t)((w[off >> 6] >> (off & 63)) & ((1ULL << D) - 1ULL));
         }
-        Ld.rows[i] = (uint16_t)row;
+        block_of<D>(Ld, k)[r] = (uint16_t)row;
     }
+}
+
+template <int D>
+__device__ __forceinline__ long long first_site_of_row(const LatticeDesc &Ld, long long k, int r)
+{
+    int dx, dy, dz;
+    domain_coords(Ld, k, dx, dy, dz);
+    return (long long)dx * D +
+           (long long)Ld.L * ((long long)dy * D + r % D + (long long)Ld.L * ((long long)dz * D + r / D));
 }
 
 template <int D>
@@ -1014,14 +971,10 @@ __global__ void pack_rows_kernel(LatticeDesc Ld, const int8_t *s8)
          i += (long long)gridDim.x * blockDim.x) {
         const long long k = i / (D * D);
         const int r = (int)(i % (D * D));
-        const int dx = (int)(k % Ld.nd), dy = (int)((k / Ld.nd) % Ld.nd),
-                  dz = (int)(k / ((long long)Ld.nd * Ld.nd));
-        const long long g0 = (long long)dx * D +
-                             (long long)Ld.L * ((long long)dy * D + r % D +
-                                                (long long)Ld.L * ((long long)dz * D + r / D));
+        const long long g0 = first_site_of_row<D>(Ld, k, r);
         uint32_t row = 0;
         for (int x = 0; x < D; ++x) row |= (s8[g0 + x] > 0 ? 1u : 0u) << x;
-        Ld.rows[i] = (uint16_t)row;
+        block_of<D>(Ld, k)[r] = (uint16_t)row;
     }
 }
 
@@ -1033,57 +986,66 @@ __global__ void unpack_rows_kernel(LatticeDesc Ld, int8_t *s8)
          i += (long long)gridDim.x * blockDim.x) {
         const long long k = i / (D * D);
         const int r = (int)(i % (D * D));
-        const int dx = (int)(k % Ld.nd), dy = (int)((k / Ld.nd) % Ld.nd),
-                  dz = (int)(k / ((long long)Ld.nd * Ld.nd));
-        const long long g0 = (long long)dx * D +
-                             (long long)Ld.L * ((long long)dy * D + r % D +
-                                                (long long)Ld.L * ((long long)dz * D + r / D));
-        const uint32_t row = Ld.rows[i];
+        const long long g0 = first_site_of_row<D>(Ld, k, r);
+        const uint32_t row = block_of<D>(Ld, k)[r];
         for (int x = 0; x < D; ++x) s8[g0 + x] = ((row >> x) & 1u) ? int8_t(1) : int8_t(-1);
     }
 }
 
+// The ghost word (face f, index i) of domain k as the neighbours' rows define it.
 template <int D>
-__global__ void build_mirrors_kernel(LatticeDesc Ld)
+__device__ __forceinline__ uint32_t ghost_word(const LatticeDesc &Ld, long long k, int f, int i)
 {
-    const long long n = Ld.K * D;
+    int dx, dy, dz;
+    domain_coords(Ld, k, dx, dy, dz);
+    const int nd = Ld.nd;
+    uint32_t w = 0;
+    if (f < 2) { // x faces: bit y of index z
+        const long long kn = domain_index(nd, wrap_coord(dx + (f == 0 ? -1 : 1), nd), dy, dz);
+        const int xb = f == 0 ? D - 1 : 0;
+        const uint16_t *rows = block_of<D>(Ld, kn);
+        for (int y = 0; y < D; ++y) w |= (((uint32_t)rows[y + D * i] >> xb) & 1u) << y;
+    } else if (f < 4) { // y faces: row (y = d-1 or 0, z = i) of the y neighbour
+        const long long kn = domain_index(nd, dx, wrap_coord(dy + (f == 2 ? -1 : 1), nd), dz);
+        w = block_of<D>(Ld, kn)[(f == 2 ? D - 1 : 0) + D * i];
+    } else { // z faces: row (y = i, z = d-1 or 0) of the z neighbour
+        const long long kn = domain_index(nd, dx, dy, wrap_coord(dz + (f == 4 ? -1 : 1), nd));
+        w = block_of<D>(Ld, kn)[i + D * (f == 4 ? D - 1 : 0)];
+    }
+    return w;
+}
+
+template <int D>
+__global__ void ghosts_kernel(LatticeDesc Ld, int mode, unsigned long long *mismatch)
+{
+    const long long n = Ld.K * 6 * D;
+    unsigned long long bad = 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const long long k = i / D;
-        const int z = (int)(i % D);
-        const uint16_t *rows = Ld.rows + k * (D * D) + D * z;
-        uint32_t x0 = 0, x1 = 0;
-        for (int y = 0; y < D; ++y) {
-            const uint32_t row = rows[y];
-            x0 |= (row & 1u) << y;
-            x1 |= ((row >> (D - 1)) & 1u) << y;
-        }
-        uint16_t *mir = Ld.mirrors + k * (4 * D);
-        mir[0 * D + z] = (uint16_t)x0;
-        mir[1 * D + z] = (uint16_t)x1;
-        mir[2 * D + z] = rows[0];
-        mir[3 * D + z] = rows[D - 1];
+        const long long k = i / (6 * D);
+        const int f = (int)((i / D) % 6), idx = (int)(i % D);
+        const uint32_t w = ghost_word<D>(Ld, k, f, idx);
+        uint16_t *slot = block_of<D>(Ld, k) + D * D + f * D + idx;
+        if (mode == 0) *slot = (uint16_t)w;
+        else bad += (*slot != (uint16_t)w);
     }
+    if (mode == 1 && bad) atomicAdd(mismatch, bad);
 }
 
 template <int D>
 __global__ void __launch_bounds__(256) count_classes_kernel(LatticeDesc Ld, int mode,
                                                             unsigned long long *mismatch)
 {
-    __shared__ uint32_t Pbuf[8][kPadWords];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t *Pw = Pbuf[warp];
     constexpr uint32_t V = ((1u << D) - 1u) << 1;
     unsigned long long bad = 0;
     for (long long k = blockIdx.x * 8LL + warp; k < Ld.K; k += gridDim.x * 8LL) {
-        const int dx = (int)(k % Ld.nd), dy = (int)((k / Ld.nd) % Ld.nd),
-                  dz = (int)(k / ((long long)Ld.nd * Ld.nd));
-        stage_padded<D>(Ld, k, dx, dy, dz, Pw, lane);
+        const uint16_t *blk = block_of<D>(Ld, k);
         int cnt[kClasses];
 #pragma unroll
         for (int c = 0; c < kClasses; ++c) cnt[c] = 0;
         for (int r = lane; r < D * D; r += 32) {
-            const RowPlanes p = classify_row<D>(Pw, r % D, r / D);
+            const RowPlanes p = classify_row<D>(blk, r % D, r / D);
 #pragma unroll
             for (int u = 0; u < 7; ++u) {
                 uint32_t e = V;
@@ -1105,38 +1067,35 @@ __global__ void __launch_bounds__(256) count_classes_kernel(LatticeDesc Ld, int 
         }
         if (mode == 0 && lane >= kClasses && lane < kCountStride) Ld.counts[k * kCountStride + lane] = 0;
         if (__any_sync(kFull, differs) && lane == 0) ++bad;
-        __syncwarp();
     }
     if (mode == 1 && lane == 0 && bad) atomicAdd(mismatch, bad);
 }
 
+// M and B of Eq. 1 / Eq. 4, one warp per domain: +x bonds inside each row
+// and against the +x ghost, +y and +z bonds against the next row or the
+// ghost faces.
 template <int D>
 __global__ void __launch_bounds__(256) observables_kernel(LatticeDesc Ld, long long *MB)
 {
-    __shared__ uint32_t Pbuf[8][kPadWords];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t *Pw = Pbuf[warp];
     constexpr uint32_t V = ((1u << D) - 1u) << 1;
     long long M = 0, B = 0;
     for (long long k = blockIdx.x * 8LL + warp; k < Ld.K; k += gridDim.x * 8LL) {
-        const int dx = (int)(k % Ld.nd), dy = (int)((k / Ld.nd) % Ld.nd),
-                  dz = (int)(k / ((long long)Ld.nd * Ld.nd));
-        stage_padded<D>(Ld, k, dx, dy, dz, Pw, lane);
+        const uint16_t *blk = block_of<D>(Ld, k);
+        const uint16_t *gh = blk + D * D;
         int m = 0, b = 0;
         for (int r = lane; r < D * D; r += 32) {
             const int y = r % D, z = r / D;
-            const int base = (y + 1) + (D + 2) * (z + 1);
-            const uint32_t s = Pw[base];
+            const uint32_t s = ((uint32_t)blk[r] << 1) | ((((uint32_t)gh[1 * D + z] >> y) & 1u) << (D + 1));
+            const uint32_t yp = (uint32_t)(y < D - 1 ? blk[r + 1] : gh[3 * D + z]) << 1;
+            const uint32_t zp = (uint32_t)(z < D - 1 ? blk[r + D] : gh[5 * D + y]) << 1;
             m += 2 * __popc(s & V) - D;
             b += 2 * __popc(~(s ^ (s >> 1)) & V) - D;
-            b += 2 * __popc(~(s ^ Pw[base + 1]) & V) - D;
-            b += 2 * __popc(~(s ^ Pw[base + (D + 2)]) & V) - D;
+            b += 2 * __popc(~(s ^ yp) & V) - D;
+            b += 2 * __popc(~(s ^ zp) & V) - D;
         }
-        m = __reduce_add_sync(kFull, m);
-        b = __reduce_add_sync(kFull, b);
-        M += m;
-        B += b;
-        __syncwarp();
+        M += __reduce_add_sync(kFull, m);
+        B += __reduce_add_sync(kFull, b);
     }
     if (lane == 0 && (M || B)) {
         atomicAdd(reinterpret_cast<unsigned long long *>(MB), (unsigned long long)M);
@@ -1233,10 +1192,10 @@ int launch_unpack_rows(const LatticeDesc &d, int8_t *dev_spins, void *stream)
     return to_status(cudaGetLastError());
 }
 
-int launch_build_mirrors(const LatticeDesc &d, void *stream)
+int launch_ghosts(const LatticeDesc &d, int mode, unsigned long long *mismatch, void *stream)
 {
-    const int grid = simple_grid(d.K * d.d, 256);
-    SPKMC_DISPATCH_D(d.d, build_mirrors_kernel, grid, 256, (cudaStream_t)stream, d);
+    const int grid = simple_grid(d.K * 6 * d.d, 256);
+    SPKMC_DISPATCH_D(d.d, ghosts_kernel, grid, 256, (cudaStream_t)stream, d, mode, mismatch);
     return to_status(cudaGetLastError());
 }
 

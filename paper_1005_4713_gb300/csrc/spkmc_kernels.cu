@@ -276,6 +276,8 @@ struct CtaShared {
     unsigned long long seg_dM[kMaxSegPerCta];
     unsigned long long seg_dB[kMaxSegPerCta];
     double seg_nlogxi[kMaxSegPerCta]; // -ln(xi) of the running cycle
+    double seg_rnow[kMaxSegPerCta];   // R_max of the running cycle
+    int seg_tick[kMaxSegPerCta];      // the clock of this lattice moves in this round
     int seg_slot[kMaxSegPerCta];
     unsigned long long mbar;
     int nsegc;
@@ -455,13 +457,6 @@ __device__ void phase_a(const LaunchParams &P, CtaShared &S, long long g, long l
                 __stcg(np + 1, make_uint4((uint32_t)n[8] | ((uint32_t)n[9] << 16), (uint32_t)n[10] | ((uint32_t)n[11] << 16),
                                           (uint32_t)n[12] | ((uint32_t)n[13] << 16), 0u));
                 rbits = (unsigned long long)__double_as_longlong(acc);
-                if (a == 0) {
-                    // -ln(xi) of this cycle's time step (step 5), drawn ahead
-                    unsigned long long wc[4];
-                    philox4x64_10((unsigned long long)t, 0ULL, 2ULL, 0ULL, Ld.seed, 0ULL, wc);
-                    const double xi = __ull2double_rn(2ULL * (wc[0] >> 12) + 1ULL) * 0x1p-53;
-                    S.seg_nlogxi[ls] = -log(xi);
-                }
             } else {
                 ls = -1;
             }
@@ -474,102 +469,134 @@ __device__ void phase_a(const LaunchParams &P, CtaShared &S, long long g, long l
             atomicMax(&S.seg_rmax[ls], rbits);
         }
     }
+    if (threadIdx.x == kThreads - 1) {
+        // -ln(xi) of this cycle's time step (step 5) for the lattices whose
+        // first active domain this CTA owns, by the last thread (usually idle)
+        for (int i = 0; i < S.nsegc; ++i) {
+            if (S.seg_base[i] < lo || g >= S.seg_part[i]) continue;
+            const LatticeDesc &Ld = P.desc[S.seg_slot[i]];
+            unsigned long long wc[4];
+            philox4x64_10((unsigned long long)(S.seg_t0[i] + g), 0ULL, 2ULL, 0ULL, Ld.seed, 0ULL, wc);
+            const double xi = __ull2double_rn(2ULL * (wc[0] >> 12) + 1ULL) * 0x1p-53;
+            S.seg_nlogxi[i] = -log(xi);
+        }
+    }
 }
 
 // Rank the sites of class w.cls in ascending local index and return the
-// w.j-th (warp-cooperative, from the staged block); -1 if the class is short.
+// w.j-th, cooperatively in the aligned group of 8 lanes (octet) that holds
+// `lane`; -1 if the class has fewer sites.  A warp works on 4 domains at once.
 template <int D>
 __device__ int select_site(const WorkItem &w, const unsigned char *stage, int lane)
 {
     const uint16_t *st = reinterpret_cast<const uint16_t *>(stage + w.off);
+    const int o = lane & 7;
+    const unsigned grp = 0xFFu << (lane & 24);
     const int sig = w.cls >= 7, us = w.cls - 7 * sig;
     if constexpr (D == 16) {
-        // lane l holds rows r0..r0+7 (z = l/2, y = 8(l&1)..+7) as four pairs of
-        // 16-bit rows per 32-bit word: bit b of pair p is site 16 (r0+2p) + b
-        const int z = lane >> 1, y0 = (lane & 1) * 8, r0 = lane * 8;
+        // octet lane o holds the planes z = 2o and 2o+1 (rows 32o .. 32o+31) as
+        // 16 words of two 16-site rows: bit b of word q is site 16 (32o + 2q) + b
         const uint16_t *g = st + 256;
-        const uint4 cur4 = *reinterpret_cast<const uint4 *>(st + r0);
-        const uint4 zm4 = *reinterpret_cast<const uint4 *>(z > 0 ? st + r0 - 16 : g + 4 * 16 + y0);
-        const uint4 zp4 = *reinterpret_cast<const uint4 *>(z < 15 ? st + r0 + 16 : g + 5 * 16 + y0);
-        const uint32_t cur[4] = {cur4.x, cur4.y, cur4.z, cur4.w};
-        const uint32_t zmv[4] = {zm4.x, zm4.y, zm4.z, zm4.w};
-        const uint32_t zpv[4] = {zp4.x, zp4.y, zp4.z, zp4.w};
-        const uint32_t below = (uint32_t)(y0 == 0 ? g[2 * 16 + z] : st[r0 - 1]); // row y0-1
-        const uint32_t above = (uint32_t)(y0 == 8 ? g[3 * 16 + z] : st[r0 + 8]); // row y0+8
-        const uint32_t hxm = g[0 * 16 + z], hxp = g[1 * 16 + z];
-        uint32_t m[4];
+        const int z0 = 2 * o;
+        uint32_t cur[16], zm[8], zp[8];
+        {
+            const uint4 *p = reinterpret_cast<const uint4 *>(st + 32 * o);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint4 v = p[i];
+                cur[4 * i] = v.x;
+                cur[4 * i + 1] = v.y;
+                cur[4 * i + 2] = v.z;
+                cur[4 * i + 3] = v.w;
+            }
+            const uint4 *pm = reinterpret_cast<const uint4 *>(z0 > 0 ? st + 16 * (z0 - 1) : g + 4 * 16);
+            const uint4 *pp = reinterpret_cast<const uint4 *>(z0 + 1 < 15 ? st + 16 * (z0 + 2) : g + 5 * 16);
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const uint4 a = pm[i], b = pp[i];
+                zm[4 * i] = a.x; zm[4 * i + 1] = a.y; zm[4 * i + 2] = a.z; zm[4 * i + 3] = a.w;
+                zp[4 * i] = b.x; zp[4 * i + 1] = b.y; zp[4 * i + 2] = b.z; zp[4 * i + 3] = b.w;
+            }
+        }
+        uint32_t m[16];
         int tot = 0;
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const int y = y0 + 2 * p;
-            const uint32_t s = cur[p];
-            const uint32_t xm = ((s << 1) & 0xFFFEFFFEu) | ((hxm >> y) & 1u) | (((hxm >> (y + 1)) & 1u) << 16);
-            const uint32_t xp = ((s >> 1) & 0x7FFF7FFFu) | (((hxp >> y) & 1u) << 15) |
-                                (((hxp >> (y + 1)) & 1u) << 31);
-            const uint32_t ym = (s << 16) | (p > 0 ? (cur[p - 1] >> 16) : below);
-            const uint32_t yp = (s >> 16) | ((p < 3 ? (cur[p + 1] & 0xFFFFu) : above) << 16);
-            const uint32_t e = zmv[p], f = zpv[p];
-            const uint32_t s1 = xm ^ xp ^ ym, c1 = (xm & xp) | (ym & (xm ^ xp));
-            const uint32_t s2 = yp ^ e ^ f, c2 = (yp & e) | (f & (yp ^ e));
-            const uint32_t k2 = s1 & s2;
-            const uint32_t u0 = s1 ^ s2, u1 = c1 ^ c2 ^ k2, u2 = (c1 & c2) | (k2 & (c1 ^ c2));
-            uint32_t mm = sig ? s : ~s;
-            mm &= (us & 1) ? u0 : ~u0;
-            mm &= (us & 2) ? u1 : ~u1;
-            mm &= (us & 4) ? u2 : ~u2;
-            m[p] = mm;
-            tot += __popc(mm);
+        for (int pl = 0; pl < 2; ++pl) {
+            const int z = z0 + pl;
+            const uint32_t below = g[2 * 16 + z], above = g[3 * 16 + z];
+            const uint32_t hxm = g[0 * 16 + z], hxp = g[1 * 16 + z];
+#pragma unroll
+            for (int p = 0; p < 8; ++p) {
+                const int y = 2 * p;
+                const uint32_t s = cur[8 * pl + p];
+                const uint32_t xm = ((s << 1) & 0xFFFEFFFEu) | ((hxm >> y) & 1u) | (((hxm >> (y + 1)) & 1u) << 16);
+                const uint32_t xp = ((s >> 1) & 0x7FFF7FFFu) | (((hxp >> y) & 1u) << 15) |
+                                    (((hxp >> (y + 1)) & 1u) << 31);
+                const uint32_t ym = (s << 16) | (p > 0 ? (cur[8 * pl + p - 1] >> 16) : below);
+                const uint32_t yp = (s >> 16) | ((p < 7 ? (cur[8 * pl + p + 1] & 0xFFFFu) : above) << 16);
+                const uint32_t e = pl == 0 ? zm[p] : cur[p];
+                const uint32_t f = pl == 0 ? cur[8 + p] : zp[p];
+                const uint32_t s1 = xm ^ xp ^ ym, c1 = (xm & xp) | (ym & (xm ^ xp));
+                const uint32_t s2 = yp ^ e ^ f, c2 = (yp & e) | (f & (yp ^ e));
+                const uint32_t k2 = s1 & s2;
+                const uint32_t u0 = s1 ^ s2, u1 = c1 ^ c2 ^ k2, u2 = (c1 & c2) | (k2 & (c1 ^ c2));
+                uint32_t mm = sig ? s : ~s;
+                mm &= (us & 1) ? u0 : ~u0;
+                mm &= (us & 2) ? u1 : ~u1;
+                mm &= (us & 4) ? u2 : ~u2;
+                m[8 * pl + p] = mm;
+                tot += __popc(mm);
+            }
         }
         int incl = tot;
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int v = __shfl_up_sync(kFull, incl, off);
-            if (lane >= off) incl += v;
+        for (int off = 1; off < 8; off <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, off, 8);
+            if (o >= off) incl += v;
         }
         const int excl = incl - tot;
         const bool mine = w.j >= excl && w.j < incl;
-        const unsigned who = __ballot_sync(kFull, mine);
-        if (who == 0) return -1;
+        const unsigned who = __ballot_sync(kFull, mine) & grp;
         int site = 0;
         if (mine) {
             int jj = w.j - excl;
 #pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                const int pc = __popc(m[p]);
+            for (int q = 0; q < 16; ++q) {
+                const int pc = __popc(m[q]);
                 if (jj >= 0 && jj < pc) {
-                    uint32_t bits = m[p];
-                    for (int q = 0; q < jj; ++q) bits &= bits - 1;
-                    site = 16 * (r0 + 2 * p) + (__ffs(bits) - 1);
+                    uint32_t bits = m[q];
+                    for (int r = 0; r < jj; ++r) bits &= bits - 1;
+                    site = 16 * (32 * o + 2 * q) + (__ffs(bits) - 1);
                 }
                 jj -= pc;
             }
         }
-        return __shfl_sync(kFull, site, __ffs(who) - 1);
+        site = __shfl_sync(kFull, site, who ? __ffs(who) - 1 : lane);
+        return who ? site : -1;
     } else {
         constexpr int kRows = D * D;
-        constexpr int kRpl = kRows >= 32 ? kRows / 32 : 1; // rows per lane, contiguous
-        const bool on = (kRows >= 32) || (lane < kRows);
+        constexpr int kRpl = kRows >= 8 ? kRows / 8 : 1; // rows per octet lane, contiguous
+        const bool on = (kRows >= 8) || (o < kRows);
         uint32_t m[kRpl];
         int tot = 0;
 #pragma unroll
         for (int i = 0; i < kRpl; ++i) {
             m[i] = 0;
             if (on) {
-                const int r = lane * kRpl + i;
+                const int r = o * kRpl + i;
                 m[i] = class_mask<D>(classify_row<D>(st, r % D, r / D), w.cls);
                 tot += __popc(m[i]);
             }
         }
         int incl = tot;
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int v = __shfl_up_sync(kFull, incl, off);
-            if (lane >= off) incl += v;
+        for (int off = 1; off < 8; off <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, off, 8);
+            if (o >= off) incl += v;
         }
         const int excl = incl - tot;
         const bool mine = w.j >= excl && w.j < incl;
-        const unsigned who = __ballot_sync(kFull, mine);
-        if (who == 0) return -1;
+        const unsigned who = __ballot_sync(kFull, mine) & grp;
         int site = 0;
         if (mine) {
             int jj = w.j - excl;
@@ -578,46 +605,33 @@ __device__ int select_site(const WorkItem &w, const unsigned char *stage, int la
                 const int pc = __popc(m[i]);
                 if (jj >= 0 && jj < pc) {
                     uint32_t bits = m[i];
-                    for (int q = 0; q < jj; ++q) bits &= bits - 1;
-                    site = D * (lane * kRpl + i) + (__ffs(bits) - 1) - 1;
+                    for (int r = 0; r < jj; ++r) bits &= bits - 1;
+                    site = D * (o * kRpl + i) + (__ffs(bits) - 1) - 1;
                 }
                 jj -= pc;
             }
         }
-        return __shfl_sync(kFull, site, __ffs(who) - 1);
+        site = __shfl_sync(kFull, site, who ? __ffs(who) - 1 : lane);
+        return who ? site : -1;
     }
 }
 
-// Up count of the neighbour (jx, jy, jz) of the flipped site, from the
-// pre-flip state: the staged block holds the one-site halo, global memory the
-// rest (the second layer and the edges of a neighbour face).  The global
-// loads of the six directions are independent of each other.
-template <int D>
-__device__ __forceinline__ int neighbour_up(const LatticeDesc &Ld, const WorkItem &w, const uint16_t *st,
-                                            int jx, int jy, int jz)
+// Global u16 load that is issued only when `pred` holds (no branch).
+__device__ __forceinline__ uint32_t ldg_u16_if(const uint16_t *p, bool pred)
 {
-    int u = 0;
-#pragma unroll
-    for (int n = 0; n < 6; ++n) {
-        const int nx = jx + (n == 0 ? -1 : n == 1 ? 1 : 0);
-        const int ny = jy + (n == 2 ? -1 : n == 3 ? 1 : 0);
-        const int nz = jz + (n == 4 ? -1 : n == 5 ? 1 : 0);
-        const int outs = (nx < 0 || nx >= D) + (ny < 0 || ny >= D) + (nz < 0 || nz >= D);
-        const bool near = nx >= -1 && nx <= D && ny >= -1 && ny <= D && nz >= -1 && nz <= D && outs <= 1;
-        if (near) {
-            u += block_bit<D>(st, nx, ny, nz);
-        } else {
-            int bit;
-            const uint16_t *row = row_of_site<D>(Ld, w.dx * D + nx, w.dy * D + ny, w.dz * D + nz, bit);
-            u += (int)((ld_u16(row) >> bit) & 1u);
-        }
-    }
-    return u;
+    unsigned short v = 0;
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.global.cg.u16 %0, [%1];\n\t}"
+        : "+h"(v)
+        : "l"(p), "r"((unsigned)pred));
+    return v;
 }
 
 // Flip the chosen site (step 6), move the class counts of the site and of its
-// 6 neighbours, and refresh the ghost faces of the neighbour domains that see
-// the site (one thread per domain).
+// 6 neighbours (read from the pre-flip state) and refresh the ghost faces of
+// the neighbour domains that see the site; one thread per domain.  For a
+// neighbour j outside the domain, the site two steps out and the neighbours
+// of j beyond the staged ghost face come from global memory; those loads are
+// all issued before any of them is used.
 template <int D>
 __device__ void apply_flip(const LaunchParams &P, CtaShared &S, const WorkItem &w,
                            const unsigned char *stage, long long g)
@@ -625,24 +639,74 @@ __device__ void apply_flip(const LaunchParams &P, CtaShared &S, const WorkItem &
     const LatticeDesc &Ld = P.desc[S.seg_slot[w.ls]];
     const uint16_t *st = reinterpret_cast<const uint16_t *>(stage + w.off);
     const int l = w.site;
-    const int x = l % D, y = (l / D) % D, z = l / (D * D);
+    const int s3[3] = {l % D, (l / D) % D, l / (D * D)};
     const int sig = w.cls >= 7, us = w.cls - 7 * sig;
     const int delta = sig ? -1 : 1; // change of the neighbours' up count
-    int32_t *cnt = Ld.counts;
     const int nd = Ld.nd;
+    const int base3[3] = {w.dx * D, w.dy * D, w.dz * D};
+    uint32_t gv[6][5];
+    int gbit[6][5];
+#pragma unroll
+    for (int dir = 0; dir < 6; ++dir) {
+        const int ax = dir >> 1, step = (dir & 1) ? 1 : -1;
+        int j3[3] = {s3[0], s3[1], s3[2]};
+        j3[ax] += step;
+        const bool out = j3[ax] < 0 || j3[ax] >= D;
+#pragma unroll
+        for (int n = 0; n < 5; ++n) {
+            int n3[3] = {j3[0], j3[1], j3[2]};
+            bool need = out;
+            if (n == 0) {
+                n3[ax] += step; // two steps out
+            } else {
+                const int b = (ax + 1 + ((n - 1) >> 1)) % 3;
+                n3[b] += (n & 1) ? -1 : 1;
+                need = out && (n3[b] < 0 || n3[b] >= D);
+            }
+            int bit;
+            const uint16_t *row = row_of_site<D>(Ld, base3[0] + n3[0], base3[1] + n3[1], base3[2] + n3[2], bit);
+            gv[dir][n] = ldg_u16_if(row, need);
+            gbit[dir][n] = bit;
+        }
+    }
     int cold[6];
     long long kj[6];
 #pragma unroll
     for (int dir = 0; dir < 6; ++dir) {
-        const int jx = x + (dir == 0 ? -1 : dir == 1 ? 1 : 0);
-        const int jy = y + (dir == 2 ? -1 : dir == 3 ? 1 : 0);
-        const int jz = z + (dir == 4 ? -1 : dir == 5 ? 1 : 0);
-        cold[dir] = 7 * block_bit<D>(st, jx, jy, jz) + neighbour_up<D>(Ld, w, st, jx, jy, jz);
-        const int ndx = wrap_coord(w.dx + (jx < 0 ? -1 : jx >= D ? 1 : 0), nd);
-        const int ndy = wrap_coord(w.dy + (jy < 0 ? -1 : jy >= D ? 1 : 0), nd);
-        const int ndz = wrap_coord(w.dz + (jz < 0 ? -1 : jz >= D ? 1 : 0), nd);
-        kj[dir] = domain_index(nd, ndx, ndy, ndz); // w.k when the neighbour is inside
+        const int ax = dir >> 1, step = (dir & 1) ? 1 : -1;
+        int j3[3] = {s3[0], s3[1], s3[2]};
+        j3[ax] += step;
+        const bool out = j3[ax] < 0 || j3[ax] >= D;
+        int u = 0;
+        if (!out) {
+#pragma unroll
+            for (int n = 0; n < 6; ++n) {
+                int n3[3] = {j3[0], j3[1], j3[2]};
+                n3[n >> 1] += (n & 1) ? 1 : -1;
+                u += block_bit<D>(st, n3[0], n3[1], n3[2]);
+            }
+        } else {
+            u = block_bit<D>(st, s3[0], s3[1], s3[2]); // the flipped site, before its flip
+#pragma unroll
+            for (int n = 0; n < 5; ++n) {
+                if (n == 0) {
+                    u += (int)((gv[dir][0] >> gbit[dir][0]) & 1u);
+                } else {
+                    int n3[3] = {j3[0], j3[1], j3[2]};
+                    const int b = (ax + 1 + ((n - 1) >> 1)) % 3;
+                    n3[b] += (n & 1) ? -1 : 1;
+                    const bool far = n3[b] < 0 || n3[b] >= D;
+                    u += far ? (int)((gv[dir][n] >> gbit[dir][n]) & 1u) : block_bit<D>(st, n3[0], n3[1], n3[2]);
+                }
+            }
+        }
+        cold[dir] = 7 * block_bit<D>(st, j3[0], j3[1], j3[2]) + u;
+        const int dd[3] = {j3[0] < 0 ? -1 : (j3[0] >= D ? 1 : 0), j3[1] < 0 ? -1 : (j3[1] >= D ? 1 : 0),
+                           j3[2] < 0 ? -1 : (j3[2] >= D ? 1 : 0)};
+        kj[dir] = domain_index(nd, wrap_coord(w.dx + dd[0], nd), wrap_coord(w.dy + dd[1], nd),
+                               wrap_coord(w.dz + dd[2], nd)); // w.k when inside
     }
+    int32_t *cnt = Ld.counts;
     bool ok = true;
     atomicAdd(cnt + w.k * kCountStride + w.cls, -1);
     atomicAdd(cnt + w.k * kCountStride + 7 * (1 - sig) + us, 1);
@@ -657,6 +721,7 @@ __device__ void apply_flip(const LaunchParams &P, CtaShared &S, const WorkItem &
         }
     }
     if (!ok) raise_error(P.err, SPKMC_EINTERNAL);
+    const int x = s3[0], y = s3[1], z = s3[2];
     // the flip, and the ghost faces of the neighbours that touch the site
     xor_u16(block_of<D>(Ld, w.k) + y + D * z, 1u << x);
     if (x == 0) xor_u16(block_of<D>(Ld, kj[0]) + D * D + 1 * D + z, 1u << y);
@@ -699,14 +764,15 @@ __device__ void phase_b(const LaunchParams &P, CtaShared &S, unsigned char *stag
         }
         __syncthreads();
         const long long q = rbase + threadIdx.x;
-        int ls = -1;
-        unsigned long long fxlo = 0, fxhi = 0;
+        int ls = -1, cls = -1, dx = 0, dy = 0, dz = 0, dval = 0;
+        long long a = 0, k = 0;
+        unsigned long long fxlo = 0, fxhi = 0, jrank = 0;
         if (threadIdx.x < R && q < hi) {
             ls = find_segment(S, q);
             if (g < S.seg_part[ls]) {
                 const int slot = S.seg_slot[ls];
                 const LatticeDesc &Ld = P.desc[slot];
-                const long long a = q - S.seg_base[ls];
+                a = q - S.seg_base[ls];
                 const long long t = S.seg_t0[ls] + g;
                 const double Rmax = __longlong_as_double(
                     (long long)__ldcg(&P.state[slot].rmax[t % 3]));
@@ -727,16 +793,14 @@ __device__ void phase_b(const LaunchParams &P, CtaShared &S, unsigned char *stag
                 // the first class whose cumulative rate exceeds it, else null.
                 const double target = __dmul_rn(uw.x, Rmax);
                 const unsigned long long tb = (unsigned long long)__double_as_longlong(target);
-                int cls = -1;
 #pragma unroll
                 for (int c = kClasses - 1; c >= 0; --c)
                     if (tb < (unsigned long long)__double_as_longlong(cum[c])) cls = c;
                 fixed64(__dadd_rn(Rmax, -cum[kClasses - 1]), fxlo, fxhi);
-                int dx, dy, dz;
                 active_domain(Ld.half, a, (int)(t & 7), dx, dy, dz);
-                const long long k = domain_index(Ld.nd, dx, dy, dz);
+                k = domain_index(Ld.nd, dx, dy, dz);
+                dval = Ld.d;
                 if (cls < 0) {
-                    atomicAdd(&S.seg_nnull[ls], 1ULL);
                     if (Ld.log) {
                         const long long idx = (t - Ld.log_t0) * Ld.Kact + a;
                         if (idx >= 0 && idx < Ld.log_cap) {
@@ -754,43 +818,68 @@ __device__ void phase_b(const LaunchParams &P, CtaShared &S, unsigned char *stag
 #pragma unroll
                     for (int c = 0; c < kClasses; ++c)
                         if (c == cls) nc = (npk[c >> 1] >> (16 * (c & 1))) & 0xFFFFu;
-                    const int idx = atomicAdd(&S.nwork, 1);
-                    WorkItem wi;
-                    wi.k = k;
-                    wi.ls = ls;
-                    wi.a = (int)a;
-                    wi.cls = cls;
-                    wi.j = (int)__umul64hi(w1, nc);
-                    wi.off = idx * P.item_bytes;
-                    wi.site = -1;
-                    wi.dx = (short)dx;
-                    wi.dy = (short)dy;
-                    wi.dz = (short)dz;
-                    wi.d = (short)Ld.d;
-                    S.work[idx] = wi;
-                    atomicAdd(&S.bulk_bytes, staged_bytes(Ld.d));
+                    jrank = __umul64hi(w1, nc);
                 }
                 if (a == 0) {
-                    // Step 5: one global time increment per cycle.
-                    const double dt = __ddiv_rn(S.seg_nlogxi[ls], Rmax);
-                    LatticeState &st = P.state[slot];
-                    st.clock = __dadd_rn(st.clock, dt);
-                    st.rmax[(t + 2) % 3] = 0ULL;
+                    S.seg_rnow[ls] = Rmax; // the clock moves once this cycle (step 5)
+                    S.seg_tick[ls] = 1;
+                    P.state[slot].rmax[(t + 2) % 3] = 0ULL;
                 }
             } else {
                 ls = -1;
             }
         }
+        // work list: warp-aggregated slots for the domains that flip
+        const bool flips = ls >= 0 && cls >= 0;
+        const unsigned bal = __ballot_sync(kFull, flips);
+        const int bytes = __reduce_add_sync(kFull, flips ? staged_bytes(dval) : 0);
+        int wbase = 0;
+        if (lane == 0 && bal) {
+            wbase = atomicAdd(&S.nwork, __popc(bal));
+            atomicAdd(&S.bulk_bytes, bytes);
+        }
+        wbase = __shfl_sync(kFull, wbase, 0);
+        if (flips) {
+            const int idx = wbase + __popc(bal & ((1u << lane) - 1u));
+            WorkItem wi;
+            wi.k = k;
+            wi.ls = ls;
+            wi.a = (int)a;
+            wi.cls = cls;
+            wi.j = (int)jrank;
+            wi.off = idx * P.item_bytes;
+            wi.site = -1;
+            wi.dx = (short)dx;
+            wi.dy = (short)dy;
+            wi.dz = (short)dz;
+            wi.d = (short)dval;
+            S.work[idx] = wi;
+        }
         const int ls0 = __shfl_sync(kFull, ls, 0);
+        const bool nul = ls >= 0 && cls < 0;
         if (__all_sync(kFull, ls == ls0) && ls0 >= 0) {
             warp_sum_u128(fxlo, fxhi);
-            if (lane == 0) atomic_add_u128(&S.seg_fxlo[ls0], &S.seg_fxhi[ls0], fxlo, fxhi);
+            const unsigned nn = __popc(__ballot_sync(kFull, nul));
+            if (lane == 0) {
+                atomic_add_u128(&S.seg_fxlo[ls0], &S.seg_fxhi[ls0], fxlo, fxhi);
+                if (nn) atomicAdd(&S.seg_nnull[ls0], (unsigned long long)nn);
+            }
         } else if (ls >= 0) {
             atomic_add_u128(&S.seg_fxlo[ls], &S.seg_fxhi[ls], fxlo, fxhi);
+            if (nul) atomicAdd(&S.seg_nnull[ls], 1ULL);
         }
         __syncthreads();
         const int nwork = S.nwork;
         const int bulk = S.bulk_bytes;
+        if (threadIdx.x == kThreads - 1) {
+            // Step 5: one global time increment per cycle, off the critical path
+            for (int i = 0; i < S.nsegc; ++i) {
+                if (!S.seg_tick[i]) continue;
+                S.seg_tick[i] = 0;
+                LatticeState &st = P.state[S.seg_slot[i]];
+                st.clock = __dadd_rn(st.clock, __ddiv_rn(S.seg_nlogxi[i], S.seg_rnow[i]));
+            }
+        }
         if (nwork == 0) continue;
         // stage the blocks of every domain that flips in this round at once
         if (threadIdx.x == 0) mbar_expect_tx(&S.mbar, (unsigned)bulk);
@@ -806,9 +895,11 @@ __device__ void phase_b(const LaunchParams &P, CtaShared &S, unsigned char *stag
         mbar_phase ^= 1u;
         __syncthreads();
         if (!*reinterpret_cast<volatile int *>(&S.ok)) return;
-        // rank and pick the site, one warp per domain
-        for (int i = warp; i < nwork; i += kWarps) {
-            const WorkItem &w = S.work[i];
+        // rank and pick the site: 4 domains per warp, 8 lanes each
+        for (int base = warp * 4; base < nwork; base += kWarps * 4) {
+            const int i = base + (lane >> 3);
+            const bool valid = i < nwork;
+            const WorkItem &w = S.work[valid ? i : base];
             int site;
             switch (w.d) {
             case 2: site = select_site<2>(w, stage, lane); break;
@@ -816,7 +907,7 @@ __device__ void phase_b(const LaunchParams &P, CtaShared &S, unsigned char *stag
             case 8: site = select_site<8>(w, stage, lane); break;
             default: site = select_site<16>(w, stage, lane); break;
             }
-            if (lane == 0) {
+            if (valid && (lane & 7) == 0) {
                 S.work[i].site = site;
                 if (site < 0) raise_error(P.err, SPKMC_EINTERNAL);
             }
@@ -885,6 +976,8 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
         S.seg_dM[i] = 0;
         S.seg_dB[i] = 0;
         S.seg_nlogxi[i] = 0.0;
+        S.seg_rnow[i] = 0.0;
+        S.seg_tick[i] = 0;
     }
     __syncthreads();
     if (ld_volatile_int(P.err) != 0) return;

@@ -487,7 +487,7 @@ int run(spkmc_batch *b, long long cycles)
         P.skip_cta = b->cfg.debug_skip_arrival_cta;
         int dmax = 2;
         for (const Segment &sg : segs) dmax = std::max(dmax, b->slots[sg.slot].d);
-        P.item_bytes = staged_bytes(dmax);
+        P.item_bytes = stage_slot_bytes(dmax);
         P.round_items = cycle_round_items(dmax);
         int rc = launch_cycles(P, (int)grid, b->stream, grid > 1);
         if (rc) return cuda_fail(cudaGetLastError(), "persistent cycle launch");

@@ -149,9 +149,12 @@ __device__ __forceinline__ void atomic_add_u128(unsigned long long *lo_p, unsign
 __device__ __forceinline__ void active_domain(int half, long long a, int colour, int &dx, int &dy,
                                               int &dz)
 {
-    dx = 2 * (int)(a % half) + (colour & 1);
-    dy = 2 * (int)((a / half) % half) + ((colour >> 1) & 1);
-    dz = 2 * (int)(a / ((long long)half * half)) + ((colour >> 2) & 1);
+    // a < K/8 < 2^28: 32-bit unsigned division is exact and much cheaper
+    const unsigned ua = (unsigned)a, h = (unsigned)half;
+    const unsigned qx = ua / h, qy = qx / h;
+    dx = 2 * (int)(ua - qx * h) + (colour & 1);
+    dy = 2 * (int)(qx - qy * h) + ((colour >> 1) & 1);
+    dz = 2 * (int)qy + ((colour >> 2) & 1);
 }
 
 __device__ __forceinline__ long long domain_index(int nd, int dx, int dy, int dz)
@@ -195,17 +198,17 @@ __device__ __forceinline__ const uint16_t *row_of_site(const LatticeDesc &Ld, in
 template <int D>
 __device__ __forceinline__ int block_bit(const uint16_t *blk, int x, int y, int z)
 {
-    const uint16_t *g = blk + D * D;
-    uint32_t w;
-    int b;
-    if (x < 0) { w = g[0 * D + z]; b = y; }
-    else if (x >= D) { w = g[1 * D + z]; b = y; }
-    else if (y < 0) { w = g[2 * D + z]; b = x; }
-    else if (y >= D) { w = g[3 * D + z]; b = x; }
-    else if (z < 0) { w = g[4 * D + y]; b = x; }
-    else if (z >= D) { w = g[5 * D + y]; b = x; }
-    else { w = blk[y + D * z]; b = x; }
-    return (int)((w >> b) & 1u);
+    // word and bit chosen with selects, not branches (callers run divergent
+    // sites side by side); a coordinate pair outside the halo reads a word of
+    // the block (in bounds) and its value is not used
+    const bool xo = x < 0 || x >= D, yo = y < 0 || y >= D, zo = z < 0 || z >= D;
+    const int cz = z & (D - 1), cy = y & (D - 1);
+    int idx = cy + D * cz;
+    idx = zo ? D * D + (z < 0 ? 4 : 5) * D + cy : idx;
+    idx = yo ? D * D + (y < 0 ? 2 : 3) * D + cz : idx;
+    idx = xo ? D * D + (x < 0 ? 0 : 1) * D + cz : idx;
+    const int b = (xo ? y : x) & 15;
+    return (int)(((uint32_t)blk[idx] >> b) & 1u);
 }
 
 // Bit-sliced count of up neighbours for the D sites of row (y, z) of a
@@ -484,14 +487,17 @@ __device__ void phase_a(const LaunchParams &P, CtaShared &S, long long g, long l
 }
 
 // Rank the sites of class w.cls in ascending local index and return the
-// w.j-th, cooperatively in the aligned group of 8 lanes (octet) that holds
-// `lane`; -1 if the class has fewer sites.  A warp works on 4 domains at once.
+// w.j-th, cooperatively in the group of 8 lanes (octet: lanes q, q+4, ...,
+// q+28 with q = lane % 4) that holds `lane`; -1 if the class has fewer
+// sites.  A warp works on 4 domains at once; with strided octets and staging
+// slots of an odd number of 16-byte units, the 16-byte shared-memory loads
+// of any 8 consecutive lanes hit distinct banks.
 template <int D>
 __device__ int select_site(const WorkItem &w, const unsigned char *stage, int lane)
 {
     const uint16_t *st = reinterpret_cast<const uint16_t *>(stage + w.off);
-    const int o = lane & 7;
-    const unsigned grp = 0xFFu << (lane & 24);
+    const int o = lane >> 2;
+    const unsigned grp = 0x11111111u << (lane & 3);
     const int sig = w.cls >= 7, us = w.cls - 7 * sig;
     if constexpr (D == 16) {
         // octet lane o holds the planes z = 2o and 2o+1 (rows 32o .. 32o+31) as
@@ -551,7 +557,7 @@ __device__ int select_site(const WorkItem &w, const unsigned char *stage, int la
         int incl = tot;
 #pragma unroll
         for (int off = 1; off < 8; off <<= 1) {
-            const int v = __shfl_up_sync(kFull, incl, off, 8);
+            const int v = __shfl_up_sync(kFull, incl, 4 * off);
             if (o >= off) incl += v;
         }
         const int excl = incl - tot;
@@ -591,7 +597,7 @@ __device__ int select_site(const WorkItem &w, const unsigned char *stage, int la
         int incl = tot;
 #pragma unroll
         for (int off = 1; off < 8; off <<= 1) {
-            const int v = __shfl_up_sync(kFull, incl, off, 8);
+            const int v = __shfl_up_sync(kFull, incl, 4 * off);
             if (o >= off) incl += v;
         }
         const int excl = incl - tot;
@@ -671,36 +677,35 @@ __device__ void apply_flip(const LaunchParams &P, CtaShared &S, const WorkItem &
     }
     int cold[6];
     long long kj[6];
+    const int sbit = block_bit<D>(st, s3[0], s3[1], s3[2]); // the flipped site, before its flip
 #pragma unroll
     for (int dir = 0; dir < 6; ++dir) {
         const int ax = dir >> 1, step = (dir & 1) ? 1 : -1;
         int j3[3] = {s3[0], s3[1], s3[2]};
         j3[ax] += step;
         const bool out = j3[ax] < 0 || j3[ax] >= D;
-        int u = 0;
-        if (!out) {
+        // up count of j if it lies inside the domain: all six from the block
+        int u_in = 0;
 #pragma unroll
-            for (int n = 0; n < 6; ++n) {
-                int n3[3] = {j3[0], j3[1], j3[2]};
-                n3[n >> 1] += (n & 1) ? 1 : -1;
-                u += block_bit<D>(st, n3[0], n3[1], n3[2]);
-            }
-        } else {
-            u = block_bit<D>(st, s3[0], s3[1], s3[2]); // the flipped site, before its flip
-#pragma unroll
-            for (int n = 0; n < 5; ++n) {
-                if (n == 0) {
-                    u += (int)((gv[dir][0] >> gbit[dir][0]) & 1u);
-                } else {
-                    int n3[3] = {j3[0], j3[1], j3[2]};
-                    const int b = (ax + 1 + ((n - 1) >> 1)) % 3;
-                    n3[b] += (n & 1) ? -1 : 1;
-                    const bool far = n3[b] < 0 || n3[b] >= D;
-                    u += far ? (int)((gv[dir][n] >> gbit[dir][n]) & 1u) : block_bit<D>(st, n3[0], n3[1], n3[2]);
-                }
-            }
+        for (int n = 0; n < 6; ++n) {
+            int n3[3] = {j3[0], j3[1], j3[2]};
+            n3[n >> 1] += (n & 1) ? 1 : -1;
+            u_in += block_bit<D>(st, n3[0], n3[1], n3[2]);
         }
-        cold[dir] = 7 * block_bit<D>(st, j3[0], j3[1], j3[2]) + u;
+        // if it lies outside: the flipped site, the site two steps out, and
+        // the four lateral neighbours (ghost face, else global)
+        int u_out = sbit + (int)((gv[dir][0] >> gbit[dir][0]) & 1u);
+#pragma unroll
+        for (int n = 1; n < 5; ++n) {
+            int n3[3] = {j3[0], j3[1], j3[2]};
+            const int b = (ax + 1 + ((n - 1) >> 1)) % 3;
+            n3[b] += (n & 1) ? -1 : 1;
+            const bool far = n3[b] < 0 || n3[b] >= D;
+            const int gbv = (int)((gv[dir][n] >> gbit[dir][n]) & 1u);
+            const int sbv = block_bit<D>(st, n3[0], n3[1], n3[2]);
+            u_out += far ? gbv : sbv;
+        }
+        cold[dir] = 7 * block_bit<D>(st, j3[0], j3[1], j3[2]) + (out ? u_out : u_in);
         const int dd[3] = {j3[0] < 0 ? -1 : (j3[0] >= D ? 1 : 0), j3[1] < 0 ? -1 : (j3[1] >= D ? 1 : 0),
                            j3[2] < 0 ? -1 : (j3[2] >= D ? 1 : 0)};
         kj[dir] = domain_index(nd, wrap_coord(w.dx + dd[0], nd), wrap_coord(w.dy + dd[1], nd),
@@ -897,7 +902,7 @@ __device__ void phase_b(const LaunchParams &P, CtaShared &S, unsigned char *stag
         if (!*reinterpret_cast<volatile int *>(&S.ok)) return;
         // rank and pick the site: 4 domains per warp, 8 lanes each
         for (int base = warp * 4; base < nwork; base += kWarps * 4) {
-            const int i = base + (lane >> 3);
+            const int i = base + (lane & 3);
             const bool valid = i < nwork;
             const WorkItem &w = S.work[valid ? i : base];
             int site;
@@ -907,7 +912,7 @@ __device__ void phase_b(const LaunchParams &P, CtaShared &S, unsigned char *stag
             case 8: site = select_site<8>(w, stage, lane); break;
             default: site = select_site<16>(w, stage, lane); break;
             }
-            if (valid && (lane & 7) == 0) {
+            if (valid && lane < 4) {
                 S.work[i].site = site;
                 if (site < 0) raise_error(P.err, SPKMC_EINTERNAL);
             }
@@ -1221,7 +1226,7 @@ KernelShape cycle_kernel_shape()
 
 int cycle_round_items(int d_max)
 {
-    const int per = kStageBytes / staged_bytes(d_max);
+    const int per = kStageBytes / stage_slot_bytes(d_max);
     return per < kThreads ? per : kThreads;
 }
 

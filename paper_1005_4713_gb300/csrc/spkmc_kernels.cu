@@ -286,6 +286,7 @@ struct CtaShared {
     int nsegc;
     int nwork;
     int bulk_bytes;
+    int early_bytes; // bytes requested at the start of the cycle (one-round CTAs)
     int ok;
     WorkItem work[kThreads];
 };
@@ -632,15 +633,22 @@ __device__ __forceinline__ uint32_t ldg_u16_if(const uint16_t *p, bool pred)
     return v;
 }
 
+struct FlipDelta {
+    int dM, dB; // change of M and B
+};
+
 // Flip the chosen site (step 6), move the class counts of the site and of its
 // 6 neighbours (read from the pre-flip state) and refresh the ghost faces of
-// the neighbour domains that see the site; one thread per domain.  For a
+// the neighbour domains that see the site; one thread per domain.  The
+// domain's own counts belong to this thread during phase B (no other active
+// domain borders it) and are rewritten in place; counts of a neighbour domain
+// can be moved by its two active neighbours along one axis and use atomics.  For a
 // neighbour j outside the domain, the site two steps out and the neighbours
 // of j beyond the staged ghost face come from global memory; those loads are
 // all issued before any of them is used.
 template <int D>
-__device__ void apply_flip(const LaunchParams &P, CtaShared &S, const WorkItem &w,
-                           const unsigned char *stage, long long g)
+__device__ FlipDelta apply_flip(const LaunchParams &P, CtaShared &S, const WorkItem &w,
+                                const unsigned char *stage, long long g)
 {
     const LatticeDesc &Ld = P.desc[S.seg_slot[w.ls]];
     const uint16_t *st = reinterpret_cast<const uint16_t *>(stage + w.off);
@@ -677,6 +685,7 @@ __device__ void apply_flip(const LaunchParams &P, CtaShared &S, const WorkItem &
     }
     int cold[6];
     long long kj[6];
+    bool outv[6];
     const int sbit = block_bit<D>(st, s3[0], s3[1], s3[2]); // the flipped site, before its flip
 #pragma unroll
     for (int dir = 0; dir < 6; ++dir) {
@@ -706,6 +715,7 @@ __device__ void apply_flip(const LaunchParams &P, CtaShared &S, const WorkItem &
             u_out += far ? gbv : sbv;
         }
         cold[dir] = 7 * block_bit<D>(st, j3[0], j3[1], j3[2]) + (out ? u_out : u_in);
+        outv[dir] = out;
         const int dd[3] = {j3[0] < 0 ? -1 : (j3[0] >= D ? 1 : 0), j3[1] < 0 ? -1 : (j3[1] >= D ? 1 : 0),
                            j3[2] < 0 ? -1 : (j3[2] >= D ? 1 : 0)};
         kj[dir] = domain_index(nd, wrap_coord(w.dx + dd[0], nd), wrap_coord(w.dy + dd[1], nd),
@@ -713,18 +723,31 @@ __device__ void apply_flip(const LaunchParams &P, CtaShared &S, const WorkItem &
     }
     int32_t *cnt = Ld.counts;
     bool ok = true;
-    atomicAdd(cnt + w.k * kCountStride + w.cls, -1);
-    atomicAdd(cnt + w.k * kCountStride + 7 * (1 - sig) + us, 1);
+    int4 *own = reinterpret_cast<int4 *>(cnt + w.k * kCountStride);
+    const int4 c0 = __ldcg(own), c1 = __ldcg(own + 1), c2 = __ldcg(own + 2), c3 = __ldcg(own + 3);
+    int v[kClasses] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y, c2.z, c2.w, c3.x, c3.y};
+    const int snew = 7 * (1 - sig) + us;
+#pragma unroll
+    for (int c = 0; c < kClasses; ++c) v[c] += (c == snew) - (c == w.cls);
 #pragma unroll
     for (int dir = 0; dir < 6; ++dir) {
         const int cn = cold[dir] + delta;
         if (cold[dir] >= 0 && cold[dir] < kClasses && cn >= 0 && cn < kClasses) {
-            atomicAdd(cnt + kj[dir] * kCountStride + cold[dir], -1);
-            atomicAdd(cnt + kj[dir] * kCountStride + cn, 1);
+            if (outv[dir]) {
+                atomicAdd(cnt + kj[dir] * kCountStride + cold[dir], -1);
+                atomicAdd(cnt + kj[dir] * kCountStride + cn, 1);
+            } else {
+#pragma unroll
+                for (int c = 0; c < kClasses; ++c) v[c] += (c == cn) - (c == cold[dir]);
+            }
         } else {
             ok = false;
         }
     }
+    __stcg(own, make_int4(v[0], v[1], v[2], v[3]));
+    __stcg(own + 1, make_int4(v[4], v[5], v[6], v[7]));
+    __stcg(own + 2, make_int4(v[8], v[9], v[10], v[11]));
+    __stcg(own + 3, make_int4(v[12], v[13], c3.z, c3.w));
     if (!ok) raise_error(P.err, SPKMC_EINTERNAL);
     const int x = s3[0], y = s3[1], z = s3[2];
     // the flip, and the ghost faces of the neighbours that touch the site
@@ -749,16 +772,17 @@ __device__ void apply_flip(const LaunchParams &P, CtaShared &S, const WorkItem &
         }
     }
     // M and B move by -2 sigma and -2 sigma S (Eq. 1 and Eq. 4, S = 2u - 6)
-    const long long sgn = sig ? 1 : -1;
-    atomicAdd(&S.seg_nflip[w.ls], 1ULL);
-    atomicAdd(&S.seg_dM[w.ls], (unsigned long long)(-2 * sgn));
-    atomicAdd(&S.seg_dB[w.ls], (unsigned long long)(-2 * sgn * (2 * us - 6)));
+    const int sgn = sig ? 1 : -1;
+    FlipDelta f;
+    f.dM = -2 * sgn;
+    f.dB = -2 * sgn * (2 * us - 6);
+    return f;
 }
 
 // Steps 3, 4/4b, 5 and 6 for the CTA's item range, in rounds that fit the
 // staging area.
 __device__ void phase_b(const LaunchParams &P, CtaShared &S, unsigned char *stage, long long g,
-                        long long lo, long long hi, unsigned &mbar_phase)
+                        long long lo, long long hi, unsigned &mbar_phase, bool early)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int R = P.round_items;
@@ -852,7 +876,7 @@ __device__ void phase_b(const LaunchParams &P, CtaShared &S, unsigned char *stag
             wi.a = (int)a;
             wi.cls = cls;
             wi.j = (int)jrank;
-            wi.off = idx * P.item_bytes;
+            wi.off = (early ? (int)(q - lo) : idx) * P.item_bytes;
             wi.site = -1;
             wi.dx = (short)dx;
             wi.dy = (short)dy;
@@ -885,21 +909,34 @@ __device__ void phase_b(const LaunchParams &P, CtaShared &S, unsigned char *stag
                 st.clock = __dadd_rn(st.clock, __ddiv_rn(S.seg_nlogxi[i], S.seg_rnow[i]));
             }
         }
-        if (nwork == 0) continue;
-        // stage the blocks of every domain that flips in this round at once
-        if (threadIdx.x == 0) mbar_expect_tx(&S.mbar, (unsigned)bulk);
-        __syncthreads();
-        if (threadIdx.x < nwork) {
-            const WorkItem &w = S.work[threadIdx.x];
-            const LatticeDesc &Ld = P.desc[S.seg_slot[w.ls]];
-            asm volatile("fence.proxy.async.global;" ::: "memory");
-            bulk_copy_g2s(stage + w.off, Ld.cells + w.k * block_words(w.d), staged_bytes(w.d), &S.mbar);
+        if (early) {
+            // the blocks of all the CTA's domains were requested at the start
+            // of the cycle; wait for them once
+            if (S.early_bytes > 0) {
+                if (threadIdx.x == 0 && !mbar_wait_bounded(P, &S.mbar, mbar_phase))
+                    S.ok = 0; // copies never landed: leave without touching the area
+                mbar_phase ^= 1u;
+                __syncthreads();
+                if (!*reinterpret_cast<volatile int *>(&S.ok)) return;
+            }
+            if (nwork == 0) continue;
+        } else {
+            if (nwork == 0) continue;
+            // stage the blocks of every domain that flips in this round at once
+            if (threadIdx.x == 0) mbar_expect_tx(&S.mbar, (unsigned)bulk);
+            __syncthreads();
+            if (threadIdx.x < nwork) {
+                const WorkItem &w = S.work[threadIdx.x];
+                const LatticeDesc &Ld = P.desc[S.seg_slot[w.ls]];
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                bulk_copy_g2s(stage + w.off, Ld.cells + w.k * block_words(w.d), staged_bytes(w.d), &S.mbar);
+            }
+            if (threadIdx.x == 0 && !mbar_wait_bounded(P, &S.mbar, mbar_phase))
+                S.ok = 0; // copies never landed: leave without touching the area
+            mbar_phase ^= 1u;
+            __syncthreads();
+            if (!*reinterpret_cast<volatile int *>(&S.ok)) return;
         }
-        if (threadIdx.x == 0 && !mbar_wait_bounded(P, &S.mbar, mbar_phase))
-            S.ok = 0; // copies never landed: leave without touching the area
-        mbar_phase ^= 1u;
-        __syncthreads();
-        if (!*reinterpret_cast<volatile int *>(&S.ok)) return;
         // rank and pick the site: 4 domains per warp, 8 lanes each
         for (int base = warp * 4; base < nwork; base += kWarps * 4) {
             const int i = base + (lane & 3);
@@ -919,16 +956,36 @@ __device__ void phase_b(const LaunchParams &P, CtaShared &S, unsigned char *stag
         }
         __syncthreads();
         // flips and class moves, one thread per domain
+        int fls = -1, fdM = 0, fdB = 0;
         if (threadIdx.x < nwork) {
             const WorkItem w = S.work[threadIdx.x];
             if (w.site >= 0) {
+                FlipDelta f;
                 switch (w.d) {
-                case 2: apply_flip<2>(P, S, w, stage, g); break;
-                case 4: apply_flip<4>(P, S, w, stage, g); break;
-                case 8: apply_flip<8>(P, S, w, stage, g); break;
-                default: apply_flip<16>(P, S, w, stage, g); break;
+                case 2: f = apply_flip<2>(P, S, w, stage, g); break;
+                case 4: f = apply_flip<4>(P, S, w, stage, g); break;
+                case 8: f = apply_flip<8>(P, S, w, stage, g); break;
+                default: f = apply_flip<16>(P, S, w, stage, g); break;
                 }
+                fls = w.ls;
+                fdM = f.dM;
+                fdB = f.dB;
             }
+        }
+        // per-lattice flip counters, one shared-memory update per warp
+        const int lsmax = __reduce_max_sync(kFull, fls);
+        if (__all_sync(kFull, fls < 0 || fls == lsmax)) {
+            const int nf = __popc(__ballot_sync(kFull, fls >= 0));
+            const int sM = __reduce_add_sync(kFull, fdM), sB = __reduce_add_sync(kFull, fdB);
+            if (lane == 0 && lsmax >= 0) {
+                atomicAdd(&S.seg_nflip[lsmax], (unsigned long long)nf);
+                atomicAdd(&S.seg_dM[lsmax], (unsigned long long)(long long)sM);
+                atomicAdd(&S.seg_dB[lsmax], (unsigned long long)(long long)sB);
+            }
+        } else if (fls >= 0) {
+            atomicAdd(&S.seg_nflip[fls], 1ULL);
+            atomicAdd(&S.seg_dM[fls], (unsigned long long)(long long)fdM);
+            atomicAdd(&S.seg_dB[fls], (unsigned long long)(long long)fdB);
         }
         __syncthreads();
     }
@@ -988,7 +1045,38 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
     if (ld_volatile_int(P.err) != 0) return;
 
     unsigned epoch = 0, mbar_phase = 0;
+    // a CTA whose domains all fit the staging area requests their blocks at
+    // the start of each cycle, so the copies overlap step 1 and the barrier
+    // (an active domain's block does not change within its cycle)
+    const bool early = hi - lo <= P.round_items;
     for (long long g = 0; g < P.ncycles; ++g) {
+        if (early) {
+            if (threadIdx.x == 0) {
+                unsigned total = 0;
+                for (int i = 0; i < S.nsegc; ++i) {
+                    if (g >= S.seg_part[i]) continue;
+                    const long long a0 = S.seg_base[i] > lo ? S.seg_base[i] : lo;
+                    const long long a1 = S.seg_base[i + 1] < hi ? S.seg_base[i + 1] : hi;
+                    total += (unsigned)(a1 - a0) * (unsigned)staged_bytes(P.desc[S.seg_slot[i]].d);
+                }
+                S.early_bytes = (int)total;
+                if (total) mbar_expect_tx(&S.mbar, total);
+            }
+            const long long q = lo + threadIdx.x;
+            if (q < hi) {
+                const int ls = find_segment(S, q);
+                if (g < S.seg_part[ls]) {
+                    const LatticeDesc &Ld = P.desc[S.seg_slot[ls]];
+                    const long long t = S.seg_t0[ls] + g;
+                    int dx, dy, dz;
+                    active_domain(Ld.half, q - S.seg_base[ls], (int)(t & 7), dx, dy, dz);
+                    const long long k = domain_index(Ld.nd, dx, dy, dz);
+                    asm volatile("fence.proxy.async.global;" ::: "memory");
+                    bulk_copy_g2s(stage + (q - lo) * P.item_bytes, Ld.cells + k * block_words(Ld.d),
+                                  staged_bytes(Ld.d), &S.mbar);
+                }
+            }
+        }
         phase_a(P, S, g, lo, hi);
         __syncthreads();
         for (int i = threadIdx.x; i < S.nsegc; i += blockDim.x) {
@@ -999,7 +1087,7 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
             S.seg_rmax[i] = 0;
         }
         if (!grid_barrier(P, S, epoch)) return;
-        phase_b(P, S, stage, g, lo, hi, mbar_phase);
+        phase_b(P, S, stage, g, lo, hi, mbar_phase, early);
         if (!*reinterpret_cast<volatile int *>(&S.ok)) return;
         if (g + 1 < P.ncycles) {
             const bool odd = P.parity0 >= 0 && (((long long)P.parity0 + g) & 1LL) == 1LL;

@@ -90,7 +90,7 @@ __host__ __device__ constexpr int staged_bytes(int d) { return 2 * block_words(d
 // Staging slot: the block rounded up to an odd number of 16-byte units, so
 // that consecutive slots start in different shared-memory banks.
 __host__ __device__ constexpr int stage_slot_bytes(int d) { return ((staged_bytes(d) / 16) | 1) * 16; }
-constexpr int kStageBytes = 88 * 1024; // phase-B staging area per CTA
+constexpr int kStageBytes = 84 * 1024; // phase-B staging area per CTA
 
 // Host-side launch helpers implemented in spkmc_kernels.cu.
 struct KernelShape {

@@ -257,14 +257,15 @@ __device__ __forceinline__ uint32_t class_mask(const RowPlanes &p, int cls)
 // Persistent cycle kernel
 // ---------------------------------------------------------------------------
 struct __align__(16) WorkItem {
-    long long k;  // domain index
-    int ls;       // local segment
-    int a;        // active index within the lattice
-    int cls;      // chosen class
-    int j;        // rank of the site within the class
-    int off;      // byte offset of the staged block
-    int site;     // chosen local site (set by the classifier), -1 if none
+    long long k;      // domain index
+    int ls;           // local segment
+    int a;            // active index within the lattice
+    int cls;          // chosen class
+    int j;            // rank of the site within the class
+    int off;          // byte offset of the staged block
+    int site;         // chosen local site (set by the classifier), -1 if none
     short dx, dy, dz, d;
+    uint32_t npk[7];  // the domain's class counts, two 16-bit counts per word
 };
 
 struct CtaShared {
@@ -417,8 +418,19 @@ __device__ bool mbar_wait_bounded(const LaunchParams &P, unsigned long long *m, 
     }
 }
 
+// The frequency line of one active domain as phase B needs it.
+struct Line {
+    double cum[kClasses];  // cumulative rates, class order
+    double u01;            // uniform draw for the event
+    unsigned long long w1; // 64-bit draw for the site rank
+    uint32_t npk[7];       // class counts, two 16-bit counts per word
+};
+
 // Step 1: frequency line of every active domain of the CTA's item range.
-__device__ void phase_a(const LaunchParams &P, CtaShared &S, long long g, long long lo, long long hi)
+// With `keep` (the CTA has at most one item per thread) the line of the
+// thread's item stays in registers for phase B; otherwise it goes to scratch.
+__device__ void phase_a(const LaunchParams &P, CtaShared &S, long long g, long long lo, long long hi,
+                        bool keep, Line &line)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (long long base = lo + warp * 32; base < hi; base += kThreads) {
@@ -437,6 +449,11 @@ __device__ void phase_a(const LaunchParams &P, CtaShared &S, long long g, long l
                 const int4 *cp = reinterpret_cast<const int4 *>(Ld.counts + k * kCountStride);
                 const int4 n0 = __ldcg(cp), n1 = __ldcg(cp + 1), n2 = __ldcg(cp + 2),
                            n3 = __ldcg(cp + 3);
+                // the draw does not depend on the counts: compute it while they load
+                unsigned long long w[4];
+                philox4x64_10((unsigned long long)t, (unsigned long long)k, 1ULL, 0ULL, Ld.seed, 0ULL,
+                              w);
+                const double u01 = __ull2double_rn(w[0] >> 11) * 0x1p-53;
                 const int n[kClasses] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z,
                                          n1.w, n2.x, n2.y, n2.z, n2.w, n3.x, n3.y};
                 double cum[kClasses];
@@ -447,19 +464,25 @@ __device__ void phase_a(const LaunchParams &P, CtaShared &S, long long g, long l
                     acc = __dadd_rn(acc, __dmul_rn((double)n[c], __ldg(&Ld.rate[c])));
                     cum[c] = acc;
                 }
-                unsigned long long w[4];
-                philox4x64_10((unsigned long long)t, (unsigned long long)k, 1ULL, 0ULL, Ld.seed, 0ULL,
-                              w);
-                const double u01 = __ull2double_rn(w[0] >> 11) * 0x1p-53;
-                double2 *sp = reinterpret_cast<double2 *>(Ld.scratch + a * kScratchStride);
+                uint32_t npk[7];
 #pragma unroll
-                for (int c = 0; c < kClasses; c += 2) __stcg(sp + c / 2, make_double2(cum[c], cum[c + 1]));
-                __stcg(sp + 7, make_double2(u01, __longlong_as_double((long long)w[1])));
-                uint4 *np = reinterpret_cast<uint4 *>(sp + 8);
-                __stcg(np, make_uint4((uint32_t)n[0] | ((uint32_t)n[1] << 16), (uint32_t)n[2] | ((uint32_t)n[3] << 16),
-                                      (uint32_t)n[4] | ((uint32_t)n[5] << 16), (uint32_t)n[6] | ((uint32_t)n[7] << 16)));
-                __stcg(np + 1, make_uint4((uint32_t)n[8] | ((uint32_t)n[9] << 16), (uint32_t)n[10] | ((uint32_t)n[11] << 16),
-                                          (uint32_t)n[12] | ((uint32_t)n[13] << 16), 0u));
+                for (int c = 0; c < 7; ++c) npk[c] = (uint32_t)n[2 * c] | ((uint32_t)n[2 * c + 1] << 16);
+                if (keep) {
+#pragma unroll
+                    for (int c = 0; c < kClasses; ++c) line.cum[c] = cum[c];
+                    line.u01 = u01;
+                    line.w1 = w[1];
+#pragma unroll
+                    for (int c = 0; c < 7; ++c) line.npk[c] = npk[c];
+                } else {
+                    double2 *sp = reinterpret_cast<double2 *>(Ld.scratch + a * kScratchStride);
+#pragma unroll
+                    for (int c = 0; c < kClasses; c += 2) __stcg(sp + c / 2, make_double2(cum[c], cum[c + 1]));
+                    __stcg(sp + 7, make_double2(u01, __longlong_as_double((long long)w[1])));
+                    uint4 *np = reinterpret_cast<uint4 *>(sp + 8);
+                    __stcg(np, make_uint4(npk[0], npk[1], npk[2], npk[3]));
+                    __stcg(np + 1, make_uint4(npk[4], npk[5], npk[6], 0u));
+                }
                 rbits = (unsigned long long)__double_as_longlong(acc);
             } else {
                 ls = -1;
@@ -473,18 +496,16 @@ __device__ void phase_a(const LaunchParams &P, CtaShared &S, long long g, long l
             atomicMax(&S.seg_rmax[ls], rbits);
         }
     }
-    if (threadIdx.x == kThreads - 1) {
-        // -ln(xi) of this cycle's time step (step 5) for the lattices whose
-        // first active domain this CTA owns, by the last thread (usually idle)
-        for (int i = 0; i < S.nsegc; ++i) {
-            if (S.seg_base[i] < lo || g >= S.seg_part[i]) continue;
-            const LatticeDesc &Ld = P.desc[S.seg_slot[i]];
-            unsigned long long wc[4];
-            philox4x64_10((unsigned long long)(S.seg_t0[i] + g), 0ULL, 2ULL, 0ULL, Ld.seed, 0ULL, wc);
-            const double xi = __ull2double_rn(2ULL * (wc[0] >> 12) + 1ULL) * 0x1p-53;
-            S.seg_nlogxi[i] = -log(xi);
-        }
-    }
+}
+
+// -ln(xi) of the time step of lattice segment i in grid cycle g (step 5).
+__device__ __forceinline__ double neg_log_xi(const LaunchParams &P, const CtaShared &S, int i, long long g)
+{
+    const LatticeDesc &Ld = P.desc[S.seg_slot[i]];
+    unsigned long long wc[4];
+    philox4x64_10((unsigned long long)(S.seg_t0[i] + g), 0ULL, 2ULL, 0ULL, Ld.seed, 0ULL, wc);
+    const double xi = __ull2double_rn(2ULL * (wc[0] >> 12) + 1ULL) * 0x1p-53;
+    return -log(xi);
 }
 
 // Rank the sites of class w.cls in ascending local index and return the
@@ -724,8 +745,9 @@ __device__ FlipDelta apply_flip(const LaunchParams &P, CtaShared &S, const WorkI
     int32_t *cnt = Ld.counts;
     bool ok = true;
     int4 *own = reinterpret_cast<int4 *>(cnt + w.k * kCountStride);
-    const int4 c0 = __ldcg(own), c1 = __ldcg(own + 1), c2 = __ldcg(own + 2), c3 = __ldcg(own + 3);
-    int v[kClasses] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y, c2.z, c2.w, c3.x, c3.y};
+    int v[kClasses];
+#pragma unroll
+    for (int c = 0; c < kClasses; ++c) v[c] = (int)((w.npk[c >> 1] >> (16 * (c & 1))) & 0xFFFFu);
     const int snew = 7 * (1 - sig) + us;
 #pragma unroll
     for (int c = 0; c < kClasses; ++c) v[c] += (c == snew) - (c == w.cls);
@@ -747,7 +769,7 @@ __device__ FlipDelta apply_flip(const LaunchParams &P, CtaShared &S, const WorkI
     __stcg(own, make_int4(v[0], v[1], v[2], v[3]));
     __stcg(own + 1, make_int4(v[4], v[5], v[6], v[7]));
     __stcg(own + 2, make_int4(v[8], v[9], v[10], v[11]));
-    __stcg(own + 3, make_int4(v[12], v[13], c3.z, c3.w));
+    __stcg(own + 3, make_int4(v[12], v[13], 0, 0));
     if (!ok) raise_error(P.err, SPKMC_EINTERNAL);
     const int x = s3[0], y = s3[1], z = s3[2];
     // the flip, and the ghost faces of the neighbours that touch the site
@@ -779,14 +801,16 @@ __device__ FlipDelta apply_flip(const LaunchParams &P, CtaShared &S, const WorkI
     return f;
 }
 
-// Steps 3, 4/4b, 5 and 6 for the CTA's item range, in rounds that fit the
-// staging area.
-__device__ void phase_b(const LaunchParams &P, CtaShared &S, unsigned char *stage, long long g,
-                        long long lo, long long hi, unsigned &mbar_phase, bool early)
+// Steps 3, 4/4b, 5 and 6 for the items [rbase, rbase + round_items) of the
+// CTA's range.  With `early` (one-round CTA) the frequency lines come from
+// registers and the blocks were requested at the start of the cycle.
+__device__ __forceinline__ void phase_b_round(const LaunchParams &P, CtaShared &S, unsigned char *stage,
+                                              long long g, long long lo, long long hi, long long rbase,
+                                              unsigned &mbar_phase, bool early, const Line &line)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int R = P.round_items;
-    for (long long rbase = lo; rbase < hi; rbase += R) {
+    {
         if (threadIdx.x == 0) {
             S.nwork = 0;
             S.bulk_bytes = 0;
@@ -794,6 +818,7 @@ __device__ void phase_b(const LaunchParams &P, CtaShared &S, unsigned char *stag
         __syncthreads();
         const long long q = rbase + threadIdx.x;
         int ls = -1, cls = -1, dx = 0, dy = 0, dz = 0, dval = 0;
+        uint32_t ownpk[7] = {0, 0, 0, 0, 0, 0, 0};
         long long a = 0, k = 0;
         unsigned long long fxlo = 0, fxhi = 0, jrank = 0;
         if (threadIdx.x < R && q < hi) {
@@ -805,22 +830,36 @@ __device__ void phase_b(const LaunchParams &P, CtaShared &S, unsigned char *stag
                 const long long t = S.seg_t0[ls] + g;
                 const double Rmax = __longlong_as_double(
                     (long long)__ldcg(&P.state[slot].rmax[t % 3]));
-                const double2 *sp = reinterpret_cast<const double2 *>(Ld.scratch + a * kScratchStride);
                 double cum[kClasses];
+                uint32_t npk[7];
+                double u01;
+                unsigned long long w1;
+                if (early) {
 #pragma unroll
-                for (int c = 0; c < kClasses; c += 2) {
-                    const double2 v = __ldcg(sp + c / 2);
-                    cum[c] = v.x;
-                    cum[c + 1] = v.y;
+                    for (int c = 0; c < kClasses; ++c) cum[c] = line.cum[c];
+#pragma unroll
+                    for (int c = 0; c < 7; ++c) npk[c] = line.npk[c];
+                    u01 = line.u01;
+                    w1 = line.w1;
+                } else {
+                    const double2 *sp = reinterpret_cast<const double2 *>(Ld.scratch + a * kScratchStride);
+#pragma unroll
+                    for (int c = 0; c < kClasses; c += 2) {
+                        const double2 v = __ldcg(sp + c / 2);
+                        cum[c] = v.x;
+                        cum[c + 1] = v.y;
+                    }
+                    const double2 uw = __ldcg(sp + 7);
+                    const uint4 n4a = __ldcg(reinterpret_cast<const uint4 *>(sp + 8));
+                    const uint4 n4b = __ldcg(reinterpret_cast<const uint4 *>(sp + 9));
+                    npk[0] = n4a.x; npk[1] = n4a.y; npk[2] = n4a.z; npk[3] = n4a.w;
+                    npk[4] = n4b.x; npk[5] = n4b.y; npk[6] = n4b.z;
+                    u01 = uw.x;
+                    w1 = (unsigned long long)__double_as_longlong(uw.y);
                 }
-                const double2 uw = __ldcg(sp + 7);
-                const uint4 n4a = __ldcg(reinterpret_cast<const uint4 *>(sp + 8));
-                const uint4 n4b = __ldcg(reinterpret_cast<const uint4 *>(sp + 9));
-                const uint32_t npk[7] = {n4a.x, n4a.y, n4a.z, n4a.w, n4b.x, n4b.y, n4b.z};
-                const unsigned long long w1 = (unsigned long long)__double_as_longlong(uw.y);
                 // target on the frequency line padded to R_max (steps 3-4):
                 // the first class whose cumulative rate exceeds it, else null.
-                const double target = __dmul_rn(uw.x, Rmax);
+                const double target = __dmul_rn(u01, Rmax);
                 const unsigned long long tb = (unsigned long long)__double_as_longlong(target);
 #pragma unroll
                 for (int c = kClasses - 1; c >= 0; --c)
@@ -848,6 +887,8 @@ __device__ void phase_b(const LaunchParams &P, CtaShared &S, unsigned char *stag
                     for (int c = 0; c < kClasses; ++c)
                         if (c == cls) nc = (npk[c >> 1] >> (16 * (c & 1))) & 0xFFFFu;
                     jrank = __umul64hi(w1, nc);
+#pragma unroll
+                    for (int c = 0; c < 7; ++c) ownpk[c] = npk[c];
                 }
                 if (a == 0) {
                     S.seg_rnow[ls] = Rmax; // the clock moves once this cycle (step 5)
@@ -882,6 +923,8 @@ __device__ void phase_b(const LaunchParams &P, CtaShared &S, unsigned char *stag
             wi.dy = (short)dy;
             wi.dz = (short)dz;
             wi.d = (short)dval;
+#pragma unroll
+            for (int c = 0; c < 7; ++c) wi.npk[c] = ownpk[c];
             S.work[idx] = wi;
         }
         const int ls0 = __shfl_sync(kFull, ls, 0);
@@ -907,6 +950,7 @@ __device__ void phase_b(const LaunchParams &P, CtaShared &S, unsigned char *stag
                 S.seg_tick[i] = 0;
                 LatticeState &st = P.state[S.seg_slot[i]];
                 st.clock = __dadd_rn(st.clock, __ddiv_rn(S.seg_nlogxi[i], S.seg_rnow[i]));
+                if (g + 1 < S.seg_part[i]) S.seg_nlogxi[i] = neg_log_xi(P, S, i, g + 1); // drawn ahead
             }
         }
         if (early) {
@@ -919,9 +963,9 @@ __device__ void phase_b(const LaunchParams &P, CtaShared &S, unsigned char *stag
                 __syncthreads();
                 if (!*reinterpret_cast<volatile int *>(&S.ok)) return;
             }
-            if (nwork == 0) continue;
+            if (nwork == 0) return;
         } else {
-            if (nwork == 0) continue;
+            if (nwork == 0) return;
             // stage the blocks of every domain that flips in this round at once
             if (threadIdx.x == 0) mbar_expect_tx(&S.mbar, (unsigned)bulk);
             __syncthreads();
@@ -991,6 +1035,19 @@ __device__ void phase_b(const LaunchParams &P, CtaShared &S, unsigned char *stag
     }
 }
 
+__device__ void phase_b(const LaunchParams &P, CtaShared &S, unsigned char *stage, long long g,
+                        long long lo, long long hi, unsigned &mbar_phase, bool early, const Line &line)
+{
+    if (early) {
+        if (lo < hi) phase_b_round(P, S, stage, g, lo, hi, lo, mbar_phase, true, line);
+        return;
+    }
+    for (long long rbase = lo; rbase < hi; rbase += P.round_items) {
+        phase_b_round(P, S, stage, g, lo, hi, rbase, mbar_phase, false, line);
+        if (!*reinterpret_cast<volatile int *>(&S.ok)) return;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams P)
 {
     __shared__ CtaShared S;
@@ -1042,6 +1099,10 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
         S.seg_tick[i] = 0;
     }
     __syncthreads();
+    if (threadIdx.x == kThreads - 1) {
+        for (int i = 0; i < S.nsegc; ++i)
+            if (S.seg_base[i] >= lo && S.seg_part[i] > 0) S.seg_nlogxi[i] = neg_log_xi(P, S, i, 0);
+    }
     if (ld_volatile_int(P.err) != 0) return;
 
     unsigned epoch = 0, mbar_phase = 0;
@@ -1050,6 +1111,7 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
     // (an active domain's block does not change within its cycle)
     const bool early = hi - lo <= P.round_items;
     for (long long g = 0; g < P.ncycles; ++g) {
+        Line line; // this cycle's frequency line of the thread's item (one-round CTAs)
         if (early) {
             if (threadIdx.x == 0) {
                 unsigned total = 0;
@@ -1077,7 +1139,7 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
                 }
             }
         }
-        phase_a(P, S, g, lo, hi);
+        phase_a(P, S, g, lo, hi, early, line);
         __syncthreads();
         for (int i = threadIdx.x; i < S.nsegc; i += blockDim.x) {
             if (g < S.seg_part[i]) {
@@ -1087,7 +1149,7 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
             S.seg_rmax[i] = 0;
         }
         if (!grid_barrier(P, S, epoch)) return;
-        phase_b(P, S, stage, g, lo, hi, mbar_phase, early);
+        phase_b(P, S, stage, g, lo, hi, mbar_phase, early, line);
         if (!*reinterpret_cast<volatile int *>(&S.ok)) return;
         if (g + 1 < P.ncycles) {
             const bool odd = P.parity0 >= 0 && (((long long)P.parity0 + g) & 1LL) == 1LL;

@@ -215,6 +215,40 @@ int spkmc_batch_get_event_log(spkmc_batch_t *b, int32_t slot, spkmc_event *buf, 
 /* Number of admitted (not retired) slots and device bytes they hold. */
 int spkmc_batch_usage(spkmc_batch_t *b, int32_t *live_slots, int64_t *device_bytes);
 
+/* ---- no-allocation variant --------------------------------------------- */
+/* Some callers cannot allocate device memory: code that runs inside a memory
+ * pool or arena owned by someone else, code that must not touch the CUDA
+ * allocator at all (real-time loops, or an allocator that is itself being
+ * set up), or a host program that only lends its own buffers.  This entry
+ * point runs spkMC cycles on such a caller's lattice without any allocation.
+ * It has no counterpart in the paper: it is the same cycle as
+ * spkmc_run_cycles, with all of its working memory taken from one
+ * file-scope device array of SPKMC_NOALLOC_SCRATCH_BYTES bytes that every GPU
+ * which loads the library holds until the process exits.
+ *
+ *   p          physics of the lattice (L, domain_edge, J, H, T, seed); init
+ *              is ignored and event_log_capacity must be 0;
+ *   dev_spins  device buffer of L^3 int8 +1/-1 in global order (input), which
+ *              receives the spins after the cycles (output);
+ *   state      host struct: cycle, clock and counters before the call (input)
+ *              and after it (output); start from all zeros;
+ *   ncycles    cycles to run (>= 0);
+ *   stream     cudaStream_t of the caller (NULL = legacy default stream).
+ *
+ * The lattice's blocks, counts, frequency lines and launch tables must fit
+ * the array: EINVAL (with the size in the message) for larger lattices, e.g.
+ * 256^3 with d = 16 fits and 512^3 does not.  The call returns after the
+ * work has finished.  No cudaMalloc, cudaFree or other allocating routine is
+ * called.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one array and it keeps
+ * the last call's contents (the call clears what must start at zero): calls
+ * that overlap on the GPU, from any thread or stream, race with each other
+ * and must be serialised by the caller. */
+#define SPKMC_NOALLOC_SCRATCH_BYTES (16u << 20)
+int spkmc_run_cycles_noalloc(const spkmc_params *p, int8_t *dev_spins, spkmc_state *state,
+                             int64_t ncycles, void *stream);
+
 /* Thread-local description of the last error of this thread. */
 const char *spkmc_last_error(void);
 

@@ -275,6 +275,15 @@ def spkmc_batch_usage(b):
     return int(n.value), int(by.value)
 
 
+def spkmc_run_cycles_noalloc(p: spkmc_params, dev_spins_ptr: int, state: spkmc_state, ncycles: int,
+                             stream=None) -> spkmc_state:
+    """Cycles on a caller-owned device int8 spin buffer with no allocation
+    (see include/spkmc.h); ``state`` is updated in place and returned."""
+    _check(lib().spkmc_run_cycles_noalloc(ctypes.byref(p), ctypes.c_void_p(dev_spins_ptr), ctypes.byref(state),
+                                          int(ncycles), stream))
+    return state
+
+
 def spkmc_last_error() -> str:
     return lib().spkmc_last_error().decode(errors="replace")
 

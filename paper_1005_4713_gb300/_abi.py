@@ -17,6 +17,8 @@ SPKMC_EINTERNAL = 6
 SPKMC_INIT_HOT = 0
 SPKMC_INIT_COLD = 1
 
+SPKMC_NOALLOC_SCRATCH_BYTES = 16 << 20
+
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EBUSY", 6: "EINTERNAL"}
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -101,6 +103,8 @@ PROTOTYPES = {
     "spkmc_batch_get_spins": (ctypes.c_int, [_h, _i32, ctypes.c_void_p, _sz]),
     "spkmc_batch_get_event_log": (ctypes.c_int, [_h, _i32, ctypes.c_void_p, _sz, P(_sz)]),
     "spkmc_batch_usage": (ctypes.c_int, [_h, P(_i32), P(_i64)]),
+    "spkmc_run_cycles_noalloc": (ctypes.c_int, [P(spkmc_params), ctypes.c_void_p, P(spkmc_state), _i64,
+                                                 ctypes.c_void_p]),
     "spkmc_last_error": (ctypes.c_char_p, []),
 }
 

@@ -13,6 +13,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -967,3 +968,157 @@ const char *spkmc_last_error(void)
 }
 
 } // extern "C"
+
+// ---------------------------------------------------------------------------
+// No-allocation variant: all working memory in one file-scope device array.
+// ---------------------------------------------------------------------------
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SPKMC_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+unsigned char *g_noalloc_ptr[kNoallocMaxDevices] = {};
+int g_noalloc_blocks_per_sm[kNoallocMaxDevices] = {};
+int g_noalloc_sms[kNoallocMaxDevices] = {};
+
+// Device address of the array on the current device, looked up once per
+// device (a host-side use of the symbol itself is not a device address).
+int noalloc_base(int dev, unsigned char **out)
+{
+    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(SPKMC_EINVAL, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) return cuda_fail(e, "cudaGetSymbolAddress of the no-allocation scratch");
+        int sms = 0;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return cuda_fail(e, "device attributes");
+        const int per = cycle_kernel_max_blocks_per_sm(dev);
+        if (per < 1) return fail(SPKMC_ECUDA, "cycle kernel cannot be resident");
+        g_noalloc_ptr[dev] = static_cast<unsigned char *>(ptr);
+        g_noalloc_sms[dev] = sms;
+        g_noalloc_blocks_per_sm[dev] = per;
+    }
+    *out = g_noalloc_ptr[dev];
+    return SPKMC_OK;
+}
+
+} // namespace
+
+extern "C" int spkmc_run_cycles_noalloc(const spkmc_params *p, int8_t *dev_spins, spkmc_state *state,
+                                        int64_t ncycles, void *stream)
+{
+    int d = 0;
+    int rc = check_params(p, &d);
+    if (rc) return rc;
+    if (!dev_spins || !state) return fail(SPKMC_EINVAL, "dev_spins and state must not be NULL");
+    if (ncycles < 0) return fail(SPKMC_EINVAL, "ncycles must be >= 0");
+    if (p->event_log_capacity != 0) return fail(SPKMC_EINVAL, "the no-allocation variant keeps no event log");
+    if (state->cycle < 0 || state->n_flip < 0 || state->n_null < 0)
+        return fail(SPKMC_EINVAL, "state counters must be >= 0");
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    unsigned char *base = nullptr;
+    if ((rc = noalloc_base(dev, &base)) != SPKMC_OK) return rc;
+
+    // carve the array: tables first, then the lattice
+    const Sizes sz = sizes_of(p->L, d, 0);
+    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+    size_t off = 0;
+    LatticeDesc *d_desc = reinterpret_cast<LatticeDesc *>(base + off);
+    off += up(sizeof(LatticeDesc));
+    LatticeState *d_state = reinterpret_cast<LatticeState *>(base + off);
+    off += up(sizeof(LatticeState));
+    Segment *d_seg = reinterpret_cast<Segment *>(base + off);
+    off += up(sizeof(Segment));
+    unsigned *d_bar = reinterpret_cast<unsigned *>(base + off);
+    off += 256;
+    int *d_err = reinterpret_cast<int *>(base + off);
+    off += 256;
+    const size_t lattice_at = off;
+    off += (size_t)sz.cells_b + (size_t)sz.counts_b + (size_t)sz.scratch_b;
+    if (off > SPKMC_NOALLOC_SCRATCH_BYTES)
+        return fail(SPKMC_EINVAL, "lattice L=%d d=%d needs %zu bytes of scratch, the no-allocation array has %u",
+                    p->L, d, off, SPKMC_NOALLOC_SCRATCH_BYTES);
+
+    LatticeDesc D{};
+    D.cells = reinterpret_cast<uint16_t *>(base + lattice_at);
+    D.counts = reinterpret_cast<int32_t *>(base + lattice_at + sz.cells_b);
+    D.scratch = reinterpret_cast<double *>(base + lattice_at + sz.cells_b + sz.counts_b);
+    D.log = nullptr;
+    D.log_cap = 0;
+    D.log_t0 = 0;
+    host_rates(p->J, p->H, p->T, D.rate);
+    D.seed = p->seed;
+    D.L = p->L;
+    D.d = d;
+    D.nd = p->L / d;
+    D.half = D.nd / 2;
+    D.K = sz.K;
+    D.Kact = sz.Kact;
+    LatticeState st{};
+    st.t = state->cycle;
+    st.clock = state->clock;
+    st.n_flip = (unsigned long long)state->n_flip;
+    st.n_null = (unsigned long long)state->n_null;
+    st.null_fx_lo = state->sum_null_rate_fx[0];
+    st.null_fx_hi = state->sum_null_rate_fx[1];
+    st.budget = -1; // rmax slots, M and B start at zero
+    Segment seg{};
+    seg.base = 0;
+    seg.slot = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    // set-up: this call's tables (the array keeps the previous call's bytes)
+    CUDA_TRY(cudaMemcpyAsync(d_desc, &D, sizeof(D), cudaMemcpyHostToDevice, s), "upload descriptor");
+    CUDA_TRY(cudaMemcpyAsync(d_state, &st, sizeof(st), cudaMemcpyHostToDevice, s), "upload state");
+    CUDA_TRY(cudaMemcpyAsync(d_seg, &seg, sizeof(seg), cudaMemcpyHostToDevice, s), "upload segment");
+    CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), s), "clear error flag");
+    if ((rc = launch_pack_rows(D, dev_spins, s)) != SPKMC_OK) return cuda_fail(cudaGetLastError(), "pack spins");
+    if ((rc = launch_ghosts(D, 0, nullptr, s)) != SPKMC_OK) return cuda_fail(cudaGetLastError(), "ghost faces");
+    if ((rc = launch_count_classes(D, 0, nullptr, s)) != SPKMC_OK) return cuda_fail(cudaGetLastError(), "class counts");
+
+    // the cycles, in launches of at most 2^18 cycles, as spkmc_run_cycles
+    const long long per_sm = g_noalloc_blocks_per_sm[dev];
+    const long long gmax = per_sm * g_noalloc_sms[dev];
+    long long grid = std::max(1LL, std::min(gmax, (sz.Kact + 63) / 64));
+    long long left = ncycles, t = state->cycle;
+    while (left > 0) {
+        const long long n = std::min(left, 1LL << 18);
+        CUDA_TRY(cudaMemsetAsync(d_bar, 0, sizeof(unsigned), s), "reset barrier");
+        LaunchParams P{};
+        P.desc = d_desc;
+        P.state = d_state;
+        P.seg = d_seg;
+        P.nseg = 1;
+        P.parity0 = (int)(t & 1);
+        P.Q = sz.Kact;
+        P.ncycles = n;
+        P.bar = d_bar;
+        P.err = d_err;
+        P.timeout_ns = 2000000000LL;
+        P.skip_cta = -1;
+        P.item_bytes = stage_slot_bytes(d);
+        P.round_items = cycle_round_items(d);
+        if (launch_cycles(P, (int)grid, s, grid > 1) != SPKMC_OK)
+            return cuda_fail(cudaGetLastError(), "persistent cycle launch");
+        left -= n;
+        t += n;
+    }
+    if ((rc = launch_unpack_rows(D, dev_spins, s)) != SPKMC_OK) return cuda_fail(cudaGetLastError(), "unpack spins");
+    int err = 0;
+    CUDA_TRY(cudaMemcpyAsync(&st, d_state, sizeof(st), cudaMemcpyDeviceToHost, s), "read state");
+    CUDA_TRY(cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s), "read error flag");
+    CUDA_TRY(cudaStreamSynchronize(s), "stream synchronize");
+    if (err == SPKMC_ETIMEOUT) return fail(SPKMC_ETIMEOUT, "a grid barrier timed out on the device");
+    if (err != 0) return fail(err, "device reported inconsistent class counts");
+    state->cycle = st.t;
+    state->clock = st.clock;
+    state->n_flip = (int64_t)st.n_flip;
+    state->n_null = (int64_t)st.n_null;
+    state->sum_null_rate_fx[0] = st.null_fx_lo;
+    state->sum_null_rate_fx[1] = st.null_fx_hi;
+    return SPKMC_OK;
+}

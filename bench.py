@@ -167,6 +167,11 @@ def dist_setup(n_gpus):
     return world, rank, local, pg
 
 
+def replica_seed(rank: int) -> int:
+    """Replicas (one lattice per GPU) differ only in their seed."""
+    return SEED_BENCH + rank
+
+
 def max_over_ranks(value: float, pg, device=None) -> float:
     if pg is None:
         return value
@@ -279,7 +284,7 @@ def run_gpu(args, world, rank, local, pg):
     stream = torch.cuda.Stream(device)
     torch.cuda.set_stream(stream)
     cfg = sp.torch_config()
-    seed = SEED_BENCH + rank
+    seed = replica_seed(rank)
     lat = sp.Lattice(L_BENCH, D_BENCH, 1.0, 0.0, 4.5115, seed, config=cfg)
     kact = lat.K_act
     cps = args.cycles_per_step

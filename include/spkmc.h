@@ -212,6 +212,10 @@ int spkmc_batch_observables(spkmc_batch_t *b, int32_t slot, spkmc_obs *out);
 int spkmc_batch_get_spins(spkmc_batch_t *b, int32_t slot, int8_t *host_buf, size_t n);
 int spkmc_batch_get_event_log(spkmc_batch_t *b, int32_t slot, spkmc_event *buf, size_t cap,
                               size_t *n_out);
+/* Observables of every slot in one synchronising read: out[slot] for
+ * slot < min(cap, capacity); slots that are not live get L = 0.  n_out
+ * receives the number of entries written. */
+int spkmc_batch_observables_all(spkmc_batch_t *b, spkmc_obs *out, int32_t cap, int32_t *n_out);
 /* Number of admitted (not retired) slots and device bytes they hold. */
 int spkmc_batch_usage(spkmc_batch_t *b, int32_t *live_slots, int64_t *device_bytes);
 

@@ -268,6 +268,14 @@ def spkmc_batch_get_event_log(b, slot: int, cap: int) -> np.ndarray:
     return buf[: n.value]
 
 
+def spkmc_batch_observables_all(b, capacity: int):
+    """Observables of all slots (list indexed by slot; L == 0 for free slots)."""
+    arr = (spkmc_obs * max(int(capacity), 1))()
+    n = ctypes.c_int32()
+    _check(lib().spkmc_batch_observables_all(b, arr, int(capacity), ctypes.byref(n)))
+    return [arr[i] for i in range(n.value)]
+
+
 def spkmc_batch_usage(b):
     n = ctypes.c_int32()
     by = ctypes.c_int64()
@@ -393,6 +401,9 @@ class Batch:
     def event_log(self, slot: int, cap=None) -> np.ndarray:
         c = self.params[slot].event_log_capacity if cap is None else cap
         return spkmc_batch_get_event_log(self.b, slot, c)
+
+    def observables_all(self):
+        return spkmc_batch_observables_all(self.b, self.capacity)
 
     def usage(self):
         return spkmc_batch_usage(self.b)

@@ -102,6 +102,7 @@ PROTOTYPES = {
     "spkmc_batch_observables": (ctypes.c_int, [_h, _i32, P(spkmc_obs)]),
     "spkmc_batch_get_spins": (ctypes.c_int, [_h, _i32, ctypes.c_void_p, _sz]),
     "spkmc_batch_get_event_log": (ctypes.c_int, [_h, _i32, ctypes.c_void_p, _sz, P(_sz)]),
+    "spkmc_batch_observables_all": (ctypes.c_int, [_h, P(spkmc_obs), _i32, P(_i32)]),
     "spkmc_batch_usage": (ctypes.c_int, [_h, P(_i32), P(_i64)]),
     "spkmc_run_cycles_noalloc": (ctypes.c_int, [P(spkmc_params), ctypes.c_void_p, P(spkmc_state), _i64,
                                                  ctypes.c_void_p]),

@@ -952,6 +952,44 @@ int spkmc_batch_get_event_log(spkmc_batch_t *b, int32_t slot, spkmc_event *buf, 
     return get_event_log(b, slot, buf, cap, n_out);
 }
 
+int spkmc_batch_observables_all(spkmc_batch_t *b, spkmc_obs *out, int32_t cap, int32_t *n_out)
+{
+    if (!b || !n_out || (cap > 0 && !out)) return fail(SPKMC_EINVAL, "NULL argument");
+    *n_out = 0;
+    DeviceGuard g(b->device);
+    const int n = std::min<int>(cap, b->capacity);
+    if (n <= 0) return SPKMC_OK;
+    CUDA_TRY(cudaMemcpyAsync(b->h_state, b->d_state, sizeof(LatticeState) * n, cudaMemcpyDeviceToHost, b->stream),
+             "read states");
+    int rc = sync_and_check(b);
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i) {
+        spkmc_obs &o = out[i];
+        std::memset(&o, 0, sizeof(o));
+        const Slot &s = b->slots[i];
+        if (!s.live) continue;
+        const LatticeState &st = b->h_state[i];
+        const double N = (double)s.params.L * s.params.L * s.params.L;
+        o.cycle = st.t;
+        o.clock = st.clock;
+        o.M = st.M;
+        o.B = st.B;
+        o.E = -s.params.J * (double)st.B - s.params.H * (double)st.M;
+        o.m = (double)st.M / N;
+        o.m2 = o.m * o.m;
+        o.m4 = o.m2 * o.m2;
+        o.n_flip = (int64_t)st.n_flip;
+        o.n_null = (int64_t)st.n_null;
+        o.sum_null_rate_fx[0] = st.null_fx_lo;
+        o.sum_null_rate_fx[1] = st.null_fx_hi;
+        o.sum_null_rate = (double)st.null_fx_hi + std::ldexp((double)st.null_fx_lo, -64);
+        o.L = s.params.L;
+        o.domain_edge = s.d;
+    }
+    *n_out = n;
+    return SPKMC_OK;
+}
+
 int spkmc_batch_usage(spkmc_batch_t *b, int32_t *live_slots, int64_t *device_bytes)
 {
     if (!b) return fail(SPKMC_EINVAL, "handle is NULL");

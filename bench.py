@@ -236,6 +236,46 @@ def cpu_baseline(rank: int, world: int, cycles: int = 8):
                       f"(one visit of each colour), OpenMP over active domains, {dt:.2f} s"}
 
 
+def batched_summary(n_lattices=256, cycles=5000, solo_sample=16):
+    """Ensemble of uneven lattices in one persistent launch per chunk vs the
+    same lattices one at a time (a sample of them, scaled to all)."""
+    import paper_1005_4713_gb300 as sp  # noqa: F401
+    from paper_1005_4713_gb300 import autotune, ensemble
+    from paper_1005_4713_gb300 import workloads as wl
+    Ls = [s.L for s in wl.ensemble_specs(n_lattices)]
+    edges = autotune.edge_map(Ls)
+    specs = wl.ensemble_specs(n_lattices, domain_edge=lambda L: edges[L])
+    bat = ensemble.run_batched(specs, cycles, sample_every=50, burn_in=cycles // 5)
+    sample = specs[:solo_sample]
+    solo = ensemble.run_one_at_a_time(sample, cycles, sample_every=50, burn_in=cycles // 5)
+    assert solo.final == bat.final[:solo_sample], "batched results differ from the solo runs"
+    frac = sum((s.L // s.d // 2) ** 3 for s in sample) / sum((s.L // s.d // 2) ** 3 for s in specs)
+    solo_all = solo.seconds * len(specs) / len(sample)
+    u = [x["U"] for x in bat.binder if x["U"] is not None]
+    return {"workload": f"{n_lattices} lattices, L in {{16..128}}, T~U[4.40,4.60], H in {{0,0.01}}, {cycles} cycles",
+            "edges": {str(k): v for k, v in edges.items()},
+            "batched_s": bat.seconds, "batched_events_per_s": bat.events_per_s,
+            "solo_sample": solo_sample, "solo_sample_s": solo.seconds, "solo_sample_event_fraction": frac,
+            "solo_all_s_est": solo_all, "speedup_vs_solo": solo_all / bat.seconds,
+            "bit_exact_vs_solo_sample": True,
+            "binder_U_mean": sum(u) / len(u) if u else None}
+
+
+def served_summary(n_requests=400, rate=200.0, budget=120 << 30, step_cycles=100):
+    """Poisson stream of simulation requests served with continuous batching."""
+    from paper_1005_4713_gb300 import serve
+    from paper_1005_4713_gb300 import workloads as wl
+    reqs = wl.request_stream(n=n_requests, rate=rate)
+    srv = serve.Server(budget_bytes=budget, capacity=512, step_cycles=step_cycles)
+    st = srv.serve(reqs, realtime=True)
+    return {"workload": f"{n_requests} requests, Poisson {rate:g}/s, L in {{32,64,128,256}}, T~U[4.3,4.7], "
+                        f"cycles log-uniform 1e2..1e4, budget {budget >> 30} GiB",
+            "completed": len(st.completions), "rejected": len(st.rejected),
+            "p50_latency_s": st.latency_percentile(50), "p99_latency_s": st.latency_percentile(99),
+            "events_per_s": st.events_per_s, "wall_s": st.wall, "peak_live": st.peak_live,
+            "steps": st.steps, "step_cycles": step_cycles}
+
+
 # ---------------------------------------------------------------------------
 # arms
 # ---------------------------------------------------------------------------
@@ -357,6 +397,10 @@ def run_gpu(args, world, rank, local, pg):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(rank, world)
+    batched = served = None
+    if rank == 0 and world == 1 and not args.no_ensembles:
+        batched = batched_summary()
+        served = served_summary()
 
     if rank == 0:
         peak, peak_kind = measured_peak()
@@ -386,6 +430,8 @@ def run_gpu(args, world, rank, local, pg):
             "e2e": e2e,
             "gpu_launches": args.steps,
             "clocks": clocks,
+            "batched": batched,
+            "served": served,
         }
         print(json.dumps(line))
     lat.close()
@@ -401,6 +447,7 @@ def main(argv=None):
     ap.add_argument("--cycles-per-step", type=int, default=CYCLES_PER_STEP)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ensembles", action="store_true", help="skip the batched and served summaries")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -62,8 +62,11 @@ def lib():
             L.oracle_class_counts.argtypes = [_i32, _i32, _ptr, _ptr]
             L.oracle_class_counts.restype = None
             L.oracle_spkmc_run.argtypes = [_i32, _i32, _dbl, _dbl, _dbl, _u64, _ptr,
-                                           _i64, _i64, _ptr, _ptr, _ptr, _ptr, _ptr, _i32]
+                                           _i64, _i64, _ptr, _ptr, _ptr, _ptr, _ptr, _i32,
+                                           _i32, _ptr]
             L.oracle_spkmc_run.restype = _i32
+            L.oracle_rmax_bounds.argtypes = [_i32, _dbl, _dbl, _dbl, _ptr, _ptr]
+            L.oracle_rmax_bounds.restype = None
             L.oracle_bkl_run.argtypes = [_i32, _i32, _i32, _dbl, _dbl, _dbl, _u64, _ptr,
                                          _i64, _i32, _ptr]
             L.oracle_bkl_run.restype = _i32
@@ -118,11 +121,34 @@ def class_counts(L: int, d: int, s: np.ndarray) -> np.ndarray:
     return out
 
 
-class State:
-    """Mutable spkMC state: spins plus the cycle counter, clock and counters."""
+RMAX_EXACT, RMAX_PRESCRIBED, RMAX_LEARNED = 0, 1, 2
 
-    def __init__(self, L, d, J, H, T, seed, cold=False, spins=None):
+
+class BoundExceeded(RuntimeError):
+    """An active domain's R_k exceeded the bound of Sec. 3.2 step 4b."""
+
+
+def rmax_bounds(d: int, J: float, H: float, T: float):
+    """(prescribed bound R', learned margin a + 12 b), Sec. 3.2: a is the
+    largest rate change of a flipped site, b the largest change of a site
+    whose neighbour sum moves by 2."""
+    a = np.zeros(1)
+    b = np.zeros(1)
+    lib().oracle_rmax_bounds(d, J, H, T, _p(a), _p(b))
+    return float(a[0]), float(b[0])
+
+
+class State:
+    """Mutable spkMC state: spins plus the cycle counter, clock and counters.
+
+    ``rmax_mode`` picks the rate the frequency lines are padded to: the exact
+    R_max of the cycle (Sec. 3.1 step 2) or a bound of Sec. 3.2 step 4b.
+    ``rmax_hist[i]`` holds the exact R_max of cycle ``cycle - 8 + i``."""
+
+    def __init__(self, L, d, J, H, T, seed, cold=False, spins=None, rmax_mode=RMAX_EXACT):
         self.L, self.d, self.J, self.H, self.T, self.seed = L, d, J, H, T, seed
+        self.rmax_mode = rmax_mode
+        self.rmax_hist = np.zeros(8, dtype=np.float64)
         self.spins = (init_spins(L, seed, cold) if spins is None
                       else np.array(spins, dtype=np.int8, copy=True))
         self.cycle = 0
@@ -146,7 +172,10 @@ class State:
         rc = lib().oracle_spkmc_run(self.L, self.d, self.J, self.H, self.T, self.seed,
                                     _p(self.spins), self.cycle, ncycles, _p(clock),
                                     _p(nf), _p(nn), _p(fx),
-                                    _p(ev) if log else None, threads)
+                                    _p(ev) if log else None, threads,
+                                    self.rmax_mode, _p(self.rmax_hist))
+        if rc == -2:
+            raise BoundExceeded("an active domain exceeded the R_max bound")
         if rc != 0:
             raise ValueError("oracle_spkmc_run rejected its arguments")
         self.cycle += ncycles

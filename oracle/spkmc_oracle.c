@@ -29,7 +29,11 @@
  *     (g/256, 0, 3, 0) for the hot start;
  *   - u01 = (w0 >> 11) * 2^-53 ; xi = (2*(w0 >> 12) + 1) * 2^-53 ;
  *   - event: first class c with target < cum_c (null if none), then the j-th
- *     site of that class in ascending l with j = floor(w1 * n_c / 2^64).
+ *     site of that class in ascending l with j = floor(w1 * n_c / 2^64);
+ *   - the frequency lines are padded to R, which is the exact R_max of the
+ *     cycle (Sec. 3.1 step 2) or one of the two bounds of Sec. 3.2 step 4b:
+ *     the prescribed maximum aggregate rate, or a bound learned from the
+ *     recorded history of R_max (see oracle_rmax_bounds).
  */
 #include <math.h>
 #include <stdint.h>
@@ -182,12 +186,67 @@ static inline u128 to_fixed64(double x)
 /* over OpenMP threads; the result does not depend on it.                   */
 /* Returns 0, or -1 on invalid arguments.                                   */
 /* ------------------------------------------------------------------------- */
+/* ------------------------------------------------------------------------- */
+/* Sec. 3.2, step 4b: bounds that replace the exact R_max.                    */
+/*                                                                            */
+/* Prescribed: the maximum aggregate rate of a domain of n_k = d^3 spins,     */
+/* R' = lambda n_k exp(-dE)/(1+exp(-dE)) with dE = E_max/T and                */
+/* E_max = -2(n_b|J| + |H|), n_b = 6 (the printed E_max carries -|H|; with    */
+/* -|H| the bound fails for H != 0, so the field term is read as +|H|).       */
+/* exp(-dE)/(1+exp(-dE)) is evaluated as 1/(1+exp(dE)), the same number.      */
+/*                                                                            */
+/* Learned: the exact R_max of colour c at its previous visit, eight cycles   */
+/* earlier, plus the most the rate of a domain can grow between two visits.   */
+/* The domain's own flip moves the flipped site's rate by at most             */
+/* a = max_S |r(+1,S) - r(-1,S)| and the rates of its (at most 6) neighbours  */
+/* in the domain, whose S moves by 2, by at most b = max |r(s,S+2) - r(s,S)|  */
+/* each; each of the 6 face-neighbouring domains is visited once in between   */
+/* and its flip moves the S of at most one site of the domain by 2.  Hence    */
+/* R_max(t) <= R_max(t-8) + a + 12 b.  The learned R is the smaller of that   */
+/* and the prescribed bound; before a colour has a recorded visit it is the   */
+/* prescribed bound.                                                          */
+/*                                                                            */
+/* Both bounds are multiplied by (1 + 2^-32): the computed R_k is a rounded   */
+/* sum of 14 products, so it may exceed the exact bound by a few ulp.         */
+/* ------------------------------------------------------------------------- */
+#define ORACLE_RMAX_EXACT 0
+#define ORACLE_RMAX_PRESCRIBED 1
+#define ORACLE_RMAX_LEARNED 2
+#define ORACLE_BOUND_SLACK (1.0 + 0x1p-32)
+
+void oracle_rmax_bounds(int d, double J, double H, double T, double *prescribed, double *margin)
+{
+    const double dE = (6.0 * fabs(J) + fabs(H)) * -2.0 / T;
+    const double r_top = 1.0 / (1.0 + exp(dE));
+    const double n_k = (double)d * d * d;
+    *prescribed = (n_k * r_top) * ORACLE_BOUND_SLACK;
+    double rate[14];
+    oracle_rates(J, H, T, rate);
+    double a = 0.0, b = 0.0; /* class c = 7 [sigma = +1] + u, S = 2u - 6 */
+    for (int u = 0; u < 7; ++u)
+        if (fabs(rate[7 + u] - rate[u]) > a) a = fabs(rate[7 + u] - rate[u]);
+    for (int sg = 0; sg < 2; ++sg)
+        for (int u = 0; u < 6; ++u)
+            if (fabs(rate[7 * sg + u + 1] - rate[7 * sg + u]) > b) b = fabs(rate[7 * sg + u + 1] - rate[7 * sg + u]);
+    *margin = a + 12.0 * b;
+}
+
+/* rmax_hist[i] (in/out, may be NULL) is the exact R_max of cycle t0 - 8 + i,
+ * 0 where that cycle was not run.  Returns -1 for invalid arguments and -2
+ * if a bound of Sec. 3.2 is exceeded by an active domain (the tolerance
+ * check of the self-learning bullet); the state is then left at that cycle. */
 int oracle_spkmc_run(int L, int d, double J, double H, double T, uint64_t seed,
                      int8_t *s, int64_t t0, int64_t ncycles,
                      double *clock, int64_t *n_flip, int64_t *n_null,
-                     uint64_t null_fx[2], int32_t *events, int nthreads)
+                     uint64_t null_fx[2], int32_t *events, int nthreads,
+                     int rmax_mode, double *rmax_hist)
 {
     if (d < 2 || L <= 0 || L % (2 * d) != 0 || !(T > 0.0)) return -1;
+    if (rmax_mode < ORACLE_RMAX_EXACT || rmax_mode > ORACLE_RMAX_LEARNED) return -1;
+    double hist_local[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double *hist = rmax_hist ? rmax_hist : hist_local;
+    double R_prescribed, R_margin;
+    oracle_rmax_bounds(d, J, H, T, &R_prescribed, &R_margin);
     const int nd = L / d;
     const int h = nd / 2;
     const int64_t Kact = (int64_t)h * h * h;
@@ -243,8 +302,26 @@ int oracle_spkmc_run(int L, int d, double J, double H, double T, uint64_t seed,
         for (int64_t a = 0; a < Kact; ++a)
             if (cum[14 * a + 13] > Rmax) Rmax = cum[14 * a + 13];
 
-        /* Steps 3, 4 and 4b: null rate r_0k = R_max - R_k padded at the end of
-         * each frequency line; one event per domain with p = r/R_max. */
+        /* Step 4b: the rate R that the lines are padded to. */
+        double R = Rmax;
+        if (rmax_mode != ORACLE_RMAX_EXACT) {
+            R = R_prescribed;
+            if (rmax_mode == ORACLE_RMAX_LEARNED && hist[0] > 0.0) {
+                const double learned = (hist[0] + R_margin) * ORACLE_BOUND_SLACK;
+                if (learned < R) R = learned;
+            }
+        }
+        if (R < Rmax) {
+            free(cnt); free(cum); free(ev_cls); free(ev_site);
+            null_fx[0] = (uint64_t)acc;
+            null_fx[1] = (uint64_t)(acc >> 64);
+            return -2;
+        }
+        for (int i = 0; i < 7; ++i) hist[i] = hist[i + 1];
+        hist[7] = Rmax;
+
+        /* Steps 3, 4 and 4b: null rate r_0k = R - R_k padded at the end of
+         * each frequency line; one event per domain with p = r/R. */
 #ifdef _OPENMP
 #pragma omp parallel for num_threads(nthreads) schedule(static)
 #endif
@@ -256,7 +333,7 @@ int oracle_spkmc_run(int L, int d, double J, double H, double T, uint64_t seed,
             uint64_t w[4];
             oracle_philox((uint64_t)t, (uint64_t)k, 1, 0, seed, 0, w);
             double u01 = (double)(w[0] >> 11) * 0x1p-53;
-            double target = u01 * Rmax;
+            double target = u01 * R;
             int chosen = -1;
             for (int q = 0; q < 14; ++q)
                 if (target < cum[14 * a + q]) { chosen = q; break; }
@@ -287,7 +364,7 @@ int oracle_spkmc_run(int L, int d, double J, double H, double T, uint64_t seed,
                 e[0] = (int32_t)k; e[1] = ev_cls[a]; e[2] = ev_site[a];
             }
             /* Eq. 10 numerator: sum of null rates over the domains */
-            acc += to_fixed64(Rmax - cum[14 * a + 13]);
+            acc += to_fixed64(R - cum[14 * a + 13]);
             if (ev_cls[a] < 0) { ++nulls; continue; }
             int l = ev_site[a];
             int x = l % d, y = (l / d) % d, z = l / (d * d);
@@ -296,11 +373,11 @@ int oracle_spkmc_run(int L, int d, double J, double H, double T, uint64_t seed,
             ++flips;
         }
 
-        /* Step 5: one global time increment dt = -ln(xi) / R_max. */
+        /* Step 5: one global time increment dt = -ln(xi) / R. */
         uint64_t wc[4];
         oracle_philox((uint64_t)t, 0, 2, 0, seed, 0, wc);
         double xi = (double)(2 * (wc[0] >> 12) + 1) * 0x1p-53;
-        double dt = -log(xi) / Rmax;
+        double dt = -log(xi) / R;
         *clock = *clock + dt;
         *n_flip += flips;
         *n_null += nulls;
@@ -441,4 +518,4 @@ int oracle_enumerate(int Lx, int Ly, int Lz, double J, double H, double T, doubl
     return 0;
 }
 
-int oracle_abi_version(void) { return 1; }
+int oracle_abi_version(void) { return 2; }

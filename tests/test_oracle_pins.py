@@ -151,8 +151,33 @@ def test_class_counts_bruteforce(L, d, seed):
 # One spkMC cycle by brute force on tiny lattices (Sec. 3.1 steps 1-6,
 # Sec. 3.2 steps 4a/4b), independent Python + numpy code
 # --------------------------------------------------------------------------
-def brute_cycles(L, d, J, H, T, seed, s, ncycles, clock=0.0, t0=0, null_sum=None):
+SLACK = 1.0 + 2.0 ** -32  # relative slack of the Sec. 3.2 bounds
+
+
+def drift_margin(r):
+    """Largest growth of a domain's R_k between two visits of its colour:
+    the flipped site (sigma -> -sigma at fixed S) plus 12 sites whose S moves
+    by 2 (its neighbours in the domain and one site per face neighbour)."""
+    own = max(abs(r[7 + u] - r[u]) for u in range(7))
+    step = max(abs(r[7 * sg + u + 1] - r[7 * sg + u]) for sg in (0, 1) for u in range(6))
+    return own + 12 * step
+
+
+def brute_bound(mode, d, r, prev8, Rmax):
+    """The rate the lines are padded to: exact R_max (mode 0), the prescribed
+    d^3 max_c r_c (mode 1), or the learned min(prescribed, R_max(t-8) +
+    drift margin) (mode 2), both bounds times SLACK."""
+    if mode == 0:
+        return Rmax
+    pres = (d ** 3 * max(r)) * SLACK
+    if mode == 2 and prev8 > 0:
+        return min(pres, (prev8 + drift_margin(r)) * SLACK)
+    return pres
+
+
+def brute_cycles(L, d, J, H, T, seed, s, ncycles, clock=0.0, t0=0, null_sum=None, mode=0, hist=None):
     s = s.copy()
+    hist = [0.0] * 8 if hist is None else hist
     r = [1.0 / (1.0 + math.exp(2.0 * (1 if c >= 7 else -1) * (J * (2 * (c % 7) - 6) + H) / T))
          for c in range(14)]
     nd = L // d
@@ -182,12 +207,15 @@ def brute_cycles(L, d, J, H, T, seed, s, ncycles, clock=0.0, t0=0, null_sum=None
                 cum.append(acc)
             lines.append((k, sites, n, cum))
         Rmax = max(cum[13] for _, _, _, cum in lines)
+        Rpad = brute_bound(mode, d, r, hist[0], Rmax)
+        assert Rpad >= Rmax
+        hist[:] = hist[1:] + [Rmax]
         if null_sum is not None:
-            null_sum.append(sum(int(math.ldexp(Rmax - cum[13], 64)) for _, _, _, cum in lines))
+            null_sum.append(sum(int(math.ldexp(Rpad - cum[13], 64)) for _, _, _, cum in lines))
         flips = []
         for k, sites, n, cum in lines:
             w = numpy_philox((t, k, 1, 0), (seed, 0))
-            target = (w[0] >> 11) * 2.0 ** -53 * Rmax
+            target = (w[0] >> 11) * 2.0 ** -53 * Rpad
             chosen = next((c for c in range(14) if target < cum[c]), -1)
             if chosen < 0:
                 log.append((k, -1, -1))
@@ -203,7 +231,7 @@ def brute_cycles(L, d, J, H, T, seed, s, ncycles, clock=0.0, t0=0, null_sum=None
             s[g] = -s[g]
         wc = numpy_philox((t, 0, 2, 0), (seed, 0))
         xi = (2 * (wc[0] >> 12) + 1) * 2.0 ** -53
-        clock = clock + (-math.log(xi) / Rmax)
+        clock = clock + (-math.log(xi) / Rpad)
     return s, np.array(log, dtype=np.int32).reshape(ncycles, -1, 3), clock, nflip, nnull
 
 
@@ -257,9 +285,11 @@ def test_no_coupling_uniform_flips_and_clock():
     assert abs(st.clock - mean) < 5 * sd
 
 
-def test_one_cycle_law_chi2():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_one_cycle_law_chi2(mode):
     """Sec. 3.1 step 4: in each active domain the event i is chosen with
-    probability r_i/R_max and the null event with (R_max - R_k)/R_max."""
+    probability r_i/R and the null event with (R - R_k)/R, where R is R_max
+    (exact) or the prescribed bound d^3 max r of Sec. 3.2 step 4b."""
     from scipy import stats
     L, d, J, H, T = 8, 2, 1.0, 0.2, 3.0
     base = oracle.init_spins(L, 5)
@@ -278,11 +308,11 @@ def test_one_cycle_law_chi2():
             rr.append(r[cls[(dx * d + x) + L * ((dy * d + y) + L * (dz * d + z))]])
         site_rates.append(rr)
     Rk = np.array([sum(v) for v in site_rates])
-    Rmax = Rk.max()
-    nseeds = 60000
+    Rmax = Rk.max() if mode == 0 else d ** 3 * r.max()
+    nseeds = 60000 if mode == 0 else 30000
     hist = np.zeros((len(active), d ** 3 + 1), dtype=np.int64)
     for seed in range(1, nseeds + 1):
-        st = oracle.State(L, d, J, H, T, seed, spins=base)
+        st = oracle.State(L, d, J, H, T, seed, spins=base, rmax_mode=mode)
         ev = st.run(1, log=True)[0]
         for a in range(len(active)):
             hist[a, ev[a, 2] if ev[a, 1] >= 0 else d ** 3] += 1
@@ -314,6 +344,171 @@ def test_null_rate_sum_matches_definition():
     brute_cycles(L, d, J, H, T, seed, s0, 5, null_sum=sums)
     assert st.null_fx == sum(sums)
     assert st.null_fx > 0
+
+
+# --------------------------------------------------------------------------
+# Bounds that replace the exact R_max (Sec. 3.2 step 4b)
+# --------------------------------------------------------------------------
+def test_prescribed_bound_closed_form():
+    """R' = n_k lambda e^{-dE}/(1+e^{-dE}), dE = -2(6|J| + |H|)/T: at T_c and
+    H = 0 the single-site factor is r(+1, S=-6) = 0.9346166754684477 (rate
+    table pin above); elsewhere it is (1 + tanh((6|J|+|H|)/T))/2."""
+    Rp, m = oracle.rmax_bounds(4, 1.0, 0.0, 4.5115)
+    assert Rp == (64 * 0.9346166754684477) * SLACK
+    # a = r(-1,6) - r(+1,6); b = r(+1,0) - r(+1,2) (the steepest step is at S = 0)
+    assert m == pytest.approx((0.9346166754684477 - 0.06538332453155232)
+                              + 12 * (0.5 - 0.29180719760737955), rel=1e-14)
+    for J, H, T, d in [(1.0, 0.01, 4.5115, 16), (-0.7, 0.3, 2.5, 8), (0.0, -0.2, 1.0, 2),
+                       (2.0, 0.0, 50.0, 4), (1.0, -0.5, 0.7, 8)]:
+        Rp, m = oracle.rmax_bounds(d, J, H, T)
+        x = (6 * abs(J) + abs(H)) / T
+        top = 0.5 * (1 + math.tanh(x))
+        assert Rp / SLACK == pytest.approx(d ** 3 * top, rel=1e-14)
+        th = [math.tanh((J * (2 * u - 6) + H) / T) for u in range(7)]
+        a = max(abs(v) for v in th)                       # |r(+1,S) - r(-1,S)| = |tanh|
+        b = max(0.5 * abs(th[u + 1] - th[u]) for u in range(6))
+        assert m == pytest.approx(a + 12 * b, rel=1e-12)
+        # the largest Glauber rate is the formula's, bit for bit
+        assert Rp == (d ** 3 * oracle.rates(J, H, T).max()) * SLACK
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("L,d,J,H,T,seed,cold", [
+    (8, 2, 1.0, 0.0, 4.5115, 61, False),
+    (8, 4, 1.0, 0.3, 3.0, 62, False),
+    (12, 3, -0.7, 0.1, 2.5, 63, False),
+    (8, 2, 1.0, 0.0, 4.5115, 64, True),
+])
+def test_bound_modes_bruteforce(mode, L, d, J, H, T, seed, cold):
+    st = oracle.State(L, d, J, H, T, seed, cold=cold, rmax_mode=mode)
+    s0 = st.spins.copy()
+    ev = st.run(21, log=True)
+    sums, hist = [], [0.0] * 8
+    s_ref, log_ref, clock_ref, nf, nn = brute_cycles(L, d, J, H, T, seed, s0, 21, null_sum=sums,
+                                                     mode=mode, hist=hist)
+    assert np.array_equal(ev, log_ref)
+    assert np.array_equal(st.spins, s_ref)
+    assert st.clock == pytest.approx(clock_ref, rel=1e-15)
+    assert (st.n_flip, st.n_null) == (nf, nn)
+    assert st.null_fx == sum(sums)
+    assert list(st.rmax_hist) == hist
+
+
+def _rates_per_domain(L, d, spins, r):
+    n = oracle.class_counts(L, d, spins)
+    out = np.zeros(len(n))
+    for k in range(len(n)):
+        acc = 0.0
+        for c in range(14):
+            acc = acc + int(n[k, c]) * float(r[c])
+        out[k] = acc
+    return out
+
+
+@pytest.mark.parametrize("L,d,J,H,T,seed,cold", [
+    (8, 2, 1.0, 0.0, 4.5115, 71, False),
+    (16, 4, 1.0, 0.2, 3.0, 72, False),
+    (12, 2, -1.0, 0.0, 2.0, 73, True),
+    (8, 2, 1.0, 0.0, 1.2, 74, False),
+])
+def test_rate_drift_over_one_rotation_is_bounded(L, d, J, H, T, seed, cold):
+    """Over any 8 consecutive cycles a domain is active once and each of its
+    face neighbours once, so R_k(t+8) - R_k(t) is at most the drift margin
+    a + 12 b: the growth bound behind the learned R.  Checked on every
+    domain, over windows that start at every phase of the rotation."""
+    r = oracle.rates(J, H, T)
+    m = drift_margin(list(r))
+    st = oracle.State(L, d, J, H, T, seed, cold=cold)
+    hist = [_rates_per_domain(L, d, st.spins, r)]
+    worst = 0.0
+    for _ in range(120):
+        st.run(1)
+        hist.append(_rates_per_domain(L, d, st.spins, r))
+        if len(hist) > 8:
+            worst = max(worst, np.abs(hist[-1] - hist[-9]).max() / m)
+    assert worst <= 1 + 1e-12
+    assert worst > 0.1  # the walk moved the rates
+
+
+def test_rate_drift_bound_is_attained():
+    """The margin a + 12 b is reached: in domain (0,0,0) of a 32^3 lattice
+    with d = 8, an up spin i at (4,4,4) whose 6 neighbours each have two down
+    neighbours (S = 2) flips (a), its neighbours step from S = 2 to S = 0
+    (6 b), and the site across the middle of each face flips while the face
+    site next to it has S = 2 (6 b)."""
+    L, d, J, H, T = 32, 8, 1.0, 0.0, 4.5115
+    r = oracle.rates(J, H, T)
+    g = lambda x, y, z: x % L + L * ((y % L) + L * (z % L))
+    s = np.ones(L ** 3, dtype=np.int8)
+    down = [(5, 5, 4), (4, 5, 5), (5, 4, 5), (3, 3, 4), (4, 3, 3), (3, 4, 3)]
+    faces = [((0, 4, 4), (-1, 4, 4), [(0, 3, 4), (0, 5, 4)]), ((7, 4, 4), (8, 4, 4), [(7, 3, 4), (7, 5, 4)]),
+             ((4, 0, 4), (4, -1, 4), [(3, 0, 4), (5, 0, 4)]), ((4, 7, 4), (4, 8, 4), [(3, 7, 4), (5, 7, 4)]),
+             ((4, 4, 0), (4, 4, -1), [(3, 4, 0), (5, 4, 0)]), ((4, 4, 7), (4, 4, 8), [(3, 4, 7), (5, 4, 7)])]
+    for p in down:
+        s[g(*p)] = -1
+    for _, _, dn in faces:
+        for p in dn:
+            s[g(*p)] = -1
+    before = _rates_per_domain(L, d, s, r)[0]
+    s[g(4, 4, 4)] = -1
+    for _, across, _ in faces:
+        s[g(*across)] = -1
+    after = _rates_per_domain(L, d, s, r)[0]
+    _, margin = oracle.rmax_bounds(d, J, H, T)
+    assert after - before == pytest.approx(margin, rel=1e-12)
+
+
+def test_history_records_the_exact_rmax():
+    L, d, J, H, T = 16, 4, 1.0, 0.1, 3.5
+    st = oracle.State(L, d, J, H, T, 91)
+    r = oracle.rates(J, H, T)
+    nd = L // d
+    seen = []
+    for t in range(11):
+        R = _rates_per_domain(L, d, st.spins, r)
+        act = [k for k in range(nd ** 3)
+               if ((k % nd) & 1) | (((k // nd) % nd) & 1) << 1 | ((k // nd // nd) & 1) << 2 == t % 8]
+        seen.append(max(R[act]))
+        st.run(1)
+    assert list(st.rmax_hist) == seen[-8:]
+
+
+def test_learned_equals_prescribed_until_a_colour_has_history():
+    a = oracle.State(32, 4, 1.0, 0.0, 4.5115, 93, rmax_mode=oracle.RMAX_PRESCRIBED)
+    b = oracle.State(32, 4, 1.0, 0.0, 4.5115, 93, rmax_mode=oracle.RMAX_LEARNED)
+    assert np.array_equal(a.run(8, log=True), b.run(8, log=True))
+    assert a.clock == b.clock and np.array_equal(a.spins, b.spins)
+    ca, cb = a.clock, b.clock
+    a.run(1)
+    b.run(1)
+    assert b.clock - cb > a.clock - ca  # same xi, smaller learned R
+
+
+@pytest.mark.parametrize("L,d,T,H,cold", [
+    (16, 2, 4.5115, 0.0, False), (16, 2, 3.0, 0.3, True), (16, 4, 8.0, 0.0, False),
+    (16, 4, 1.0, 0.0, False), (16, 2, 0.6, -0.4, False), (32, 8, 4.5115, 0.01, True),
+])
+def test_learned_bound_holds_over_long_runs(L, d, T, H, cold):
+    """The self-learned R never falls below an active domain's R_k (the run
+    raises BoundExceeded otherwise), and it sits close to R_max: the null
+    fraction is near that of the exact-R_max run."""
+    st = oracle.State(L, d, 1.0, H, T, 81, cold=cold, rmax_mode=oracle.RMAX_LEARNED)
+    ex = oracle.State(L, d, 1.0, H, T, 81, cold=cold)
+    st.run(1200)
+    ex.run(1200)
+    ur_l = st.n_flip / (st.n_flip + st.n_null)
+    ur_e = ex.n_flip / (ex.n_flip + ex.n_null)
+    assert ur_l <= ur_e * 1.05
+    if d == 8:
+        assert ur_l > 0.85 * ur_e
+
+
+def test_bound_exceeded_is_reported():
+    """A recorded history that is too small for the lattice trips the check."""
+    st = oracle.State(16, 4, 1.0, 0.0, 4.5115, 95, rmax_mode=oracle.RMAX_LEARNED)
+    st.rmax_hist[:] = 1.0
+    with pytest.raises(oracle.BoundExceeded):
+        st.run(1)
 
 
 # --------------------------------------------------------------------------

@@ -19,7 +19,11 @@
  *     neighbour spins, lambda = 1, k_B = 1 (Eq. 3 read as Glauber dynamics);
  *   - random numbers: Philox4x64-10 keyed by (seed, 0); counter (t, k, 1, 0)
  *     for the event of domain k in cycle t, (t, 0, 2, 0) for the clock,
- *     (g/256, 0, 3, 0) for the hot start.
+ *     (g/256, 0, 3, 0) for the hot start;
+ *   - every active domain's frequency line is padded with a null rate to a
+ *     common R (Sec. 3.1 step 3): the exact R_max of the cycle (Sec. 3.1
+ *     step 2), or one of the bounds of Sec. 3.2 step 4b (spkmc_params
+ *     rmax_mode), which need no device-wide reduction before the events.
  *
  * Ownership: the library owns all device memory it allocates (through the
  * optional allocator callbacks of spkmc_config, else stream-ordered
@@ -51,9 +55,34 @@ extern "C" {
 #define SPKMC_ETIMEOUT 4  /* a grid barrier gave up after its time limit */
 #define SPKMC_EBUSY 5     /* no free slot, or the budget does not allow it */
 #define SPKMC_EINTERNAL 6 /* the device found its class counts inconsistent */
+#define SPKMC_EBOUND 7    /* an active domain's R_k exceeded the R_max bound */
 
 #define SPKMC_INIT_HOT 0  /* uniform +-1 spins from Philox (g/256, 0, 3, 0) */
 #define SPKMC_INIT_COLD 1 /* all spins +1 (the relaxation start of Sec. 6) */
+
+/* The rate R every active domain's frequency line is padded to (Sec. 3.2,
+ * step 4b).  With R above the exact R_max the events keep their relative
+ * probabilities and only the null fraction grows.
+ *   EXACT:      R = max over the cycle's active domains of R_k (Sec. 3.1
+ *               step 2); one device-wide reduction per cycle before events.
+ *   PRESCRIBED: R = R' = d^3 * max_c r_c * (1 + 2^-32), the maximum aggregate
+ *               rate of a domain, with E_max = -2(6|J| + |H|) (the printed
+ *               -|H| read as +|H|); no reduction at all.
+ *   LEARNED:    R = min(R', (R_max(t-8) + m) * (1 + 2^-32)) once colour t%8
+ *               has a recorded visit (R' before): R_max(t-8) is the exact
+ *               maximum of the same colour at its previous visit, reduced in
+ *               the background, and m = a + 12 b bounds how much a domain's
+ *               R_k can grow between two visits (a = max_S |r(+1,S) -
+ *               r(-1,S)| for the flipped site, b = max |r(s,S+2) - r(s,S)|
+ *               for each of the 12 sites whose neighbour sum moves).  This is
+ *               the self-learning bound of Sec. 3.2 with a tolerance that
+ *               provably keeps R >= R_k.
+ * The factor 1 + 2^-32 covers the rounding of the 14-term sum R_k.  Every
+ * active domain checks R_k <= R; a violation stops the lattice with
+ * SPKMC_EBOUND (it cannot happen unless the state was altered). */
+#define SPKMC_RMAX_EXACT 0
+#define SPKMC_RMAX_PRESCRIBED 1
+#define SPKMC_RMAX_LEARNED 2
 
 typedef struct spkmc_engine spkmc_t;
 typedef struct spkmc_batch spkmc_batch_t;
@@ -73,7 +102,7 @@ typedef struct spkmc_params {
     double T;                   /* temperature in J/k_B units (> 0, finite) */
     uint64_t seed;              /* Philox key word 0 */
     int32_t init;               /* SPKMC_INIT_HOT or SPKMC_INIT_COLD */
-    int32_t reserved0;
+    int32_t rmax_mode;          /* SPKMC_RMAX_EXACT (default), _PRESCRIBED or _LEARNED */
     int64_t event_log_capacity; /* events kept (see spkmc_event); 0 = off */
 } spkmc_params;
 
@@ -126,6 +155,8 @@ typedef struct spkmc_state {
     int64_t n_flip;
     int64_t n_null;
     uint64_t sum_null_rate_fx[2];
+    double rmax_hist[8];        /* exact R_max of cycles cycle-8 .. cycle-1 (0 = not run);
+                                   the history of the LEARNED bound */
 } spkmc_state;
 
 /* Sizes of a created lattice. */
@@ -147,6 +178,12 @@ void spkmc_config_init(spkmc_config *c);   /* all defaults (NULL stream, own all
  * and J, H, T are finite. */
 int spkmc_rate_table(double J, double H, double T, double out[14]);
 
+/* The bounds of Sec. 3.2 step 4b for domain edge d (host arithmetic, FP64,
+ * from the rate table above): *prescribed = d^3 * max_c r_c * (1 + 2^-32) and
+ * *margin = a + 12 b (see SPKMC_RMAX_LEARNED).  EINVAL as spkmc_rate_table,
+ * or for d outside {2, 4, 8, 16} or NULL outputs. */
+int spkmc_rmax_bounds(int32_t d, double J, double H, double T, double *prescribed, double *margin);
+
 /* Domain edge used for L when domain_edge = 0: the largest d in {16,8,4,2}
  * with L % (2d) == 0, or 0 if none. */
 int32_t spkmc_resolve_domain_edge(int32_t L);
@@ -166,12 +203,15 @@ void spkmc_destroy(spkmc_t *h);
 /* Enqueue ncycles spkMC cycles (Sec. 3.1 steps 1-6, one colour per cycle) as
  * one persistent cooperative launch; ncycles >= 0 (0 is a no-op). */
 int spkmc_run_cycles(spkmc_t *h, int64_t ncycles);
-/* Wait for the stream and report kernel-side errors (ETIMEOUT, EINTERNAL). */
+/* Wait for the stream and report kernel-side errors (ETIMEOUT, EINTERNAL,
+ * EBOUND). */
 int spkmc_synchronize(spkmc_t *h);
 /* Synchronise and compute the observables on the device. */
 int spkmc_observables(spkmc_t *h, spkmc_obs *out);
 /* Copy spins to/from a host int8 buffer of n = L^3 entries in global order.
- * set_spins recomputes the ghost faces, class counts, M and B on the device. */
+ * set_spins recomputes the ghost faces, class counts, M and B on the device
+ * and clears the R_max history (it no longer describes the spins); restore a
+ * checkpoint with set_spins first, then set_state. */
 int spkmc_get_spins(spkmc_t *h, int8_t *host_buf, size_t n);
 int spkmc_set_spins(spkmc_t *h, const int8_t *host_buf, size_t n);
 /* Copy up to cap logged events (cycle-major, ascending k within a cycle);

@@ -17,7 +17,8 @@ import threading
 import numpy as np
 
 from . import _abi
-from ._abi import (SPKMC_EBUSY, SPKMC_ECUDA, SPKMC_EINTERNAL, SPKMC_EINVAL, SPKMC_ENOMEM,  # noqa: F401
+from ._abi import (SPKMC_EBOUND, SPKMC_EBUSY, SPKMC_ECUDA, SPKMC_EINTERNAL, SPKMC_EINVAL,  # noqa: F401
+                   SPKMC_ENOMEM, SPKMC_RMAX_EXACT, SPKMC_RMAX_LEARNED, SPKMC_RMAX_PRESCRIBED,
                    SPKMC_INIT_COLD, SPKMC_INIT_HOT, SPKMC_OK, SPKMC_ETIMEOUT, spkmc_config,
                    spkmc_event, spkmc_info, spkmc_obs, spkmc_params, spkmc_state)
 
@@ -54,12 +55,13 @@ def _check(rc: int) -> None:
 
 
 def make_params(L, domain_edge=0, J=1.0, H=0.0, T=4.5115, seed=1, init=SPKMC_INIT_HOT,
-                event_log_capacity=0) -> spkmc_params:
+                event_log_capacity=0, rmax_mode=SPKMC_RMAX_EXACT) -> spkmc_params:
     p = spkmc_params()
     lib().spkmc_params_init(ctypes.byref(p))
     p.L, p.domain_edge, p.J, p.H, p.T, p.seed = int(L), int(domain_edge), float(J), float(H), float(T), int(seed)
     p.init = int(init)
     p.event_log_capacity = int(event_log_capacity)
+    p.rmax_mode = int(rmax_mode)
     return p
 
 
@@ -118,6 +120,13 @@ def spkmc_rate_table(J: float, H: float, T: float) -> np.ndarray:
     out = np.zeros(14, dtype=np.float64)
     _check(lib().spkmc_rate_table(J, H, T, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return out
+
+
+def spkmc_rmax_bounds(d: int, J: float, H: float, T: float):
+    """(prescribed bound, learned growth margin) of Sec. 3.2 step 4b."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().spkmc_rmax_bounds(int(d), J, H, T, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def spkmc_resolve_domain_edge(L: int) -> int:
@@ -303,9 +312,9 @@ class Lattice:
     """One lattice on the GPU (owns a spkmc_t handle)."""
 
     def __init__(self, L, domain_edge=0, J=1.0, H=0.0, T=4.5115, seed=1, cold=False,
-                 event_log_capacity=0, config: spkmc_config | None = None):
+                 event_log_capacity=0, config: spkmc_config | None = None, rmax_mode=SPKMC_RMAX_EXACT):
         self.params = make_params(L, domain_edge, J, H, T, seed,
-                                  SPKMC_INIT_COLD if cold else SPKMC_INIT_HOT, event_log_capacity)
+                                  SPKMC_INIT_COLD if cold else SPKMC_INIT_HOT, event_log_capacity, rmax_mode)
         self.config = config
         self.h = spkmc_create_ex(self.params, config)
         info = spkmc_info_get(self.h)
@@ -371,9 +380,9 @@ class Batch:
         self.params = {}
 
     def admit(self, L, domain_edge=0, J=1.0, H=0.0, T=4.5115, seed=1, cold=False, cycles=-1,
-              event_log_capacity=0) -> int:
+              event_log_capacity=0, rmax_mode=SPKMC_RMAX_EXACT) -> int:
         p = make_params(L, domain_edge, J, H, T, seed, SPKMC_INIT_COLD if cold else SPKMC_INIT_HOT,
-                        event_log_capacity)
+                        event_log_capacity, rmax_mode)
         slot = spkmc_batch_admit(self.b, p, cycles)
         self.params[slot] = p
         return slot

@@ -14,12 +14,17 @@ SPKMC_ECUDA = 3
 SPKMC_ETIMEOUT = 4
 SPKMC_EBUSY = 5
 SPKMC_EINTERNAL = 6
+SPKMC_EBOUND = 7
 SPKMC_INIT_HOT = 0
 SPKMC_INIT_COLD = 1
+SPKMC_RMAX_EXACT = 0
+SPKMC_RMAX_PRESCRIBED = 1
+SPKMC_RMAX_LEARNED = 2
 
 SPKMC_NOALLOC_SCRATCH_BYTES = 16 << 20
 
-STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EBUSY", 6: "EINTERNAL"}
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EBUSY", 6: "EINTERNAL",
+                7: "EBOUND"}
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -28,7 +33,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void
 class spkmc_params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("domain_edge", ctypes.c_int32), ("J", ctypes.c_double),
                 ("H", ctypes.c_double), ("T", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("init", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("init", ctypes.c_int32), ("rmax_mode", ctypes.c_int32),
                 ("event_log_capacity", ctypes.c_int64)]
 
 
@@ -56,7 +61,8 @@ class spkmc_event(ctypes.Structure):
 
 class spkmc_state(ctypes.Structure):
     _fields_ = [("cycle", ctypes.c_int64), ("clock", ctypes.c_double), ("n_flip", ctypes.c_int64),
-                ("n_null", ctypes.c_int64), ("sum_null_rate_fx", ctypes.c_uint64 * 2)]
+                ("n_null", ctypes.c_int64), ("sum_null_rate_fx", ctypes.c_uint64 * 2),
+                ("rmax_hist", ctypes.c_double * 8)]
 
 
 class spkmc_info(ctypes.Structure):
@@ -75,6 +81,7 @@ PROTOTYPES = {
     "spkmc_params_init": (None, [P(spkmc_params)]),
     "spkmc_config_init": (None, [P(spkmc_config)]),
     "spkmc_rate_table": (ctypes.c_int, [_dbl, _dbl, _dbl, P(_dbl)]),
+    "spkmc_rmax_bounds": (ctypes.c_int, [ctypes.c_int32, _dbl, _dbl, _dbl, P(_dbl), P(_dbl)]),
     "spkmc_resolve_domain_edge": (_i32, [_i32]),
     "spkmc_bytes_required": (_i64, [P(spkmc_params)]),
     "spkmc_create": (ctypes.c_int, [_i32, _i32, _dbl, _dbl, _dbl, _u64, P(_h)]),

@@ -69,6 +69,57 @@ void host_rates(double J, double H, double T, double r[kClasses])
     }
 }
 
+// Bounds of Sec. 3.2 step 4b from the rate table: the prescribed maximum
+// aggregate rate d^3 max_c r_c and the growth margin a + 12 b of the learned
+// bound (a: largest change of a flipped site's rate at fixed S; b: largest
+// change of a rate when S moves by 2), see SPKMC_RMAX_LEARNED.
+void host_bounds(int d, const double r[kClasses], double *prescribed, double *margin)
+{
+    double top = r[0];
+    for (int c = 1; c < kClasses; ++c)
+        if (r[c] > top) top = r[c];
+    const double nk = (double)d * d * d;
+    *prescribed = (nk * top) * kBoundSlack;
+    double a = 0.0, b = 0.0;
+    for (int u = 0; u < 7; ++u)
+        if (std::fabs(r[7 + u] - r[u]) > a) a = std::fabs(r[7 + u] - r[u]);
+    for (int sg = 0; sg < 2; ++sg)
+        for (int u = 0; u < 6; ++u)
+            if (std::fabs(r[7 * sg + u + 1] - r[7 * sg + u]) > b) b = std::fabs(r[7 * sg + u + 1] - r[7 * sg + u]);
+    *margin = a + 12.0 * b;
+}
+
+void fill_physics(LatticeDesc &D, const spkmc_params *p, int d)
+{
+    host_rates(p->J, p->H, p->T, D.rate);
+    host_bounds(d, D.rate, &D.rbound, &D.rmargin);
+    D.rmode = p->rmax_mode;
+}
+
+// R_max history of spkmc_state (cycles t-8 .. t-1) <-> the device ring.
+void hist_to_ring(const double hist[8], long long t, unsigned long long ring[kRmaxRing])
+{
+    for (int i = 0; i < kRmaxRing; ++i) ring[i] = 0ULL;
+    for (int i = 0; i < 8; ++i) {
+        unsigned long long bits;
+        std::memcpy(&bits, &hist[i], 8);
+        ring[(t - 8 + i) & (kRmaxRing - 1)] = bits;
+    }
+}
+
+void ring_to_hist(const unsigned long long ring[kRmaxRing], long long t, double hist[8])
+{
+    for (int i = 0; i < 8; ++i) std::memcpy(&hist[i], &ring[(t - 8 + i) & (kRmaxRing - 1)], 8);
+}
+
+int check_hist(const double hist[8])
+{
+    for (int i = 0; i < 8; ++i)
+        if (!std::isfinite(hist[i]) || hist[i] < 0.0)
+            return fail(SPKMC_EINVAL, "rmax_hist[%d] must be finite and >= 0", i);
+    return SPKMC_OK;
+}
+
 int check_params(const spkmc_params *p, int *d_out)
 {
     if (!p) return fail(SPKMC_EINVAL, "params is NULL");
@@ -86,6 +137,10 @@ int check_params(const spkmc_params *p, int *d_out)
     if (p->init != SPKMC_INIT_HOT && p->init != SPKMC_INIT_COLD)
         return fail(SPKMC_EINVAL, "init must be SPKMC_INIT_HOT or SPKMC_INIT_COLD");
     if (p->event_log_capacity < 0) return fail(SPKMC_EINVAL, "event_log_capacity must be >= 0");
+    if (p->rmax_mode != SPKMC_RMAX_EXACT && p->rmax_mode != SPKMC_RMAX_PRESCRIBED &&
+        p->rmax_mode != SPKMC_RMAX_LEARNED)
+        return fail(SPKMC_EINVAL, "rmax_mode must be SPKMC_RMAX_EXACT, _PRESCRIBED or _LEARNED (got %d)",
+                    p->rmax_mode);
     const long long nd = p->L / d;
     if (nd * nd * nd > (1LL << 31) - 1) return fail(SPKMC_EINVAL, "too many domains (L/d)^3 for int32 ids");
     *d_out = d;
@@ -303,6 +358,8 @@ int sync_and_check(spkmc_batch *b)
         b->sticky_error = *b->h_err;
         if (*b->h_err == SPKMC_ETIMEOUT)
             return fail(SPKMC_ETIMEOUT, "a grid barrier timed out on the device");
+        if (*b->h_err == SPKMC_EBOUND)
+            return fail(SPKMC_EBOUND, "an active domain's R_k exceeded the R_max bound");
         return fail(*b->h_err, "device reported inconsistent class counts");
     }
     return SPKMC_OK;
@@ -324,9 +381,8 @@ int upload_slot(spkmc_batch *b, int slot)
 
 int refresh_derived(spkmc_batch *b, const LatticeDesc &d)
 {
-    int rc;
-    if ((rc = launch_ghosts(d, 0, nullptr, b->stream)) != SPKMC_OK) return cuda_fail(cudaGetLastError(), "ghost faces");
-    if ((rc = launch_count_classes(d, 0, nullptr, b->stream)) != SPKMC_OK)
+    if (launch_ghosts(d, 0, nullptr, b->stream) != SPKMC_OK) return cuda_fail(cudaGetLastError(), "ghost faces");
+    if (launch_count_classes(d, 0, nullptr, b->stream) != SPKMC_OK)
         return cuda_fail(cudaGetLastError(), "class counts");
     return SPKMC_OK;
 }
@@ -382,7 +438,7 @@ int admit(spkmc_batch *b, const spkmc_params *p, long long cycles, int slot_hint
     D.log = p->event_log_capacity > 0 ? (spkmc_event *)s.blocks[3] : nullptr;
     D.log_cap = p->event_log_capacity;
     D.log_t0 = 0;
-    host_rates(p->J, p->H, p->T, D.rate);
+    fill_physics(D, p, d);
     D.seed = p->seed;
     D.L = p->L;
     D.d = d;
@@ -490,6 +546,8 @@ int run(spkmc_batch *b, long long cycles)
         for (const Segment &sg : segs) dmax = std::max(dmax, b->slots[sg.slot].d);
         P.item_bytes = stage_slot_bytes(dmax);
         P.round_items = cycle_round_items(dmax);
+        P.exact_any = 0;
+        for (const Segment &sg : segs) P.exact_any |= b->slots[sg.slot].desc.rmode == SPKMC_RMAX_EXACT;
         int rc = launch_cycles(P, (int)grid, b->stream, grid > 1);
         if (rc) return cuda_fail(cudaGetLastError(), "persistent cycle launch");
         b->last_grid = (int)grid;
@@ -585,6 +643,8 @@ int set_spins(spkmc_batch *b, int slot, const int8_t *host, size_t n)
     int8_t *tmp = (int8_t *)b->dev_alloc(N);
     if (!tmp) return fail(SPKMC_ENOMEM, "device allocation of %zu bytes failed", N);
     cudaError_t e = cudaMemcpyAsync(tmp, host, N, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) // the R_max history described the old spins
+        e = cudaMemsetAsync(b->d_state[slot].rmax, 0, sizeof(b->d_state[slot].rmax), b->stream);
     if (e == cudaSuccess) {
         rc = launch_pack_rows(s.desc, tmp, b->stream);
         if (!rc) rc = refresh_derived(b, s.desc);
@@ -651,6 +711,18 @@ int spkmc_rate_table(double J, double H, double T, double out[14])
     if (!std::isfinite(J) || !std::isfinite(H) || !std::isfinite(T) || !(T > 0.0))
         return fail(SPKMC_EINVAL, "J, H, T must be finite and T > 0");
     host_rates(J, H, T, out);
+    return SPKMC_OK;
+}
+
+int spkmc_rmax_bounds(int32_t d, double J, double H, double T, double *prescribed, double *margin)
+{
+    if (!prescribed || !margin) return fail(SPKMC_EINVAL, "outputs must not be NULL");
+    if (!std::isfinite(J) || !std::isfinite(H) || !std::isfinite(T) || !(T > 0.0))
+        return fail(SPKMC_EINVAL, "J, H, T must be finite and T > 0");
+    if (!valid_edge(d)) return fail(SPKMC_EINVAL, "domain edge must be 2, 4, 8 or 16 (got %d)", d);
+    double r[kClasses];
+    host_rates(J, H, T, r);
+    host_bounds(d, r, prescribed, margin);
     return SPKMC_OK;
 }
 
@@ -779,6 +851,7 @@ int spkmc_get_state(spkmc_t *h, spkmc_state *out)
     out->n_null = (int64_t)st.n_null;
     out->sum_null_rate_fx[0] = st.null_fx_lo;
     out->sum_null_rate_fx[1] = st.null_fx_hi;
+    ring_to_hist(st.rmax, st.t, out->rmax_hist);
     return SPKMC_OK;
 }
 
@@ -787,6 +860,7 @@ int spkmc_set_state(spkmc_t *h, const spkmc_state *in)
     if (!h || !in) return fail(SPKMC_EINVAL, "NULL argument");
     if (in->cycle < 0 || in->n_flip < 0 || in->n_null < 0)
         return fail(SPKMC_EINVAL, "state counters must be >= 0");
+    if (int rc0 = check_hist(in->rmax_hist)) return rc0;
     spkmc_batch *b = h->b;
     DeviceGuard g(b->device);
     CUDA_TRY(cudaStreamSynchronize(b->stream), "stream synchronize");
@@ -798,6 +872,7 @@ int spkmc_set_state(spkmc_t *h, const spkmc_state *in)
     st.n_null = (unsigned long long)in->n_null;
     st.null_fx_lo = in->sum_null_rate_fx[0];
     st.null_fx_hi = in->sum_null_rate_fx[1];
+    hist_to_ring(in->rmax_hist, in->cycle, st.rmax);
     Slot &s = b->slots[h->slot];
     st.budget = s.budget;
     s.t = in->cycle;
@@ -1056,6 +1131,7 @@ extern "C" int spkmc_run_cycles_noalloc(const spkmc_params *p, int8_t *dev_spins
     if (p->event_log_capacity != 0) return fail(SPKMC_EINVAL, "the no-allocation variant keeps no event log");
     if (state->cycle < 0 || state->n_flip < 0 || state->n_null < 0)
         return fail(SPKMC_EINVAL, "state counters must be >= 0");
+    if ((rc = check_hist(state->rmax_hist)) != SPKMC_OK) return rc;
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
     unsigned char *base = nullptr;
@@ -1088,7 +1164,7 @@ extern "C" int spkmc_run_cycles_noalloc(const spkmc_params *p, int8_t *dev_spins
     D.log = nullptr;
     D.log_cap = 0;
     D.log_t0 = 0;
-    host_rates(p->J, p->H, p->T, D.rate);
+    fill_physics(D, p, d);
     D.seed = p->seed;
     D.L = p->L;
     D.d = d;
@@ -1103,7 +1179,8 @@ extern "C" int spkmc_run_cycles_noalloc(const spkmc_params *p, int8_t *dev_spins
     st.n_null = (unsigned long long)state->n_null;
     st.null_fx_lo = state->sum_null_rate_fx[0];
     st.null_fx_hi = state->sum_null_rate_fx[1];
-    st.budget = -1; // rmax slots, M and B start at zero
+    hist_to_ring(state->rmax_hist, state->cycle, st.rmax);
+    st.budget = -1; // M and B start at zero
     Segment seg{};
     seg.base = 0;
     seg.slot = 0;
@@ -1140,6 +1217,7 @@ extern "C" int spkmc_run_cycles_noalloc(const spkmc_params *p, int8_t *dev_spins
         P.skip_cta = -1;
         P.item_bytes = stage_slot_bytes(d);
         P.round_items = cycle_round_items(d);
+        P.exact_any = p->rmax_mode == SPKMC_RMAX_EXACT;
         if (launch_cycles(P, (int)grid, s, grid > 1) != SPKMC_OK)
             return cuda_fail(cudaGetLastError(), "persistent cycle launch");
         left -= n;
@@ -1151,6 +1229,7 @@ extern "C" int spkmc_run_cycles_noalloc(const spkmc_params *p, int8_t *dev_spins
     CUDA_TRY(cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s), "read error flag");
     CUDA_TRY(cudaStreamSynchronize(s), "stream synchronize");
     if (err == SPKMC_ETIMEOUT) return fail(SPKMC_ETIMEOUT, "a grid barrier timed out on the device");
+    if (err == SPKMC_EBOUND) return fail(SPKMC_EBOUND, "an active domain's R_k exceeded the R_max bound");
     if (err != 0) return fail(err, "device reported inconsistent class counts");
     state->cycle = st.t;
     state->clock = st.clock;
@@ -1158,5 +1237,6 @@ extern "C" int spkmc_run_cycles_noalloc(const spkmc_params *p, int8_t *dev_spins
     state->n_null = (int64_t)st.n_null;
     state->sum_null_rate_fx[0] = st.null_fx_lo;
     state->sum_null_rate_fx[1] = st.null_fx_hi;
+    ring_to_hist(st.rmax, st.t, state->rmax_hist);
     return SPKMC_OK;
 }

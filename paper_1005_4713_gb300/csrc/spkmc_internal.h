@@ -41,10 +41,17 @@ struct LatticeDesc {
     int64_t log_cap;
     int64_t log_t0;
     double rate[kClasses];
+    double rbound;   // prescribed bound d^3 max r (1 + 2^-32) (Sec. 3.2 step 4b)
+    double rmargin;  // growth of R_k between two visits of a colour, a + 12 b
     uint64_t seed;
     int32_t L, d, nd, half;
     int64_t K, Kact;
+    int32_t rmode;   // SPKMC_RMAX_*
+    int32_t pad;
 };
+
+constexpr double kBoundSlack = 1.0 + 0x1p-32; // rounding cover of the R_max bounds
+constexpr int kRmaxRing = 16;                 // exact R_max of cycle t in slot t % 16
 
 // Per-lattice state written by the persistent kernel.
 struct LatticeState {
@@ -55,7 +62,9 @@ struct LatticeState {
     unsigned long long null_fx_lo;  // sum of floor(r_0k * 2^64), 128-bit
     unsigned long long null_fx_hi;
     int64_t budget;                 // cycles left; < 0 = unlimited
-    unsigned long long rmax[3];     // R_max bit patterns, slot t % 3
+    unsigned long long rmax[kRmaxRing]; // exact R_max bit patterns of cycle t in slot t % 16:
+                                        // written at t, read at t (exact) or t + 8
+                                        // (learned), cleared at t - 12
     long long M;                    // sum of spins, kept exact flip by flip
     long long B;                    // forward bond sum, kept exact flip by flip
 };
@@ -81,7 +90,7 @@ struct LaunchParams {
     int skip_cta;         // debug: CTA that never arrives (-1 = none)
     int round_items;      // active domains per phase-B round (staging capacity)
     int item_bytes;       // staging bytes per domain (largest edge of the launch)
-    int pad;
+    int exact_any;        // some lattice pads to the exact R_max: reduce before the events
 };
 
 // u16 words and bytes of one domain block (rows and ghost faces).

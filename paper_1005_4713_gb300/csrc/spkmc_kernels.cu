@@ -93,11 +93,6 @@ __device__ __forceinline__ int ld_volatile_int(const int *p)
     return *reinterpret_cast<const volatile int *>(p);
 }
 
-__device__ __forceinline__ uint32_t ld_u16(const uint16_t *p)
-{
-    return (uint32_t)__ldcg(reinterpret_cast<const unsigned short *>(p));
-}
-
 // XOR into one 16-bit slot through the 32-bit word that holds it.
 __device__ __forceinline__ void xor_u16(uint16_t *p, uint32_t bits)
 {
@@ -828,8 +823,23 @@ __device__ __forceinline__ void phase_b_round(const LaunchParams &P, CtaShared &
                 const LatticeDesc &Ld = P.desc[slot];
                 a = q - S.seg_base[ls];
                 const long long t = S.seg_t0[ls] + g;
-                const double Rmax = __longlong_as_double(
-                    (long long)__ldcg(&P.state[slot].rmax[t % 3]));
+                // the rate R the lines are padded to (Sec. 3.1 step 2 or the
+                // bounds of Sec. 3.2 step 4b)
+                double R;
+                if (Ld.rmode == SPKMC_RMAX_EXACT) {
+                    R = __longlong_as_double((long long)__ldcg(&P.state[slot].rmax[t & (kRmaxRing - 1)]));
+                } else {
+                    R = Ld.rbound;
+                    if (Ld.rmode == SPKMC_RMAX_LEARNED) {
+                        // exact R_max of this colour's previous visit, cycle t - 8
+                        const double h = __longlong_as_double(
+                            (long long)__ldcg(&P.state[slot].rmax[(t + 8) & (kRmaxRing - 1)]));
+                        if (h > 0.0) {
+                            const double b = __dmul_rn(__dadd_rn(h, Ld.rmargin), kBoundSlack);
+                            if (b < R) R = b;
+                        }
+                    }
+                }
                 double cum[kClasses];
                 uint32_t npk[7];
                 double u01;
@@ -857,14 +867,16 @@ __device__ __forceinline__ void phase_b_round(const LaunchParams &P, CtaShared &
                     u01 = uw.x;
                     w1 = (unsigned long long)__double_as_longlong(uw.y);
                 }
-                // target on the frequency line padded to R_max (steps 3-4):
-                // the first class whose cumulative rate exceeds it, else null.
-                const double target = __dmul_rn(u01, Rmax);
+                // the bound must cover the domain (tolerance check of Sec. 3.2)
+                if (cum[kClasses - 1] > R) raise_error(P.err, SPKMC_EBOUND);
+                // target on the frequency line padded to R (steps 3-4): the
+                // first class whose cumulative rate exceeds it, else null.
+                const double target = __dmul_rn(u01, R);
                 const unsigned long long tb = (unsigned long long)__double_as_longlong(target);
 #pragma unroll
                 for (int c = kClasses - 1; c >= 0; --c)
                     if (tb < (unsigned long long)__double_as_longlong(cum[c])) cls = c;
-                fixed64(__dadd_rn(Rmax, -cum[kClasses - 1]), fxlo, fxhi);
+                fixed64(__dadd_rn(R, -cum[kClasses - 1]), fxlo, fxhi);
                 active_domain(Ld.half, a, (int)(t & 7), dx, dy, dz);
                 k = domain_index(Ld.nd, dx, dy, dz);
                 dval = Ld.d;
@@ -891,9 +903,10 @@ __device__ __forceinline__ void phase_b_round(const LaunchParams &P, CtaShared &
                     for (int c = 0; c < 7; ++c) ownpk[c] = npk[c];
                 }
                 if (a == 0) {
-                    S.seg_rnow[ls] = Rmax; // the clock moves once this cycle (step 5)
+                    S.seg_rnow[ls] = R; // the clock moves once this cycle (step 5)
                     S.seg_tick[ls] = 1;
-                    P.state[slot].rmax[(t + 2) % 3] = 0ULL;
+                    // slot of cycle t - 12, last read at t - 4: free for t + 4
+                    P.state[slot].rmax[(t + 4) & (kRmaxRing - 1)] = 0ULL;
                 }
             } else {
                 ls = -1;
@@ -1144,11 +1157,18 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
         for (int i = threadIdx.x; i < S.nsegc; i += blockDim.x) {
             if (g < S.seg_part[i]) {
                 const long long t = S.seg_t0[i] + g;
-                atomicMax(&P.state[S.seg_slot[i]].rmax[t % 3], S.seg_rmax[i]);
+                atomicMax(&P.state[S.seg_slot[i]].rmax[t & (kRmaxRing - 1)], S.seg_rmax[i]);
             }
             S.seg_rmax[i] = 0;
         }
-        if (!grid_barrier(P, S, epoch)) return;
+        // the exact R_max is needed before the events; the bounds are not
+        // (their reductions are read eight cycles later)
+        if (P.exact_any && !grid_barrier(P, S, epoch)) {
+            // leaving on an error: the cycle's block copies must land first
+            if (early && threadIdx.x == 0 && S.early_bytes > 0) mbar_wait_bounded(P, &S.mbar, mbar_phase);
+            __syncthreads();
+            return;
+        }
         phase_b(P, S, stage, g, lo, hi, mbar_phase, early, line);
         if (!*reinterpret_cast<volatile int *>(&S.ok)) return;
         if (g + 1 < P.ncycles) {

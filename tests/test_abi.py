@@ -43,6 +43,32 @@ def test_rate_table_bitwise_equal_to_oracle():
         assert np.array_equal(sp.spkmc_rate_table(J, H, T), oracle.rates(J, H, T))
 
 
+def test_rmax_bounds_bitwise_equal_to_oracle():
+    """The library takes the bounds from its rate table; the oracle evaluates
+    the prescribed formula of Sec. 3.2 directly.  Same bits."""
+    for d in (2, 4, 8, 16):
+        for J, H, T in [(1.0, 0.0, 4.5115), (1.0, 0.01, 4.43), (-0.5, 0.2, 2.0), (1.0, -0.3, 0.01),
+                        (0.0, 0.0, 3.0), (2.0, 0.0, 1e6)]:
+            assert sp.spkmc_rmax_bounds(d, J, H, T) == oracle.rmax_bounds(d, J, H, T)
+
+
+@pytest.mark.parametrize("d,T", [(3, 1.0), (32, 1.0), (4, 0.0), (4, float("nan"))])
+def test_rmax_bounds_rejects_bad_arguments(d, T):
+    with pytest.raises(sp.SpkmcError) as e:
+        sp.spkmc_rmax_bounds(d, 1.0, 0.0, T)
+    assert e.value.code == sp.SPKMC_EINVAL
+
+
+@pytest.mark.parametrize("mode", [-1, 3])
+def test_create_rejects_unknown_rmax_mode(mode):
+    p = sp.make_params(16, 4, rmax_mode=mode)
+    assert sp.spkmc_bytes_required(p) == 0
+    with pytest.raises(sp.SpkmcError) as e:
+        sp.spkmc_create_ex(p)
+    assert e.value.code == sp.SPKMC_EINVAL
+    assert "rmax_mode" in sp.spkmc_last_error()
+
+
 @pytest.mark.parametrize("J,H,T", [(1.0, 0.0, 0.0), (1.0, 0.0, -1.0), (float("nan"), 0.0, 1.0),
                                    (1.0, float("inf"), 1.0), (1.0, 0.0, float("inf"))])
 def test_rate_table_rejects_bad_arguments(J, H, T):

@@ -279,6 +279,36 @@ def served_summary(n_requests=400, rate=200.0, budget=120 << 30, step_cycles=100
 # ---------------------------------------------------------------------------
 # arms
 # ---------------------------------------------------------------------------
+def bounds_summary(cfg, stream, steps, cps):
+    """The bounds of Sec. 3.2 step 4b on the same workload: the launch has no
+    grid barrier before the events.  Events/s counts nulls like the headline;
+    flips/s and the useful fraction (flips / events) say what the bound
+    costs in null events."""
+    import torch
+
+    import paper_1005_4713_gb300 as sp
+
+    out = {}
+    for mode, name in ((sp.SPKMC_RMAX_LEARNED, "learned"), (sp.SPKMC_RMAX_PRESCRIBED, "prescribed")):
+        with sp.Lattice(L_BENCH, D_BENCH, 1.0, 0.0, 4.5115, SEED_BENCH, config=cfg, rmax_mode=mode) as lat:
+            for _ in range(3):
+                lat.run(cps)
+            o0 = lat.observables()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                lat.run(cps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            s = e0.elapsed_time(e1) / 1e3
+            o = lat.observables()
+            nf, nn = o.n_flip - o0.n_flip, o.n_null - o0.n_null
+            out[name] = {"events_per_s": (nf + nn) / s, "flips_per_s": nf / s,
+                         "useful_fraction": nf / (nf + nn), "us_per_cycle": s / (steps * cps) * 1e6}
+    return out
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
@@ -339,6 +369,7 @@ def run_gpu(args, world, rank, local, pg):
     barrier(pg, device)
     torch.cuda.synchronize(device)
 
+    obs0 = lat.observables()
     sampler = ClockSampler(local).start()
     k0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     k1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -362,6 +393,9 @@ def run_gpu(args, world, rank, local, pg):
     events = world * args.steps * cps * kact
     value = events / (ms_max / 1e3)
     lat_info = lat.info()
+    obs1 = lat.observables()
+    flips = obs1.n_flip - obs0.n_flip
+    useful = flips / max(1, (obs1.n_flip + obs1.n_null) - (obs0.n_flip + obs0.n_null))
 
     # end to end through the C ABI with host buffers: upload the start
     # lattice from pinned memory, run the steps with observables, read the
@@ -397,10 +431,12 @@ def run_gpu(args, world, rank, local, pg):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(rank, world)
-    batched = served = None
+    batched = served = bounds = None
     if rank == 0 and world == 1 and not args.no_ensembles:
         batched = batched_summary()
         served = served_summary()
+    if rank == 0 and world == 1 and not args.no_bounds:
+        bounds = bounds_summary(cfg, stream, args.steps, cps)
 
     if rank == 0:
         peak, peak_kind = measured_peak()
@@ -430,6 +466,8 @@ def run_gpu(args, world, rank, local, pg):
             "e2e": e2e,
             "gpu_launches": args.steps,
             "clocks": clocks,
+            "exact_rmax": {"flips_per_s": flips * world / (ms_max / 1e3), "useful_fraction": useful},
+            "rmax_bounds": bounds,
             "batched": batched,
             "served": served,
         }
@@ -448,6 +486,7 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensembles", action="store_true", help="skip the batched and served summaries")
+    ap.add_argument("--no-bounds", action="store_true", help="skip the prescribed/learned R_max summary")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -899,8 +899,9 @@ int spkmc_class_counts(spkmc_t *h, int32_t *host_counts, size_t n)
     CUDA_TRY(cudaMemcpyAsync(tmp.data(), s.desc.counts, tmp.size() * 4, cudaMemcpyDeviceToHost, b->stream),
              "read counts");
     CUDA_TRY(cudaStreamSynchronize(b->stream), "stream synchronize");
+    // the device words carry the lower-half count in bits 16-31
     for (long long k = 0; k < s.desc.K; ++k)
-        std::memcpy(host_counts + k * kClasses, tmp.data() + k * kCountStride, kClasses * 4);
+        for (int c = 0; c < kClasses; ++c) host_counts[k * kClasses + c] = tmp[k * kCountStride + c] & 0xFFFF;
     return SPKMC_OK;
 }
 

@@ -13,10 +13,13 @@
 //             5 gzp[y] bit x = spin (x, y, z=d)
 //           so a domain with its halo is 2d^2 + 12d bytes (704 for d = 16),
 //           read by one bulk copy;
-//   counts  [K][16]   int32: number of sites of each of the 14 classes;
-//   scratch [K/8][20] 8-byte words: per active domain of the running cycle,
+//   counts  [K][16]   uint32 per class c < 14: bits 0-15 the number of sites
+//           of class c in the domain, bits 16-31 the number of those in its
+//           lower half (z < d/2), so a class move of one site is a single
+//           add of +-(1 + [z < d/2] << 16); words 14, 15 are zero;
+//   scratch [K/8][24] 8-byte words: per active domain of the running cycle,
 //           the cumulative frequency line cum[0..13], u01, w1 and the 14
-//           class counts as uint16.
+//           count words.
 #pragma once
 
 #include <cstdint>
@@ -27,7 +30,7 @@ namespace spkmc {
 
 constexpr int kClasses = 14;
 constexpr int kCountStride = 16;   // int32 per domain in counts
-constexpr int kScratchStride = 20; // 8-byte words per active domain in scratch
+constexpr int kScratchStride = 24; // 8-byte words per active domain in scratch
 constexpr int kMaxEdge = 16;
 constexpr int kPadRow = kMaxEdge + 2;           // padded rows per axis
 constexpr int kPadWords = kPadRow * kPadRow;    // words of one padded domain
@@ -96,10 +99,13 @@ struct LaunchParams {
 // u16 words and bytes of one domain block (rows and ghost faces).
 __host__ __device__ constexpr int block_words(int d) { return d * d + 6 * d; }
 __host__ __device__ constexpr int staged_bytes(int d) { return 2 * block_words(d); }
-// Staging slot: the block rounded up to an odd number of 16-byte units, so
-// that consecutive slots start in different shared-memory banks.
-__host__ __device__ constexpr int stage_slot_bytes(int d) { return ((staged_bytes(d) / 16) | 1) * 16; }
-constexpr int kStageBytes = 84 * 1024; // phase-B staging area per CTA
+// Staging slot of one domain in shared memory: the block, then (in the last
+// 64 bytes of the slot) the domain's 14 class count words of the cycle; the
+// slot is an odd number of 16-byte units, so that consecutive slots start in
+// different shared-memory banks.
+__host__ __device__ constexpr int stage_slot_bytes(int d) { return (((staged_bytes(d) + 64) / 16) | 1) * 16; }
+constexpr int kSlotCountBytes = 64; // count words at the end of each staging slot
+constexpr int kStageBytes = 88 * 1024; // phase-B staging area per CTA
 
 // Host-side launch helpers implemented in spkmc_kernels.cu.
 struct KernelShape {

@@ -259,8 +259,8 @@ struct __align__(16) WorkItem {
     int j;            // rank of the site within the class
     int off;          // byte offset of the staged block
     int site;         // chosen local site (set by the classifier), -1 if none
+    int half;         // half of the domain (z < d/2: 0) that holds the j-th site
     short dx, dy, dz, d;
-    uint32_t npk[7];  // the domain's class counts, two 16-bit counts per word
 };
 
 struct CtaShared {
@@ -418,14 +418,20 @@ struct Line {
     double cum[kClasses];  // cumulative rates, class order
     double u01;            // uniform draw for the event
     unsigned long long w1; // 64-bit draw for the site rank
-    uint32_t npk[7];       // class counts, two 16-bit counts per word
 };
+
+// The class count words (total | lower-half count << 16) of the domain staged
+// in the slot at byte offset `off`.
+__device__ __forceinline__ uint32_t *slot_counts(unsigned char *stage, int off, int item_bytes)
+{
+    return reinterpret_cast<uint32_t *>(stage + off + item_bytes - kSlotCountBytes);
+}
 
 // Step 1: frequency line of every active domain of the CTA's item range.
 // With `keep` (the CTA has at most one item per thread) the line of the
 // thread's item stays in registers for phase B; otherwise it goes to scratch.
-__device__ void phase_a(const LaunchParams &P, CtaShared &S, long long g, long long lo, long long hi,
-                        bool keep, Line &line)
+__device__ void phase_a(const LaunchParams &P, CtaShared &S, unsigned char *stage, long long g, long long lo,
+                        long long hi, bool keep, Line &line)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (long long base = lo + warp * 32; base < hi; base += kThreads) {
@@ -443,40 +449,46 @@ __device__ void phase_a(const LaunchParams &P, CtaShared &S, long long g, long l
                 const long long k = domain_index(Ld.nd, dx, dy, dz);
                 const int4 *cp = reinterpret_cast<const int4 *>(Ld.counts + k * kCountStride);
                 const int4 n0 = __ldcg(cp), n1 = __ldcg(cp + 1), n2 = __ldcg(cp + 2),
-                           n3 = __ldcg(cp + 3);
+                           n3 = __ldcg(cp + 3); // total | lower-half count << 16
                 // the draw does not depend on the counts: compute it while they load
                 unsigned long long w[4];
                 philox4x64_10((unsigned long long)t, (unsigned long long)k, 1ULL, 0ULL, Ld.seed, 0ULL,
                               w);
                 const double u01 = __ull2double_rn(w[0] >> 11) * 0x1p-53;
-                const int n[kClasses] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z,
-                                         n1.w, n2.x, n2.y, n2.z, n2.w, n3.x, n3.y};
+                const uint32_t cw[kClasses] = {(uint32_t)n0.x, (uint32_t)n0.y, (uint32_t)n0.z, (uint32_t)n0.w,
+                                               (uint32_t)n1.x, (uint32_t)n1.y, (uint32_t)n1.z, (uint32_t)n1.w,
+                                               (uint32_t)n2.x, (uint32_t)n2.y, (uint32_t)n2.z, (uint32_t)n2.w,
+                                               (uint32_t)n3.x, (uint32_t)n3.y};
                 double cum[kClasses];
-                double acc = __dmul_rn((double)n[0], __ldg(&Ld.rate[0]));
+                double acc = __dmul_rn((double)(cw[0] & 0xFFFFu), __ldg(&Ld.rate[0]));
                 cum[0] = acc;
 #pragma unroll
                 for (int c = 1; c < kClasses; ++c) {
-                    acc = __dadd_rn(acc, __dmul_rn((double)n[c], __ldg(&Ld.rate[c])));
+                    acc = __dadd_rn(acc, __dmul_rn((double)(cw[c] & 0xFFFFu), __ldg(&Ld.rate[c])));
                     cum[c] = acc;
                 }
-                uint32_t npk[7];
-#pragma unroll
-                for (int c = 0; c < 7; ++c) npk[c] = (uint32_t)n[2 * c] | ((uint32_t)n[2 * c + 1] << 16);
                 if (keep) {
 #pragma unroll
                     for (int c = 0; c < kClasses; ++c) line.cum[c] = cum[c];
                     line.u01 = u01;
                     line.w1 = w[1];
-#pragma unroll
-                    for (int c = 0; c < 7; ++c) line.npk[c] = npk[c];
+                    // the count words go to the end of the domain's staging slot
+                    // (the block copy fills only its front)
+                    uint4 *tw = reinterpret_cast<uint4 *>(slot_counts(stage, (int)(q - lo) * P.item_bytes, P.item_bytes));
+                    tw[0] = make_uint4(cw[0], cw[1], cw[2], cw[3]);
+                    tw[1] = make_uint4(cw[4], cw[5], cw[6], cw[7]);
+                    tw[2] = make_uint4(cw[8], cw[9], cw[10], cw[11]);
+                    tw[3] = make_uint4(cw[12], cw[13], 0u, 0u);
                 } else {
                     double2 *sp = reinterpret_cast<double2 *>(Ld.scratch + a * kScratchStride);
 #pragma unroll
                     for (int c = 0; c < kClasses; c += 2) __stcg(sp + c / 2, make_double2(cum[c], cum[c + 1]));
                     __stcg(sp + 7, make_double2(u01, __longlong_as_double((long long)w[1])));
                     uint4 *np = reinterpret_cast<uint4 *>(sp + 8);
-                    __stcg(np, make_uint4(npk[0], npk[1], npk[2], npk[3]));
-                    __stcg(np + 1, make_uint4(npk[4], npk[5], npk[6], 0u));
+                    __stcg(np, make_uint4(cw[0], cw[1], cw[2], cw[3]));
+                    __stcg(np + 1, make_uint4(cw[4], cw[5], cw[6], cw[7]));
+                    __stcg(np + 2, make_uint4(cw[8], cw[9], cw[10], cw[11]));
+                    __stcg(np + 3, make_uint4(cw[12], cw[13], 0u, 0u));
                 }
                 rbits = (unsigned long long)__double_as_longlong(acc);
             } else {
@@ -503,12 +515,11 @@ __device__ __forceinline__ double neg_log_xi(const LaunchParams &P, const CtaSha
     return -log(xi);
 }
 
-// Rank the sites of class w.cls in ascending local index and return the
-// w.j-th, cooperatively in the group of 8 lanes (octet: lanes q, q+4, ...,
-// q+28 with q = lane % 4) that holds `lane`; -1 if the class has fewer
-// sites.  A warp works on 4 domains at once; with strided octets and staging
-// slots of an odd number of 16-byte units, the 16-byte shared-memory loads
-// of any 8 consecutive lanes hit distinct banks.
+// Rank the sites of class w.cls in the half w.half of the domain (z < d/2
+// or z >= d/2) in ascending local index and return the w.j-th,
+// cooperatively in the group of 8 lanes (octet: lanes q, q+4, ..., q+28 with
+// q = lane % 4) that holds `lane`; -1 if the half has fewer such sites.  A
+// warp works on 4 domains at once.
 template <int D>
 __device__ int select_site(const WorkItem &w, const unsigned char *stage, int lane)
 {
@@ -517,59 +528,47 @@ __device__ int select_site(const WorkItem &w, const unsigned char *stage, int la
     const unsigned grp = 0x11111111u << (lane & 3);
     const int sig = w.cls >= 7, us = w.cls - 7 * sig;
     if constexpr (D == 16) {
-        // octet lane o holds the planes z = 2o and 2o+1 (rows 32o .. 32o+31) as
-        // 16 words of two 16-site rows: bit b of word q is site 16 (32o + 2q) + b
+        // octet lane o holds the plane z = 8 half + o as 8 words of two
+        // 16-site rows: bit b of word p is site 16 (16 z + 2p) + b
         const uint16_t *g = st + 256;
-        const int z0 = 2 * o;
-        uint32_t cur[16], zm[8], zp[8];
+        const int z = 8 * w.half + o;
+        uint32_t cur[8], zm[8], zp[8];
         {
-            const uint4 *p = reinterpret_cast<const uint4 *>(st + 32 * o);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const uint4 v = p[i];
-                cur[4 * i] = v.x;
-                cur[4 * i + 1] = v.y;
-                cur[4 * i + 2] = v.z;
-                cur[4 * i + 3] = v.w;
-            }
-            const uint4 *pm = reinterpret_cast<const uint4 *>(z0 > 0 ? st + 16 * (z0 - 1) : g + 4 * 16);
-            const uint4 *pp = reinterpret_cast<const uint4 *>(z0 + 1 < 15 ? st + 16 * (z0 + 2) : g + 5 * 16);
+            const uint4 *pc = reinterpret_cast<const uint4 *>(st + 16 * z);
+            const uint4 *pm = reinterpret_cast<const uint4 *>(z > 0 ? st + 16 * (z - 1) : g + 4 * 16);
+            const uint4 *pp = reinterpret_cast<const uint4 *>(z < 15 ? st + 16 * (z + 1) : g + 5 * 16);
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
-                const uint4 a = pm[i], b = pp[i];
+                const uint4 c = pc[i], a = pm[i], b = pp[i];
+                cur[4 * i] = c.x; cur[4 * i + 1] = c.y; cur[4 * i + 2] = c.z; cur[4 * i + 3] = c.w;
                 zm[4 * i] = a.x; zm[4 * i + 1] = a.y; zm[4 * i + 2] = a.z; zm[4 * i + 3] = a.w;
                 zp[4 * i] = b.x; zp[4 * i + 1] = b.y; zp[4 * i + 2] = b.z; zp[4 * i + 3] = b.w;
             }
         }
-        uint32_t m[16];
+        const uint32_t below = g[2 * 16 + z], above = g[3 * 16 + z];
+        const uint32_t hxm = g[0 * 16 + z], hxp = g[1 * 16 + z];
+        uint32_t m[8];
         int tot = 0;
 #pragma unroll
-        for (int pl = 0; pl < 2; ++pl) {
-            const int z = z0 + pl;
-            const uint32_t below = g[2 * 16 + z], above = g[3 * 16 + z];
-            const uint32_t hxm = g[0 * 16 + z], hxp = g[1 * 16 + z];
-#pragma unroll
-            for (int p = 0; p < 8; ++p) {
-                const int y = 2 * p;
-                const uint32_t s = cur[8 * pl + p];
-                const uint32_t xm = ((s << 1) & 0xFFFEFFFEu) | ((hxm >> y) & 1u) | (((hxm >> (y + 1)) & 1u) << 16);
-                const uint32_t xp = ((s >> 1) & 0x7FFF7FFFu) | (((hxp >> y) & 1u) << 15) |
-                                    (((hxp >> (y + 1)) & 1u) << 31);
-                const uint32_t ym = (s << 16) | (p > 0 ? (cur[8 * pl + p - 1] >> 16) : below);
-                const uint32_t yp = (s >> 16) | ((p < 7 ? (cur[8 * pl + p + 1] & 0xFFFFu) : above) << 16);
-                const uint32_t e = pl == 0 ? zm[p] : cur[p];
-                const uint32_t f = pl == 0 ? cur[8 + p] : zp[p];
-                const uint32_t s1 = xm ^ xp ^ ym, c1 = (xm & xp) | (ym & (xm ^ xp));
-                const uint32_t s2 = yp ^ e ^ f, c2 = (yp & e) | (f & (yp ^ e));
-                const uint32_t k2 = s1 & s2;
-                const uint32_t u0 = s1 ^ s2, u1 = c1 ^ c2 ^ k2, u2 = (c1 & c2) | (k2 & (c1 ^ c2));
-                uint32_t mm = sig ? s : ~s;
-                mm &= (us & 1) ? u0 : ~u0;
-                mm &= (us & 2) ? u1 : ~u1;
-                mm &= (us & 4) ? u2 : ~u2;
-                m[8 * pl + p] = mm;
-                tot += __popc(mm);
-            }
+        for (int p = 0; p < 8; ++p) {
+            const int y = 2 * p;
+            const uint32_t s = cur[p];
+            const uint32_t xm = ((s << 1) & 0xFFFEFFFEu) | ((hxm >> y) & 1u) | (((hxm >> (y + 1)) & 1u) << 16);
+            const uint32_t xp = ((s >> 1) & 0x7FFF7FFFu) | (((hxp >> y) & 1u) << 15) |
+                                (((hxp >> (y + 1)) & 1u) << 31);
+            const uint32_t ym = (s << 16) | (p > 0 ? (cur[p - 1] >> 16) : below);
+            const uint32_t yp = (s >> 16) | ((p < 7 ? (cur[p + 1] & 0xFFFFu) : above) << 16);
+            const uint32_t e = zm[p], f = zp[p];
+            const uint32_t s1 = xm ^ xp ^ ym, c1 = (xm & xp) | (ym & (xm ^ xp));
+            const uint32_t s2 = yp ^ e ^ f, c2 = (yp & e) | (f & (yp ^ e));
+            const uint32_t k2 = s1 & s2;
+            const uint32_t u0 = s1 ^ s2, u1 = c1 ^ c2 ^ k2, u2 = (c1 & c2) | (k2 & (c1 ^ c2));
+            uint32_t mm = sig ? s : ~s;
+            mm &= (us & 1) ? u0 : ~u0;
+            mm &= (us & 2) ? u1 : ~u1;
+            mm &= (us & 4) ? u2 : ~u2;
+            m[p] = mm;
+            tot += __popc(mm);
         }
         int incl = tot;
 #pragma unroll
@@ -584,12 +583,12 @@ __device__ int select_site(const WorkItem &w, const unsigned char *stage, int la
         if (mine) {
             int jj = w.j - excl;
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
+            for (int q = 0; q < 8; ++q) {
                 const int pc = __popc(m[q]);
                 if (jj >= 0 && jj < pc) {
                     uint32_t bits = m[q];
                     for (int r = 0; r < jj; ++r) bits &= bits - 1;
-                    site = 16 * (32 * o + 2 * q) + (__ffs(bits) - 1);
+                    site = 16 * (16 * z + 2 * q) + (__ffs(bits) - 1);
                 }
                 jj -= pc;
             }
@@ -597,17 +596,19 @@ __device__ int select_site(const WorkItem &w, const unsigned char *stage, int la
         site = __shfl_sync(kFull, site, who ? __ffs(who) - 1 : lane);
         return who ? site : -1;
     } else {
-        constexpr int kRows = D * D;
-        constexpr int kRpl = kRows >= 8 ? kRows / 8 : 1; // rows per octet lane, contiguous
-        const bool on = (kRows >= 8) || (o < kRows);
+        constexpr int kHalfRows = D * D / 2;                   // rows y + D z with z in the half
+        constexpr int kRpl = kHalfRows >= 8 ? kHalfRows / 8 : 1; // rows per octet lane, contiguous
+        static_assert(D % kRpl == 0, "the rows of an octet lane lie in one plane");
+        const bool on = (kHalfRows >= 8) || (o < kHalfRows);
+        const int r0 = w.half * kHalfRows;
+        const int rl = r0 + o * kRpl, zl = rl / D, yl = rl % D; // first row of this lane
         uint32_t m[kRpl];
         int tot = 0;
 #pragma unroll
         for (int i = 0; i < kRpl; ++i) {
             m[i] = 0;
             if (on) {
-                const int r = o * kRpl + i;
-                m[i] = class_mask<D>(classify_row<D>(st, r % D, r / D), w.cls);
+                m[i] = class_mask<D>(classify_row<D>(st, yl + i, zl), w.cls);
                 tot += __popc(m[i]);
             }
         }
@@ -629,7 +630,7 @@ __device__ int select_site(const WorkItem &w, const unsigned char *stage, int la
                 if (jj >= 0 && jj < pc) {
                     uint32_t bits = m[i];
                     for (int r = 0; r < jj; ++r) bits &= bits - 1;
-                    site = D * (o * kRpl + i) + (__ffs(bits) - 1) - 1;
+                    site = D * (r0 + o * kRpl + i) + (__ffs(bits) - 1) - 1;
                 }
                 jj -= pc;
             }
@@ -668,6 +669,12 @@ __device__ FlipDelta apply_flip(const LaunchParams &P, CtaShared &S, const WorkI
 {
     const LatticeDesc &Ld = P.desc[S.seg_slot[w.ls]];
     const uint16_t *st = reinterpret_cast<const uint16_t *>(stage + w.off);
+    int32_t *cnt = Ld.counts;
+    // the domain's own count words (staged with the block); no other thread
+    // touches them this cycle
+    int4 *own = reinterpret_cast<int4 *>(cnt + w.k * kCountStride);
+    const int4 *tw = reinterpret_cast<const int4 *>(slot_counts(const_cast<unsigned char *>(stage), w.off, P.item_bytes));
+    const int4 o0 = tw[0], o1 = tw[1], o2 = tw[2], o3 = tw[3];
     const int l = w.site;
     const int s3[3] = {l % D, (l / D) % D, l / (D * D)};
     const int sig = w.cls >= 7, us = w.cls - 7 * sig;
@@ -737,25 +744,27 @@ __device__ FlipDelta apply_flip(const LaunchParams &P, CtaShared &S, const WorkI
         kj[dir] = domain_index(nd, wrap_coord(w.dx + dd[0], nd), wrap_coord(w.dy + dd[1], nd),
                                wrap_coord(w.dz + dd[2], nd)); // w.k when inside
     }
-    int32_t *cnt = Ld.counts;
     bool ok = true;
-    int4 *own = reinterpret_cast<int4 *>(cnt + w.k * kCountStride);
-    int v[kClasses];
-#pragma unroll
-    for (int c = 0; c < kClasses; ++c) v[c] = (int)((w.npk[c >> 1] >> (16 * (c & 1))) & 0xFFFFu);
+    // a class move of a site adds 1 to the total and, in the lower half of
+    // its domain (z < D/2), 1 to bits 16-31 of the class word
+    int v[kClasses] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w, o2.x, o2.y, o2.z, o2.w, o3.x, o3.y};
     const int snew = 7 * (1 - sig) + us;
+    const int inc_s = 1 + ((s3[2] < D / 2) << 16);
 #pragma unroll
-    for (int c = 0; c < kClasses; ++c) v[c] += (c == snew) - (c == w.cls);
+    for (int c = 0; c < kClasses; ++c) v[c] += ((c == snew) - (c == w.cls)) * inc_s;
 #pragma unroll
     for (int dir = 0; dir < 6; ++dir) {
         const int cn = cold[dir] + delta;
+        int j3z = s3[2] + (dir == 4 ? -1 : (dir == 5 ? 1 : 0));
+        j3z = j3z < 0 ? D - 1 : (j3z >= D ? 0 : j3z); // z of the neighbour in its own domain
+        const int inc = 1 + ((j3z < D / 2) << 16);
         if (cold[dir] >= 0 && cold[dir] < kClasses && cn >= 0 && cn < kClasses) {
             if (outv[dir]) {
-                atomicAdd(cnt + kj[dir] * kCountStride + cold[dir], -1);
-                atomicAdd(cnt + kj[dir] * kCountStride + cn, 1);
+                atomicAdd(cnt + kj[dir] * kCountStride + cold[dir], -inc);
+                atomicAdd(cnt + kj[dir] * kCountStride + cn, inc);
             } else {
 #pragma unroll
-                for (int c = 0; c < kClasses; ++c) v[c] += (c == cn) - (c == cold[dir]);
+                for (int c = 0; c < kClasses; ++c) v[c] += ((c == cn) - (c == cold[dir])) * inc;
             }
         } else {
             ok = false;
@@ -813,7 +822,8 @@ __device__ __forceinline__ void phase_b_round(const LaunchParams &P, CtaShared &
         __syncthreads();
         const long long q = rbase + threadIdx.x;
         int ls = -1, cls = -1, dx = 0, dy = 0, dz = 0, dval = 0;
-        uint32_t ownpk[7] = {0, 0, 0, 0, 0, 0, 0};
+        int jhalf = 0;
+        uint4 cw4[4]; // count words of the item (rounds after the first: from scratch)
         long long a = 0, k = 0;
         unsigned long long fxlo = 0, fxhi = 0, jrank = 0;
         if (threadIdx.x < R && q < hi) {
@@ -841,14 +851,11 @@ __device__ __forceinline__ void phase_b_round(const LaunchParams &P, CtaShared &
                     }
                 }
                 double cum[kClasses];
-                uint32_t npk[7];
                 double u01;
                 unsigned long long w1;
                 if (early) {
 #pragma unroll
                     for (int c = 0; c < kClasses; ++c) cum[c] = line.cum[c];
-#pragma unroll
-                    for (int c = 0; c < 7; ++c) npk[c] = line.npk[c];
                     u01 = line.u01;
                     w1 = line.w1;
                 } else {
@@ -860,10 +867,11 @@ __device__ __forceinline__ void phase_b_round(const LaunchParams &P, CtaShared &
                         cum[c + 1] = v.y;
                     }
                     const double2 uw = __ldcg(sp + 7);
-                    const uint4 n4a = __ldcg(reinterpret_cast<const uint4 *>(sp + 8));
-                    const uint4 n4b = __ldcg(reinterpret_cast<const uint4 *>(sp + 9));
-                    npk[0] = n4a.x; npk[1] = n4a.y; npk[2] = n4a.z; npk[3] = n4a.w;
-                    npk[4] = n4b.x; npk[5] = n4b.y; npk[6] = n4b.z;
+                    const uint4 *np = reinterpret_cast<const uint4 *>(sp + 8);
+                    cw4[0] = __ldcg(np);
+                    cw4[1] = __ldcg(np + 1);
+                    cw4[2] = __ldcg(np + 2);
+                    cw4[3] = __ldcg(np + 3);
                     u01 = uw.x;
                     w1 = (unsigned long long)__double_as_longlong(uw.y);
                 }
@@ -894,13 +902,26 @@ __device__ __forceinline__ void phase_b_round(const LaunchParams &P, CtaShared &
                         }
                     }
                 } else {
-                    unsigned long long nc = 0;
+                    uint32_t word;
+                    if (early) {
+                        word = slot_counts(stage, (int)(q - lo) * P.item_bytes, P.item_bytes)[cls];
+                    } else {
+                        const uint32_t cw[16] = {cw4[0].x, cw4[0].y, cw4[0].z, cw4[0].w, cw4[1].x, cw4[1].y,
+                                                 cw4[1].z, cw4[1].w, cw4[2].x, cw4[2].y, cw4[2].z, cw4[2].w,
+                                                 cw4[3].x, cw4[3].y, cw4[3].z, cw4[3].w};
+                        word = 0;
 #pragma unroll
-                    for (int c = 0; c < kClasses; ++c)
-                        if (c == cls) nc = (npk[c >> 1] >> (16 * (c & 1))) & 0xFFFFu;
+                        for (int c = 0; c < kClasses; ++c)
+                            if (c == cls) word = cw[c];
+                    }
+                    // rank j of the site in its class (step 4), then the half of
+                    // the domain that holds it and its rank there
+                    const unsigned long long nc = word & 0xFFFFu, nlow = word >> 16;
                     jrank = __umul64hi(w1, nc);
-#pragma unroll
-                    for (int c = 0; c < 7; ++c) ownpk[c] = npk[c];
+                    if (jrank >= nlow) {
+                        jhalf = 1;
+                        jrank -= nlow;
+                    }
                 }
                 if (a == 0) {
                     S.seg_rnow[ls] = R; // the clock moves once this cycle (step 5)
@@ -936,9 +957,15 @@ __device__ __forceinline__ void phase_b_round(const LaunchParams &P, CtaShared &
             wi.dy = (short)dy;
             wi.dz = (short)dz;
             wi.d = (short)dval;
-#pragma unroll
-            for (int c = 0; c < 7; ++c) wi.npk[c] = ownpk[c];
+            wi.half = jhalf;
             S.work[idx] = wi;
+            if (!early) {
+                uint4 *tw = reinterpret_cast<uint4 *>(slot_counts(stage, wi.off, P.item_bytes));
+                tw[0] = cw4[0];
+                tw[1] = cw4[1];
+                tw[2] = cw4[2];
+                tw[3] = cw4[3];
+            }
         }
         const int ls0 = __shfl_sync(kFull, ls, 0);
         const bool nul = ls >= 0 && cls < 0;
@@ -1152,7 +1179,7 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
                 }
             }
         }
-        phase_a(P, S, g, lo, hi, early, line);
+        phase_a(P, S, stage, g, lo, hi, early, line);
         __syncthreads();
         for (int i = threadIdx.x; i < S.nsegc; i += blockDim.x) {
             if (g < S.seg_part[i]) {
@@ -1314,14 +1341,15 @@ __global__ void __launch_bounds__(256) count_classes_kernel(LatticeDesc Ld, int 
         for (int c = 0; c < kClasses; ++c) cnt[c] = 0;
         for (int r = lane; r < D * D; r += 32) {
             const RowPlanes p = classify_row<D>(blk, r % D, r / D);
+            const int inc_low = (r < D * D / 2) ? (1 << 16) : 0; // lower half: z < D/2
 #pragma unroll
             for (int u = 0; u < 7; ++u) {
                 uint32_t e = V;
                 e &= (u & 1) ? p.u0 : ~p.u0;
                 e &= (u & 2) ? p.u1 : ~p.u1;
                 e &= (u & 4) ? p.u2 : ~p.u2;
-                cnt[7 + u] += __popc(e & p.s);
-                cnt[u] += __popc(e & ~p.s);
+                cnt[7 + u] += __popc(e & p.s) * (1 + inc_low);
+                cnt[u] += __popc(e & ~p.s) * (1 + inc_low);
             }
         }
         int differs = 0;

@@ -515,6 +515,23 @@ __device__ __forceinline__ double neg_log_xi(const LaunchParams &P, const CtaSha
     return -log(xi);
 }
 
+// Step 5 for the lattices whose clock this CTA keeps (those whose first
+// active domain it holds), one cycle behind: the time increment of the cycle
+// that ended (its R and -ln xi are known), then, with `draw`, the -ln xi of
+// cycle g.  One thread; the clock advances in cycle order.
+__device__ __forceinline__ void clock_catch_up(const LaunchParams &P, CtaShared &S, long long g, long long lo,
+                                               bool draw)
+{
+    for (int i = 0; i < S.nsegc; ++i) {
+        if (S.seg_tick[i]) {
+            S.seg_tick[i] = 0;
+            LatticeState &st = P.state[S.seg_slot[i]];
+            st.clock = __dadd_rn(st.clock, __ddiv_rn(S.seg_nlogxi[i], S.seg_rnow[i]));
+        }
+        if (draw && S.seg_base[i] >= lo && g < S.seg_part[i]) S.seg_nlogxi[i] = neg_log_xi(P, S, i, g);
+    }
+}
+
 // Rank the sites of class w.cls in the half w.half of the domain (z < d/2
 // or z >= d/2) in ascending local index and return the w.j-th,
 // cooperatively in the group of 8 lanes (octet: lanes q, q+4, ..., q+28 with
@@ -983,16 +1000,6 @@ __device__ __forceinline__ void phase_b_round(const LaunchParams &P, CtaShared &
         __syncthreads();
         const int nwork = S.nwork;
         const int bulk = S.bulk_bytes;
-        if (threadIdx.x == kThreads - 1) {
-            // Step 5: one global time increment per cycle, off the critical path
-            for (int i = 0; i < S.nsegc; ++i) {
-                if (!S.seg_tick[i]) continue;
-                S.seg_tick[i] = 0;
-                LatticeState &st = P.state[S.seg_slot[i]];
-                st.clock = __dadd_rn(st.clock, __ddiv_rn(S.seg_nlogxi[i], S.seg_rnow[i]));
-                if (g + 1 < S.seg_part[i]) S.seg_nlogxi[i] = neg_log_xi(P, S, i, g + 1); // drawn ahead
-            }
-        }
         if (early) {
             // the blocks of all the CTA's domains were requested at the start
             // of the cycle; wait for them once
@@ -1139,10 +1146,6 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
         S.seg_tick[i] = 0;
     }
     __syncthreads();
-    if (threadIdx.x == kThreads - 1) {
-        for (int i = 0; i < S.nsegc; ++i)
-            if (S.seg_base[i] >= lo && S.seg_part[i] > 0) S.seg_nlogxi[i] = neg_log_xi(P, S, i, 0);
-    }
     if (ld_volatile_int(P.err) != 0) return;
 
     unsigned epoch = 0, mbar_phase = 0;
@@ -1179,6 +1182,9 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
                 }
             }
         }
+        // step 5 one cycle behind, on a thread that normally has no domain
+        // in step 1
+        if (threadIdx.x == kThreads - 1) clock_catch_up(P, S, g, lo, true);
         phase_a(P, S, stage, g, lo, hi, early, line);
         __syncthreads();
         for (int i = threadIdx.x; i < S.nsegc; i += blockDim.x) {
@@ -1208,6 +1214,7 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
         }
     }
     __syncthreads();
+    if (threadIdx.x == kThreads - 1) clock_catch_up(P, S, 0, lo, false); // the last cycle's step
     for (int i = threadIdx.x; i < S.nsegc; i += blockDim.x) {
         LatticeState &st = P.state[S.seg_slot[i]];
         if (S.seg_nflip[i]) atomicAdd(&st.n_flip, S.seg_nflip[i]);

@@ -148,9 +148,20 @@ int check_params(const spkmc_params *p, int *d_out)
 }
 
 struct Sizes {
-    long long K, Kact, cells_b, counts_b, scratch_b, log_b;
-    long long total() const { return cells_b + counts_b + scratch_b + log_b; }
+    long long K, Kact, cells_b, counts_b, scratch_b, log_b, nrate_b;
+    long long total() const { return cells_b + counts_b + scratch_b + log_b + nrate_b; }
 };
+
+// The products fl(n r_c) of step 1 for n = 0 .. d^3, class-major (host FP64,
+// no contraction: the same rounding as the device's __dmul_rn).
+std::vector<double> host_nrate(int d, const double r[kClasses])
+{
+    const long long n1 = (long long)d * d * d + 1;
+    std::vector<double> t((size_t)(kClasses * n1));
+    for (int c = 0; c < kClasses; ++c)
+        for (long long n = 0; n < n1; ++n) t[(size_t)(c * n1 + n)] = (double)n * r[c];
+    return t;
+}
 
 Sizes sizes_of(int L, int d, long long log_cap)
 {
@@ -163,6 +174,7 @@ Sizes sizes_of(int L, int d, long long log_cap)
     s.counts_b = up(s.K * kCountStride * 4);
     s.scratch_b = up(s.Kact * kScratchStride * 8);
     s.log_b = up(log_cap * (long long)sizeof(spkmc_event));
+    s.nrate_b = up(kClasses * ((long long)d * d * d + 1) * 8);
     return s;
 }
 
@@ -194,8 +206,8 @@ struct Slot {
     LatticeDesc desc{};   // host copy of the device descriptor
     long long t = 0;      // host mirror of the cycle counter
     long long budget = -1;
-    void *blocks[4] = {nullptr, nullptr, nullptr, nullptr};
-    size_t block_bytes[4] = {0, 0, 0, 0};
+    void *blocks[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    size_t block_bytes[5] = {0, 0, 0, 0, 0};
 };
 
 struct spkmc_batch {
@@ -253,7 +265,7 @@ namespace {
 
 void free_slot_memory(spkmc_batch *b, Slot &s)
 {
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 5; ++i) {
         b->dev_free(s.blocks[i], s.block_bytes[i]);
         s.blocks[i] = nullptr;
         s.block_bytes[i] = 0;
@@ -420,8 +432,8 @@ int admit(spkmc_batch *b, const spkmc_params *p, long long cycles, int slot_hint
     s.params.domain_edge = d;
     s.d = d;
     s.sz = sizes_of(p->L, d, p->event_log_capacity);
-    const long long bytes[4] = {s.sz.cells_b, s.sz.counts_b, s.sz.scratch_b, s.sz.log_b};
-    for (int i = 0; i < 4; ++i) {
+    const long long bytes[5] = {s.sz.cells_b, s.sz.counts_b, s.sz.scratch_b, s.sz.log_b, s.sz.nrate_b};
+    for (int i = 0; i < 5; ++i) {
         if (bytes[i] == 0) continue;
         s.blocks[i] = b->dev_alloc((size_t)bytes[i]);
         s.block_bytes[i] = (size_t)bytes[i];
@@ -439,6 +451,7 @@ int admit(spkmc_batch *b, const spkmc_params *p, long long cycles, int slot_hint
     D.log_cap = p->event_log_capacity;
     D.log_t0 = 0;
     fill_physics(D, p, d);
+    D.nrate = (const double *)s.blocks[4];
     D.seed = p->seed;
     D.L = p->L;
     D.d = d;
@@ -446,6 +459,15 @@ int admit(spkmc_batch *b, const spkmc_params *p, long long cycles, int slot_hint
     D.half = D.nd / 2;
     D.K = s.sz.K;
     D.Kact = s.sz.Kact;
+    {
+        const std::vector<double> t = host_nrate(d, D.rate);
+        const cudaError_t e = cudaMemcpyAsync(s.blocks[4], t.data(), t.size() * 8, cudaMemcpyHostToDevice,
+                                              b->stream);
+        if (e != cudaSuccess) {
+            free_slot_memory(b, s);
+            return cuda_fail(e, "upload rate products");
+        }
+    }
     std::memset(&b->h_state[slot], 0, sizeof(LatticeState));
     b->h_state[slot].budget = cycles;
     s.t = 0;
@@ -1153,7 +1175,7 @@ extern "C" int spkmc_run_cycles_noalloc(const spkmc_params *p, int8_t *dev_spins
     int *d_err = reinterpret_cast<int *>(base + off);
     off += 256;
     const size_t lattice_at = off;
-    off += (size_t)sz.cells_b + (size_t)sz.counts_b + (size_t)sz.scratch_b;
+    off += (size_t)sz.cells_b + (size_t)sz.counts_b + (size_t)sz.scratch_b + (size_t)sz.nrate_b;
     if (off > SPKMC_NOALLOC_SCRATCH_BYTES)
         return fail(SPKMC_EINVAL, "lattice L=%d d=%d needs %zu bytes of scratch, the no-allocation array has %u",
                     p->L, d, off, SPKMC_NOALLOC_SCRATCH_BYTES);
@@ -1162,6 +1184,7 @@ extern "C" int spkmc_run_cycles_noalloc(const spkmc_params *p, int8_t *dev_spins
     D.cells = reinterpret_cast<uint16_t *>(base + lattice_at);
     D.counts = reinterpret_cast<int32_t *>(base + lattice_at + sz.cells_b);
     D.scratch = reinterpret_cast<double *>(base + lattice_at + sz.cells_b + sz.counts_b);
+    D.nrate = reinterpret_cast<const double *>(base + lattice_at + sz.cells_b + sz.counts_b + sz.scratch_b);
     D.log = nullptr;
     D.log_cap = 0;
     D.log_t0 = 0;
@@ -1191,6 +1214,9 @@ extern "C" int spkmc_run_cycles_noalloc(const spkmc_params *p, int8_t *dev_spins
     CUDA_TRY(cudaMemcpyAsync(d_desc, &D, sizeof(D), cudaMemcpyHostToDevice, s), "upload descriptor");
     CUDA_TRY(cudaMemcpyAsync(d_state, &st, sizeof(st), cudaMemcpyHostToDevice, s), "upload state");
     CUDA_TRY(cudaMemcpyAsync(d_seg, &seg, sizeof(seg), cudaMemcpyHostToDevice, s), "upload segment");
+    const std::vector<double> nrate = host_nrate(d, D.rate);
+    CUDA_TRY(cudaMemcpyAsync(const_cast<double *>(D.nrate), nrate.data(), nrate.size() * 8, cudaMemcpyHostToDevice, s),
+             "upload rate products");
     CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), s), "clear error flag");
     if ((rc = launch_pack_rows(D, dev_spins, s)) != SPKMC_OK) return cuda_fail(cudaGetLastError(), "pack spins");
     if ((rc = launch_ghosts(D, 0, nullptr, s)) != SPKMC_OK) return cuda_fail(cudaGetLastError(), "ghost faces");

@@ -19,7 +19,10 @@
 //           add of +-(1 + [z < d/2] << 16); words 14, 15 are zero;
 //   scratch [K/8][24] 8-byte words: per active domain of the running cycle,
 //           the cumulative frequency line cum[0..13], u01, w1 and the 14
-//           count words.
+//           count words;
+//   nrate   [14][d^3 + 1] double: fl(n * r_c) for every count n a domain can
+//           hold, computed on the host with the same IEEE product, so step 1
+//           looks the products up instead of converting and multiplying.
 #pragma once
 
 #include <cstdint>
@@ -40,6 +43,7 @@ struct LatticeDesc {
     uint16_t *cells;
     int32_t *counts;
     double *scratch;
+    const double *nrate; // fl(n r_c) at [c * (d^3 + 1) + n]
     spkmc_event *log;
     int64_t log_cap;
     int64_t log_t0;

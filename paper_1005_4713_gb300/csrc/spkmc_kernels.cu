@@ -420,6 +420,16 @@ struct Line {
     unsigned long long w1; // 64-bit draw for the site rank
 };
 
+// x * 2^-53 for an integer 0 <= x < 2^53, assembled from its bits (exact;
+// the same value as the rounded conversion times 2^-53, with no FP64 work)
+__device__ __forceinline__ double u53_times_2m53(unsigned long long x)
+{
+    if (x == 0) return 0.0;
+    const int e = 63 - __clzll((long long)x); // top set bit, 0..52
+    const unsigned long long mant = (x << (52 - e)) & ((1ULL << 52) - 1ULL);
+    return __longlong_as_double((long long)(((unsigned long long)(1023 + e - 53) << 52) | mant));
+}
+
 // The class count words (total | lower-half count << 16) of the domain staged
 // in the slot at byte offset `off`.
 __device__ __forceinline__ uint32_t *slot_counts(unsigned char *stage, int off, int item_bytes)
@@ -454,17 +464,22 @@ __device__ void phase_a(const LaunchParams &P, CtaShared &S, unsigned char *stag
                 unsigned long long w[4];
                 philox4x64_10((unsigned long long)t, (unsigned long long)k, 1ULL, 0ULL, Ld.seed, 0ULL,
                               w);
-                const double u01 = __ull2double_rn(w[0] >> 11) * 0x1p-53;
+                const double u01 = u53_times_2m53(w[0] >> 11);
                 const uint32_t cw[kClasses] = {(uint32_t)n0.x, (uint32_t)n0.y, (uint32_t)n0.z, (uint32_t)n0.w,
                                                (uint32_t)n1.x, (uint32_t)n1.y, (uint32_t)n1.z, (uint32_t)n1.w,
                                                (uint32_t)n2.x, (uint32_t)n2.y, (uint32_t)n2.z, (uint32_t)n2.w,
                                                (uint32_t)n3.x, (uint32_t)n3.y};
+                // the products fl(n_c r_c) come from the lattice's table
+                const int tstride = Ld.d * Ld.d * Ld.d + 1;
+                double prod[kClasses];
+#pragma unroll
+                for (int c = 0; c < kClasses; ++c) prod[c] = __ldg(Ld.nrate + c * tstride + (cw[c] & 0xFFFFu));
                 double cum[kClasses];
-                double acc = __dmul_rn((double)(cw[0] & 0xFFFFu), __ldg(&Ld.rate[0]));
+                double acc = prod[0];
                 cum[0] = acc;
 #pragma unroll
                 for (int c = 1; c < kClasses; ++c) {
-                    acc = __dadd_rn(acc, __dmul_rn((double)(cw[c] & 0xFFFFu), __ldg(&Ld.rate[c])));
+                    acc = __dadd_rn(acc, prod[c]);
                     cum[c] = acc;
                 }
                 if (keep) {

@@ -103,9 +103,11 @@ def test_resolve_domain_edge_none():
 def test_bytes_required():
     p = sp.make_params(1024, 16)
     # domain blocks: rows (L^3/8 bytes) and 6 ghost faces of d 16-bit words;
-    # counts: 64 B per domain; scratch: 192 B per active domain
+    # counts: 64 B per domain; scratch: 192 B per active domain; the table
+    # of products fl(n r_c), 14 x (d^3 + 1) doubles rounded up to 256 B
     K = 64 ** 3
-    expect = 1024 ** 3 // 8 + K * 6 * 16 * 2 + K * 64 + (K // 8) * 192
+    table = -(-14 * (16 ** 3 + 1) * 8 // 256) * 256
+    expect = 1024 ** 3 // 8 + K * 6 * 16 * 2 + K * 64 + (K // 8) * 192 + table
     assert sp.spkmc_bytes_required(p) == expect
     assert sp.spkmc_bytes_required(sp.make_params(16, 3)) == 0
 

@@ -38,8 +38,8 @@ def test_served_results_equal_solo_runs():
 
 def test_admission_respects_a_small_memory_budget():
     reqs = small_stream(n=12, seed=3)
-    p = sp.make_params(48, wl.default_edge(48))
-    budget = 2 * sp.spkmc_bytes_required(p) + 1
+    largest = max(sp.spkmc_bytes_required(sp.make_params(r.spec.L, r.spec.d)) for r in reqs)
+    budget = 2 * largest + 1  # at most two of the largest at a time
     srv = serve.Server(budget_bytes=budget, capacity=16, step_cycles=50)
     stats = srv.serve(reqs, realtime=False)
     assert stats.peak_bytes <= budget

@@ -547,21 +547,25 @@ __device__ __forceinline__ void clock_catch_up(const LaunchParams &P, CtaShared 
     }
 }
 
-// Rank the sites of class w.cls in the half w.half of the domain (z < d/2
-// or z >= d/2) in ascending local index and return the w.j-th,
-// cooperatively in the group of 8 lanes (octet: lanes q, q+4, ..., q+28 with
-// q = lane % 4) that holds `lane`; -1 if the half has fewer such sites.  A
-// warp works on 4 domains at once.
+// The sites of class w.cls in the half w.half of the domain (z < d/2 or
+// z >= d/2) held by octet lane o (lanes q, q+4, ..., q+28 with q = lane % 4
+// work on one domain; lane o takes the o-th eighth of the half's rows, in
+// ascending local index): up to 8 words of class masks, and the local index
+// of bit b of word i, base + i * stride + b + offset.  No collective: the
+// four domains of a warp may have different edges.
+struct ClassBits {
+    uint32_t m[8];
+    int nw, base, stride, offset;
+};
+
 template <int D>
-__device__ int select_site(const WorkItem &w, const unsigned char *stage, int lane)
+__device__ __forceinline__ void class_bits(const WorkItem &w, const unsigned char *stage, int o, ClassBits &cb)
 {
     const uint16_t *st = reinterpret_cast<const uint16_t *>(stage + w.off);
-    const int o = lane >> 2;
-    const unsigned grp = 0x11111111u << (lane & 3);
     const int sig = w.cls >= 7, us = w.cls - 7 * sig;
     if constexpr (D == 16) {
-        // octet lane o holds the plane z = 8 half + o as 8 words of two
-        // 16-site rows: bit b of word p is site 16 (16 z + 2p) + b
+        // lane o holds the plane z = 8 half + o as 8 words of two 16-site
+        // rows: bit b of word p is site 16 (16 z + 2p) + b
         const uint16_t *g = st + 256;
         const int z = 8 * w.half + o;
         uint32_t cur[8], zm[8], zp[8];
@@ -579,8 +583,6 @@ __device__ int select_site(const WorkItem &w, const unsigned char *stage, int la
         }
         const uint32_t below = g[2 * 16 + z], above = g[3 * 16 + z];
         const uint32_t hxm = g[0 * 16 + z], hxp = g[1 * 16 + z];
-        uint32_t m[8];
-        int tot = 0;
 #pragma unroll
         for (int p = 0; p < 8; ++p) {
             const int y = 2 * p;
@@ -599,77 +601,75 @@ __device__ int select_site(const WorkItem &w, const unsigned char *stage, int la
             mm &= (us & 1) ? u0 : ~u0;
             mm &= (us & 2) ? u1 : ~u1;
             mm &= (us & 4) ? u2 : ~u2;
-            m[p] = mm;
-            tot += __popc(mm);
+            cb.m[p] = mm;
         }
-        int incl = tot;
-#pragma unroll
-        for (int off = 1; off < 8; off <<= 1) {
-            const int v = __shfl_up_sync(kFull, incl, 4 * off);
-            if (o >= off) incl += v;
-        }
-        const int excl = incl - tot;
-        const bool mine = w.j >= excl && w.j < incl;
-        const unsigned who = __ballot_sync(kFull, mine) & grp;
-        int site = 0;
-        if (mine) {
-            int jj = w.j - excl;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int pc = __popc(m[q]);
-                if (jj >= 0 && jj < pc) {
-                    uint32_t bits = m[q];
-                    for (int r = 0; r < jj; ++r) bits &= bits - 1;
-                    site = 16 * (16 * z + 2 * q) + (__ffs(bits) - 1);
-                }
-                jj -= pc;
-            }
-        }
-        site = __shfl_sync(kFull, site, who ? __ffs(who) - 1 : lane);
-        return who ? site : -1;
+        cb.nw = 8;
+        cb.base = 256 * z;
+        cb.stride = 32;
+        cb.offset = 0;
     } else {
-        constexpr int kHalfRows = D * D / 2;                   // rows y + D z with z in the half
+        constexpr int kHalfRows = D * D / 2;                     // rows y + D z with z in the half
         constexpr int kRpl = kHalfRows >= 8 ? kHalfRows / 8 : 1; // rows per octet lane, contiguous
-        static_assert(D % kRpl == 0, "the rows of an octet lane lie in one plane");
+        static_assert(kRpl <= 8, "at most 8 words per lane");
         const bool on = (kHalfRows >= 8) || (o < kHalfRows);
-        const int r0 = w.half * kHalfRows;
-        const int rl = r0 + o * kRpl, zl = rl / D, yl = rl % D; // first row of this lane
-        uint32_t m[kRpl];
-        int tot = 0;
+        const int rl = w.half * kHalfRows + o * kRpl; // first row of this lane
+#pragma unroll
+        for (int i = 0; i < 8; ++i) cb.m[i] = 0;
 #pragma unroll
         for (int i = 0; i < kRpl; ++i) {
-            m[i] = 0;
-            if (on) {
-                m[i] = class_mask<D>(classify_row<D>(st, yl + i, zl), w.cls);
-                tot += __popc(m[i]);
-            }
+            const int r = rl + i;
+            if (on) cb.m[i] = class_mask<D>(classify_row<D>(st, r % D, r / D), w.cls);
         }
-        int incl = tot;
-#pragma unroll
-        for (int off = 1; off < 8; off <<= 1) {
-            const int v = __shfl_up_sync(kFull, incl, 4 * off);
-            if (o >= off) incl += v;
-        }
-        const int excl = incl - tot;
-        const bool mine = w.j >= excl && w.j < incl;
-        const unsigned who = __ballot_sync(kFull, mine) & grp;
-        int site = 0;
-        if (mine) {
-            int jj = w.j - excl;
-#pragma unroll
-            for (int i = 0; i < kRpl; ++i) {
-                const int pc = __popc(m[i]);
-                if (jj >= 0 && jj < pc) {
-                    uint32_t bits = m[i];
-                    for (int r = 0; r < jj; ++r) bits &= bits - 1;
-                    site = D * (r0 + o * kRpl + i) + (__ffs(bits) - 1) - 1;
-                }
-                jj -= pc;
-            }
-        }
-        site = __shfl_sync(kFull, site, who ? __ffs(who) - 1 : lane);
-        return who ? site : -1;
+        cb.nw = on ? kRpl : 0;
+        cb.base = D * rl;
+        cb.stride = D;
+        cb.offset = -1; // bit x + 1 of a classified row is site x
     }
+}
+
+// Rank the sites of class w.cls in the half w.half of the domain in
+// ascending local index and return the w.j-th (-1 if the half has fewer),
+// cooperatively in the octet that holds `lane`.  Every lane of the warp
+// calls this together (one domain per octet, any mix of edges).
+__device__ __forceinline__ int select_site(const WorkItem &w, const unsigned char *stage, int lane)
+{
+    const int o = lane >> 2;
+    const unsigned grp = 0x11111111u << (lane & 3);
+    ClassBits cb;
+    switch (w.d) {
+    case 2: class_bits<2>(w, stage, o, cb); break;
+    case 4: class_bits<4>(w, stage, o, cb); break;
+    case 8: class_bits<8>(w, stage, o, cb); break;
+    default: class_bits<16>(w, stage, o, cb); break;
+    }
+    int tot = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) tot += __popc(cb.m[i]);
+    int incl = tot;
+#pragma unroll
+    for (int off = 1; off < 8; off <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, 4 * off);
+        if (o >= off) incl += v;
+    }
+    const int excl = incl - tot;
+    const bool mine = w.j >= excl && w.j < incl;
+    const unsigned who = __ballot_sync(kFull, mine) & grp;
+    int site = 0;
+    if (mine) {
+        int jj = w.j - excl;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int pc = __popc(cb.m[i]);
+            if (jj >= 0 && jj < pc) {
+                uint32_t bits = cb.m[i];
+                for (int r = 0; r < jj; ++r) bits &= bits - 1;
+                site = cb.base + i * cb.stride + (__ffs(bits) - 1) + cb.offset;
+            }
+            jj -= pc;
+        }
+    }
+    site = __shfl_sync(kFull, site, who ? __ffs(who) - 1 : lane);
+    return who ? site : -1;
 }
 
 // Global u16 load that is issued only when `pred` holds (no branch).
@@ -1048,13 +1048,7 @@ __device__ __forceinline__ void phase_b_round(const LaunchParams &P, CtaShared &
             const int i = base + (lane & 3);
             const bool valid = i < nwork;
             const WorkItem &w = S.work[valid ? i : base];
-            int site;
-            switch (w.d) {
-            case 2: site = select_site<2>(w, stage, lane); break;
-            case 4: site = select_site<4>(w, stage, lane); break;
-            case 8: site = select_site<8>(w, stage, lane); break;
-            default: site = select_site<16>(w, stage, lane); break;
-            }
+            const int site = select_site(w, stage, lane);
             if (valid && lane < 4) {
                 S.work[i].site = site;
                 if (site < 0) raise_error(P.err, SPKMC_EINTERNAL);

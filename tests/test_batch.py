@@ -91,3 +91,24 @@ def test_many_small_lattices_in_one_launch():
             assert np.array_equal(b.spins(slot), st.spins)
             o = b.observables(slot)
             assert (o.n_flip, o.n_null) == (st.n_flip, st.n_null)
+
+
+@pytest.mark.parametrize("kw", [dict(max_ctas=1), dict(items_per_cta=5)])
+def test_mixed_edges_share_warps(kw):
+    """Lattices of every edge in few CTAs: the four domains a warp searches
+    together belong to lattices of different edges (the per-octet branch of
+    the site search); each lattice still equals its oracle run."""
+    specs = [wl.LatticeSpec(L=8, d=2, seed=71), wl.LatticeSpec(L=16, d=4, seed=72, T=4.0),
+             wl.LatticeSpec(L=16, d=8, seed=73, H=0.1), wl.LatticeSpec(L=32, d=16, seed=74),
+             wl.LatticeSpec(L=12, d=2, seed=75, T=3.0), wl.LatticeSpec(L=32, d=8, seed=76),
+             wl.LatticeSpec(L=8, d=4, seed=77), wl.LatticeSpec(L=64, d=16, seed=78, cold=True)]
+    n = 40
+    with sp.Batch(len(specs), sp.make_config(**kw)) as b:
+        slots = [b.admit(s.L, s.d, s.J, s.H, s.T, s.seed, cold=s.cold) for s in specs]
+        b.run(n)
+        for s, slot in zip(specs, slots):
+            st = oracle.State(s.L, s.d, s.J, s.H, s.T, s.seed, cold=s.cold)
+            st.run(n)
+            o = b.observables(slot)
+            assert (o.n_flip, o.n_null) == (st.n_flip, st.n_null)
+            assert np.array_equal(b.spins(slot), st.spins)

@@ -63,7 +63,7 @@ def lib():
             L.oracle_class_counts.restype = None
             L.oracle_spkmc_run.argtypes = [_i32, _i32, _dbl, _dbl, _dbl, _u64, _ptr,
                                            _i64, _i64, _ptr, _ptr, _ptr, _ptr, _ptr, _i32,
-                                           _i32, _ptr]
+                                           _i32, _ptr, _i32]
             L.oracle_spkmc_run.restype = _i32
             L.oracle_rmax_bounds.argtypes = [_i32, _dbl, _dbl, _dbl, _ptr, _ptr]
             L.oracle_rmax_bounds.restype = None
@@ -122,6 +122,7 @@ def class_counts(L: int, d: int, s: np.ndarray) -> np.ndarray:
 
 
 RMAX_EXACT, RMAX_PRESCRIBED, RMAX_LEARNED = 0, 1, 2
+SUB_8_ROTATING, SUB_2_RANDOM = 0, 1
 
 
 class BoundExceeded(RuntimeError):
@@ -143,11 +144,15 @@ class State:
 
     ``rmax_mode`` picks the rate the frequency lines are padded to: the exact
     R_max of the cycle (Sec. 3.1 step 2) or a bound of Sec. 3.2 step 4b.
-    ``rmax_hist[i]`` holds the exact R_max of cycle ``cycle - 8 + i``."""
+    ``rmax_hist[i]`` holds the exact R_max of cycle ``cycle - 8 + i``.
+    ``sublattice``: eight colours in rotation, or the paper's two colours
+    drawn at random each cycle (Sec. 3.2 step 4a)."""
 
-    def __init__(self, L, d, J, H, T, seed, cold=False, spins=None, rmax_mode=RMAX_EXACT):
+    def __init__(self, L, d, J, H, T, seed, cold=False, spins=None, rmax_mode=RMAX_EXACT,
+                 sublattice=SUB_8_ROTATING):
         self.L, self.d, self.J, self.H, self.T, self.seed = L, d, J, H, T, seed
         self.rmax_mode = rmax_mode
+        self.sublattice = sublattice
         self.rmax_hist = np.zeros(8, dtype=np.float64)
         self.spins = (init_spins(L, seed, cold) if spins is None
                       else np.array(spins, dtype=np.int8, copy=True))
@@ -159,7 +164,8 @@ class State:
 
     @property
     def k_act(self):
-        return (self.L // self.d // 2) ** 3
+        nd = self.L // self.d
+        return (nd // 2) ** 3 if self.sublattice == SUB_8_ROTATING else nd ** 3 // 2
 
     def run(self, ncycles: int, log: bool = False, threads: int = 1):
         """Advance ``ncycles`` cycles.  With ``log`` returns an int32 array of
@@ -173,7 +179,7 @@ class State:
                                     _p(self.spins), self.cycle, ncycles, _p(clock),
                                     _p(nf), _p(nn), _p(fx),
                                     _p(ev) if log else None, threads,
-                                    self.rmax_mode, _p(self.rmax_hist))
+                                    self.rmax_mode, _p(self.rmax_hist), self.sublattice)
         if rc == -2:
             raise BoundExceeded("an active domain exceeded the R_max bound")
         if rc != 0:

@@ -21,7 +21,10 @@
  *   - sites (X,Y,Z), global index g = X + L*(Y + L*Z), spin +1/-1;
  *   - domain edge d, nd = L/d domains per axis (nd even), domain index
  *     k = dx + nd*(dy + nd*dz), local site index l = x + d*(y + d*z);
- *   - colour(k) = (dx&1) | (dy&1)<<1 | (dz&1)<<2; cycle t activates colour t%8;
+ *   - eight colours (default): colour(k) = (dx&1) | (dy&1)<<1 | (dz&1)<<2 and
+ *     cycle t activates colour t%8; two colours (the paper's own scheme):
+ *     colour(k) = (dx+dy+dz)&1 and cycle t activates the colour given by the
+ *     top bit of Philox word 0 at counter (t, 0, 5, 0);
  *   - u = number of up neighbours (0..6), S = 2u-6, class c = 7*[sigma=+1] + u;
  *   - Glauber rate r(sigma,S) = 1/(1+exp(2*sigma*(J*S+H)/T)) (lambda = 1);
  *   - Philox4x64-10 with key (seed, 0); counters (t, k, 1, 0) for the event of
@@ -231,6 +234,36 @@ void oracle_rmax_bounds(int d, double J, double H, double T, double *prescribed,
     *margin = a + 12.0 * b;
 }
 
+/* Sec. 3.2, step 4a: the sublattice of cycle t and its a-th domain, in
+ * ascending domain index.  Eight colours: a deterministic rotation over the
+ * 2x2x2 parity classes of (dx, dy, dz) (a = ix + h (iy + h iz), dx = 2 ix + cx,
+ * ...).  Two colours: the chessboard (dx+dy+dz) mod 2, drawn at random each
+ * cycle; in each (dy, dz) row of domains the active ones are every other dx. */
+#define ORACLE_SUB_8_ROTATING 0
+#define ORACLE_SUB_2_RANDOM 1
+
+static int cycle_colour(int sublattice, int64_t t, uint64_t seed)
+{
+    if (sublattice == ORACLE_SUB_8_ROTATING) return (int)(t % 8);
+    uint64_t w[4];
+    oracle_philox((uint64_t)t, 0, 5, 0, seed, 0, w);
+    return (int)(w[0] >> 63);
+}
+
+static void active_domain(int sublattice, int nd, int64_t a, int c, int *dx, int *dy, int *dz)
+{
+    const int h = nd / 2;
+    if (sublattice == ORACLE_SUB_8_ROTATING) {
+        *dx = 2 * (int)(a % h) + (c & 1);
+        *dy = 2 * (int)((a / h) % h) + ((c >> 1) & 1);
+        *dz = 2 * (int)(a / ((int64_t)h * h)) + ((c >> 2) & 1);
+    } else {
+        *dy = (int)((a / h) % nd);
+        *dz = (int)(a / ((int64_t)h * nd));
+        *dx = 2 * (int)(a % h) + ((*dy + *dz + c) & 1);
+    }
+}
+
 /* rmax_hist[i] (in/out, may be NULL) is the exact R_max of cycle t0 - 8 + i,
  * 0 where that cycle was not run.  Returns -1 for invalid arguments and -2
  * if a bound of Sec. 3.2 is exceeded by an active domain (the tolerance
@@ -239,17 +272,21 @@ int oracle_spkmc_run(int L, int d, double J, double H, double T, uint64_t seed,
                      int8_t *s, int64_t t0, int64_t ncycles,
                      double *clock, int64_t *n_flip, int64_t *n_null,
                      uint64_t null_fx[2], int32_t *events, int nthreads,
-                     int rmax_mode, double *rmax_hist)
+                     int rmax_mode, double *rmax_hist, int sublattice)
 {
     if (d < 2 || L <= 0 || L % (2 * d) != 0 || !(T > 0.0)) return -1;
     if (rmax_mode < ORACLE_RMAX_EXACT || rmax_mode > ORACLE_RMAX_LEARNED) return -1;
+    if (sublattice != ORACLE_SUB_8_ROTATING && sublattice != ORACLE_SUB_2_RANDOM) return -1;
+    /* the learned bound rests on the eight-colour rotation (one visit of
+     * every colour in any eight cycles) */
+    if (sublattice == ORACLE_SUB_2_RANDOM && rmax_mode == ORACLE_RMAX_LEARNED) return -1;
     double hist_local[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     double *hist = rmax_hist ? rmax_hist : hist_local;
     double R_prescribed, R_margin;
     oracle_rmax_bounds(d, J, H, T, &R_prescribed, &R_margin);
     const int nd = L / d;
     const int h = nd / 2;
-    const int64_t Kact = (int64_t)h * h * h;
+    const int64_t Kact = sublattice == ORACLE_SUB_8_ROTATING ? (int64_t)h * h * h : (int64_t)h * nd * nd;
     const int64_t nsite = (int64_t)d * d * d;
 
     double rate[14];
@@ -272,8 +309,7 @@ int oracle_spkmc_run(int L, int d, double J, double H, double T, uint64_t seed,
 
     for (int64_t t = t0; t < t0 + ncycles; ++t) {
         /* Step 4a: the sublattice (colour) of this cycle. */
-        const int c = (int)(t % 8);
-        const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
+        const int c = cycle_colour(sublattice, t, seed);
 
         /* Step 1: frequency line of every active domain, R_k = sum_c n_c r_c,
          * summed in class order 0..13. */
@@ -281,9 +317,8 @@ int oracle_spkmc_run(int L, int d, double J, double H, double T, uint64_t seed,
 #pragma omp parallel for num_threads(nthreads) schedule(static)
 #endif
         for (int64_t a = 0; a < Kact; ++a) {
-            int dx = 2 * (int)(a % h) + cx;
-            int dy = 2 * (int)((a / h) % h) + cy;
-            int dz = 2 * (int)(a / ((int64_t)h * h)) + cz;
+            int dx, dy, dz;
+            active_domain(sublattice, nd, a, c, &dx, &dy, &dz);
             int32_t *n = cnt + 14 * a;
             for (int q = 0; q < 14; ++q) n[q] = 0;
             for (int z = 0; z < d; ++z)
@@ -326,9 +361,8 @@ int oracle_spkmc_run(int L, int d, double J, double H, double T, uint64_t seed,
 #pragma omp parallel for num_threads(nthreads) schedule(static)
 #endif
         for (int64_t a = 0; a < Kact; ++a) {
-            int dx = 2 * (int)(a % h) + cx;
-            int dy = 2 * (int)((a / h) % h) + cy;
-            int dz = 2 * (int)(a / ((int64_t)h * h)) + cz;
+            int dx, dy, dz;
+            active_domain(sublattice, nd, a, c, &dx, &dy, &dz);
             int64_t k = dx + (int64_t)nd * (dy + (int64_t)nd * dz);
             uint64_t w[4];
             oracle_philox((uint64_t)t, (uint64_t)k, 1, 0, seed, 0, w);
@@ -355,9 +389,8 @@ int oracle_spkmc_run(int L, int d, double J, double H, double T, uint64_t seed,
         /* Step 6: the chosen flips become visible to the neighbours. */
         int64_t flips = 0, nulls = 0;
         for (int64_t a = 0; a < Kact; ++a) {
-            int dx = 2 * (int)(a % h) + cx;
-            int dy = 2 * (int)((a / h) % h) + cy;
-            int dz = 2 * (int)(a / ((int64_t)h * h)) + cz;
+            int dx, dy, dz;
+            active_domain(sublattice, nd, a, c, &dx, &dy, &dz);
             int64_t k = dx + (int64_t)nd * (dy + (int64_t)nd * dz);
             if (events) {
                 int32_t *e = events + 3 * ((t - t0) * Kact + a);

@@ -175,7 +175,22 @@ def brute_bound(mode, d, r, prev8, Rmax):
     return pres
 
 
-def brute_cycles(L, d, J, H, T, seed, s, ncycles, clock=0.0, t0=0, null_sum=None, mode=0, hist=None):
+def brute_colour(sublattice, t, seed):
+    """Sec. 3.2 step 4a: colour t mod 8 (rotation), or the top bit of a
+    Philox draw (two random colours)."""
+    if sublattice == 0:
+        return t % 8
+    return numpy_philox((t, 0, 5, 0), (seed, 0))[0] >> 63
+
+
+def brute_colour_of(sublattice, dx, dy, dz):
+    if sublattice == 0:
+        return (dx & 1) | (dy & 1) << 1 | (dz & 1) << 2
+    return (dx + dy + dz) & 1
+
+
+def brute_cycles(L, d, J, H, T, seed, s, ncycles, clock=0.0, t0=0, null_sum=None, mode=0, hist=None,
+                 sublattice=0):
     s = s.copy()
     hist = [0.0] * 8 if hist is None else hist
     r = [1.0 / (1.0 + math.exp(2.0 * (1 if c >= 7 else -1) * (J * (2 * (c % 7) - 6) + H) / T))
@@ -185,11 +200,11 @@ def brute_cycles(L, d, J, H, T, seed, s, ncycles, clock=0.0, t0=0, null_sum=None
     nflip = nnull = 0
     for t in range(t0, t0 + ncycles):
         cls = numpy_classes(L, s)
-        col = t % 8
+        col = brute_colour(sublattice, t, seed)
         active = []
         for k in range(nd ** 3):
             dx, dy, dz = k % nd, (k // nd) % nd, k // (nd * nd)
-            if (dx & 1) | (dy & 1) << 1 | (dz & 1) << 2 == col:
+            if brute_colour_of(sublattice, dx, dy, dz) == col:
                 active.append((k, dx, dy, dz))
         lines = []
         for k, dx, dy, dz in active:
@@ -508,6 +523,57 @@ def test_bound_exceeded_is_reported():
     st = oracle.State(16, 4, 1.0, 0.0, 4.5115, 95, rmax_mode=oracle.RMAX_LEARNED)
     st.rmax_hist[:] = 1.0
     with pytest.raises(oracle.BoundExceeded):
+        st.run(1)
+
+
+# --------------------------------------------------------------------------
+# The paper's two-colour sublattice, chosen at random each cycle (Sec. 3.2
+# step 4a)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("L,d,J,H,T,seed,cold", [
+    (8, 2, 1.0, 0.0, 4.5115, 101, False),
+    (8, 4, 1.0, 0.3, 3.0, 102, False),
+    (12, 3, -0.7, 0.1, 2.5, 103, False),
+    (8, 2, 1.0, 0.0, 4.5115, 104, True),
+])
+def test_two_colour_bruteforce(mode, L, d, J, H, T, seed, cold):
+    st = oracle.State(L, d, J, H, T, seed, cold=cold, rmax_mode=mode, sublattice=oracle.SUB_2_RANDOM)
+    s0 = st.spins.copy()
+    ev = st.run(19, log=True)
+    assert ev.shape == (19, (L // d) ** 3 // 2, 3)
+    sums = []
+    s_ref, log_ref, clock_ref, nf, nn = brute_cycles(L, d, J, H, T, seed, s0, 19, null_sum=sums, mode=mode,
+                                                     sublattice=1)
+    assert np.array_equal(ev, log_ref)
+    assert np.array_equal(st.spins, s_ref)
+    assert st.clock == pytest.approx(clock_ref, rel=1e-15)
+    assert (st.n_flip, st.n_null) == (nf, nn)
+    assert st.null_fx == sum(sums)
+
+
+def test_two_colour_draw_is_fair_and_not_alternating():
+    """The cycle colours come from the log: half of the cycles on each colour
+    (binomial, 5 sigma) and as many repeats as changes."""
+    L, d, n = 8, 2, 20000
+    st = oracle.State(L, d, 1.0, 0.0, 4.5115, 105, sublattice=oracle.SUB_2_RANDOM)
+    ev = st.run(n, log=True)
+    nd = L // d
+    k = ev[:, 0, 0]
+    col = ((k % nd) + (k // nd) % nd + k // (nd * nd)) & 1
+    ones = int(col.sum())
+    assert abs(ones - n / 2) < 5 * math.sqrt(n / 4)
+    same = int(np.sum(col[1:] == col[:-1]))
+    assert abs(same - (n - 1) / 2) < 5 * math.sqrt((n - 1) / 4)
+    # every active domain of a cycle has that cycle's colour
+    kk = ev[:, :, 0]
+    c_all = ((kk % nd) + (kk // nd) % nd + kk // (nd * nd)) & 1
+    assert np.all(c_all == col[:, None])
+
+
+def test_two_colour_rejects_the_learned_bound():
+    st = oracle.State(8, 2, 1.0, 0.0, 4.5115, 106, rmax_mode=oracle.RMAX_LEARNED, sublattice=oracle.SUB_2_RANDOM)
+    with pytest.raises(ValueError):
         st.run(1)
 
 

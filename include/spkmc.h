@@ -12,8 +12,12 @@
  *   - site (X,Y,Z), global index g = X + L*(Y + L*Z) (x fastest); spins are
  *     exchanged with the host as int8 +1/-1 in that order;
  *   - domain (dx,dy,dz), index k = dx + nd*(dy + nd*dz); local site
- *     l = x + d*(y + d*z); colour = (dx&1) | (dy&1)<<1 | (dz&1)<<2; cycle t
- *     works on colour t % 8 (Sec. 3.2 step 4a, deterministic rotation);
+ *     l = x + d*(y + d*z); sublattices of Sec. 3.2 step 4a
+ *     (spkmc_params.sublattice): eight colours, colour = (dx&1) | (dy&1)<<1 |
+ *     (dz&1)<<2, cycle t works on colour t % 8 (deterministic rotation, the
+ *     default); or two colours, colour = (dx+dy+dz) & 1, cycle t works on
+ *     the colour given by the top bit of Philox word 0 at counter (t, 0, 5, 0)
+ *     (the paper's random choice);
  *   - class of a site = 7*[sigma = +1] + (number of up neighbours), 0..13;
  *     rate r = 1/(1 + exp(2 sigma (J S + H) / T)), S = sum of the 6
  *     neighbour spins, lambda = 1, k_B = 1 (Eq. 3 read as Glauber dynamics);
@@ -84,6 +88,17 @@ extern "C" {
 #define SPKMC_RMAX_PRESCRIBED 1
 #define SPKMC_RMAX_LEARNED 2
 
+/* Sublattice scheme of Sec. 3.2 step 4a.  EIGHT_ROTATING: K/8 active domains
+ * per cycle, colours in rotation; class counts are kept up to date flip by
+ * flip.  TWO_RANDOM: K/2 active domains per cycle, colour drawn per cycle;
+ * an inactive site can then see flips in up to three neighbouring domains
+ * in one cycle, so the class counts of an active domain are recounted from
+ * its spins at the start of its cycle instead (the linear frequency-line
+ * evaluation of Sec. 3.1 step 1).  The LEARNED bound needs EIGHT_ROTATING
+ * (it relies on one visit of every colour in any eight cycles). */
+#define SPKMC_SUBLATTICE_8_ROTATING 0
+#define SPKMC_SUBLATTICE_2_RANDOM 1
+
 typedef struct spkmc_engine spkmc_t;
 typedef struct spkmc_batch spkmc_batch_t;
 
@@ -104,6 +119,8 @@ typedef struct spkmc_params {
     int32_t init;               /* SPKMC_INIT_HOT or SPKMC_INIT_COLD */
     int32_t rmax_mode;          /* SPKMC_RMAX_EXACT (default), _PRESCRIBED or _LEARNED */
     int64_t event_log_capacity; /* events kept (see spkmc_event); 0 = off */
+    int32_t sublattice;         /* SPKMC_SUBLATTICE_8_ROTATING (default) or _2_RANDOM */
+    int32_t reserved1;          /* 0 */
 } spkmc_params;
 
 /* Engine runtime: stream, allocator and launch geometry. */
@@ -163,7 +180,7 @@ typedef struct spkmc_state {
 typedef struct spkmc_info {
     int32_t L, domain_edge, nd, reserved;
     int64_t K;                  /* domains */
-    int64_t K_act;              /* active domains (events) per cycle = K/8 */
+    int64_t K_act;              /* active domains (events) per cycle: K/8, or K/2 with two colours */
     int64_t device_bytes;       /* device memory held for this lattice */
     int32_t grid_ctas;          /* CTAs of the persistent launch */
     int32_t threads_per_cta;

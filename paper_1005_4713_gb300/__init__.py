@@ -19,6 +19,7 @@ import numpy as np
 from . import _abi
 from ._abi import (SPKMC_EBOUND, SPKMC_EBUSY, SPKMC_ECUDA, SPKMC_EINTERNAL, SPKMC_EINVAL,  # noqa: F401
                    SPKMC_ENOMEM, SPKMC_RMAX_EXACT, SPKMC_RMAX_LEARNED, SPKMC_RMAX_PRESCRIBED,
+                   SPKMC_SUBLATTICE_2_RANDOM, SPKMC_SUBLATTICE_8_ROTATING,
                    SPKMC_INIT_COLD, SPKMC_INIT_HOT, SPKMC_OK, SPKMC_ETIMEOUT, spkmc_config,
                    spkmc_event, spkmc_info, spkmc_obs, spkmc_params, spkmc_state)
 
@@ -55,13 +56,15 @@ def _check(rc: int) -> None:
 
 
 def make_params(L, domain_edge=0, J=1.0, H=0.0, T=4.5115, seed=1, init=SPKMC_INIT_HOT,
-                event_log_capacity=0, rmax_mode=SPKMC_RMAX_EXACT) -> spkmc_params:
+                event_log_capacity=0, rmax_mode=SPKMC_RMAX_EXACT,
+                sublattice=SPKMC_SUBLATTICE_8_ROTATING) -> spkmc_params:
     p = spkmc_params()
     lib().spkmc_params_init(ctypes.byref(p))
     p.L, p.domain_edge, p.J, p.H, p.T, p.seed = int(L), int(domain_edge), float(J), float(H), float(T), int(seed)
     p.init = int(init)
     p.event_log_capacity = int(event_log_capacity)
     p.rmax_mode = int(rmax_mode)
+    p.sublattice = int(sublattice)
     return p
 
 
@@ -312,9 +315,11 @@ class Lattice:
     """One lattice on the GPU (owns a spkmc_t handle)."""
 
     def __init__(self, L, domain_edge=0, J=1.0, H=0.0, T=4.5115, seed=1, cold=False,
-                 event_log_capacity=0, config: spkmc_config | None = None, rmax_mode=SPKMC_RMAX_EXACT):
+                 event_log_capacity=0, config: spkmc_config | None = None, rmax_mode=SPKMC_RMAX_EXACT,
+                 sublattice=SPKMC_SUBLATTICE_8_ROTATING):
         self.params = make_params(L, domain_edge, J, H, T, seed,
-                                  SPKMC_INIT_COLD if cold else SPKMC_INIT_HOT, event_log_capacity, rmax_mode)
+                                  SPKMC_INIT_COLD if cold else SPKMC_INIT_HOT, event_log_capacity, rmax_mode,
+                                  sublattice)
         self.config = config
         self.h = spkmc_create_ex(self.params, config)
         info = spkmc_info_get(self.h)
@@ -380,9 +385,9 @@ class Batch:
         self.params = {}
 
     def admit(self, L, domain_edge=0, J=1.0, H=0.0, T=4.5115, seed=1, cold=False, cycles=-1,
-              event_log_capacity=0, rmax_mode=SPKMC_RMAX_EXACT) -> int:
+              event_log_capacity=0, rmax_mode=SPKMC_RMAX_EXACT, sublattice=SPKMC_SUBLATTICE_8_ROTATING) -> int:
         p = make_params(L, domain_edge, J, H, T, seed, SPKMC_INIT_COLD if cold else SPKMC_INIT_HOT,
-                        event_log_capacity, rmax_mode)
+                        event_log_capacity, rmax_mode, sublattice)
         slot = spkmc_batch_admit(self.b, p, cycles)
         self.params[slot] = p
         return slot

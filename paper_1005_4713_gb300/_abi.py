@@ -20,6 +20,8 @@ SPKMC_INIT_COLD = 1
 SPKMC_RMAX_EXACT = 0
 SPKMC_RMAX_PRESCRIBED = 1
 SPKMC_RMAX_LEARNED = 2
+SPKMC_SUBLATTICE_8_ROTATING = 0
+SPKMC_SUBLATTICE_2_RANDOM = 1
 
 SPKMC_NOALLOC_SCRATCH_BYTES = 16 << 20
 
@@ -34,7 +36,8 @@ class spkmc_params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("domain_edge", ctypes.c_int32), ("J", ctypes.c_double),
                 ("H", ctypes.c_double), ("T", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("init", ctypes.c_int32), ("rmax_mode", ctypes.c_int32),
-                ("event_log_capacity", ctypes.c_int64)]
+                ("event_log_capacity", ctypes.c_int64), ("sublattice", ctypes.c_int32),
+                ("reserved1", ctypes.c_int32)]
 
 
 class spkmc_config(ctypes.Structure):

@@ -94,6 +94,7 @@ void fill_physics(LatticeDesc &D, const spkmc_params *p, int d)
     host_rates(p->J, p->H, p->T, D.rate);
     host_bounds(d, D.rate, &D.rbound, &D.rmargin);
     D.rmode = p->rmax_mode;
+    D.sub2 = p->sublattice == SPKMC_SUBLATTICE_2_RANDOM;
 }
 
 // R_max history of spkmc_state (cycles t-8 .. t-1) <-> the device ring.
@@ -141,6 +142,11 @@ int check_params(const spkmc_params *p, int *d_out)
         p->rmax_mode != SPKMC_RMAX_LEARNED)
         return fail(SPKMC_EINVAL, "rmax_mode must be SPKMC_RMAX_EXACT, _PRESCRIBED or _LEARNED (got %d)",
                     p->rmax_mode);
+    if (p->sublattice != SPKMC_SUBLATTICE_8_ROTATING && p->sublattice != SPKMC_SUBLATTICE_2_RANDOM)
+        return fail(SPKMC_EINVAL, "sublattice must be SPKMC_SUBLATTICE_8_ROTATING or _2_RANDOM (got %d)",
+                    p->sublattice);
+    if (p->sublattice == SPKMC_SUBLATTICE_2_RANDOM && p->rmax_mode == SPKMC_RMAX_LEARNED)
+        return fail(SPKMC_EINVAL, "the learned R_max bound needs the eight-colour rotation");
     const long long nd = p->L / d;
     if (nd * nd * nd > (1LL << 31) - 1) return fail(SPKMC_EINVAL, "too many domains (L/d)^3 for int32 ids");
     *d_out = d;
@@ -163,12 +169,12 @@ std::vector<double> host_nrate(int d, const double r[kClasses])
     return t;
 }
 
-Sizes sizes_of(int L, int d, long long log_cap)
+Sizes sizes_of(int L, int d, long long log_cap, int sublattice)
 {
     Sizes s;
     const long long nd = L / d;
     s.K = nd * nd * nd;
-    s.Kact = s.K / 8;
+    s.Kact = sublattice == SPKMC_SUBLATTICE_2_RANDOM ? s.K / 2 : s.K / 8;
     auto up = [](long long b) { return (b + 255) & ~255LL; };
     s.cells_b = up(s.K * staged_bytes(d));
     s.counts_b = up(s.K * kCountStride * 4);
@@ -431,7 +437,7 @@ int admit(spkmc_batch *b, const spkmc_params *p, long long cycles, int slot_hint
     s.params = *p;
     s.params.domain_edge = d;
     s.d = d;
-    s.sz = sizes_of(p->L, d, p->event_log_capacity);
+    s.sz = sizes_of(p->L, d, p->event_log_capacity, p->sublattice);
     const long long bytes[5] = {s.sz.cells_b, s.sz.counts_b, s.sz.scratch_b, s.sz.log_b, s.sz.nrate_b};
     for (int i = 0; i < 5; ++i) {
         if (bytes[i] == 0) continue;
@@ -569,7 +575,13 @@ int run(spkmc_batch *b, long long cycles)
         P.item_bytes = stage_slot_bytes(dmax);
         P.round_items = cycle_round_items(dmax);
         P.exact_any = 0;
-        for (const Segment &sg : segs) P.exact_any |= b->slots[sg.slot].desc.rmode == SPKMC_RMAX_EXACT;
+        P.sub2_any = 0;
+        for (const Segment &sg : segs) {
+            P.exact_any |= b->slots[sg.slot].desc.rmode == SPKMC_RMAX_EXACT;
+            P.sub2_any |= b->slots[sg.slot].desc.sub2;
+        }
+        // two random colours: consecutive cycles may use face-adjacent colours
+        if (P.sub2_any) P.parity0 = -1;
         int rc = launch_cycles(P, (int)grid, b->stream, grid > 1);
         if (rc) return cuda_fail(cudaGetLastError(), "persistent cycle launch");
         b->last_grid = (int)grid;
@@ -760,7 +772,7 @@ int64_t spkmc_bytes_required(const spkmc_params *p)
 {
     int d = 0;
     if (check_params(p, &d) != SPKMC_OK) return 0;
-    return sizes_of(p->L, d, p->event_log_capacity).total();
+    return sizes_of(p->L, d, p->event_log_capacity, p->sublattice).total();
 }
 
 int spkmc_create(int32_t L, int32_t domain_edge, double J, double H, double T, uint64_t seed,
@@ -917,6 +929,9 @@ int spkmc_class_counts(spkmc_t *h, int32_t *host_counts, size_t n)
     DeviceGuard g(b->device);
     int rc = sync_and_check(b);
     if (rc) return rc;
+    // two-colour lattices keep no class counts between visits: count now
+    if (s.desc.sub2 && launch_count_classes(s.desc, 0, nullptr, b->stream) != SPKMC_OK)
+        return cuda_fail(cudaGetLastError(), "recount");
     std::vector<int32_t> tmp((size_t)(s.desc.K * kCountStride));
     CUDA_TRY(cudaMemcpyAsync(tmp.data(), s.desc.counts, tmp.size() * 4, cudaMemcpyDeviceToHost, b->stream),
              "read counts");
@@ -937,7 +952,9 @@ int spkmc_check_counts(spkmc_t *h, int64_t *mismatched)
     CUDA_TRY(cudaMemsetAsync(b->d_mismatch, 0, 8, b->stream), "clear");
     CUDA_TRY(cudaMemsetAsync(b->d_MB, 0, 2 * sizeof(long long), b->stream), "clear");
     const LatticeDesc &D = b->slots[h->slot].desc;
-    if ((rc = launch_count_classes(D, 1, b->d_mismatch, b->stream)) != SPKMC_OK)
+    // two-colour lattices keep no class counts between visits: refresh them
+    // (the ghost faces and M, B are still checked)
+    if ((rc = launch_count_classes(D, D.sub2 ? 0 : 1, b->d_mismatch, b->stream)) != SPKMC_OK)
         return cuda_fail(cudaGetLastError(), "recount");
     if ((rc = launch_ghosts(D, 1, b->d_mismatch, b->stream)) != SPKMC_OK)
         return cuda_fail(cudaGetLastError(), "ghost check");
@@ -1161,7 +1178,7 @@ extern "C" int spkmc_run_cycles_noalloc(const spkmc_params *p, int8_t *dev_spins
     if ((rc = noalloc_base(dev, &base)) != SPKMC_OK) return rc;
 
     // carve the array: tables first, then the lattice
-    const Sizes sz = sizes_of(p->L, d, 0);
+    const Sizes sz = sizes_of(p->L, d, 0, p->sublattice);
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
     size_t off = 0;
     LatticeDesc *d_desc = reinterpret_cast<LatticeDesc *>(base + off);
@@ -1245,6 +1262,8 @@ extern "C" int spkmc_run_cycles_noalloc(const spkmc_params *p, int8_t *dev_spins
         P.item_bytes = stage_slot_bytes(d);
         P.round_items = cycle_round_items(d);
         P.exact_any = p->rmax_mode == SPKMC_RMAX_EXACT;
+        P.sub2_any = D.sub2;
+        if (D.sub2) P.parity0 = -1;
         if (launch_cycles(P, (int)grid, s, grid > 1) != SPKMC_OK)
             return cuda_fail(cudaGetLastError(), "persistent cycle launch");
         left -= n;

@@ -54,7 +54,7 @@ struct LatticeDesc {
     int32_t L, d, nd, half;
     int64_t K, Kact;
     int32_t rmode;   // SPKMC_RMAX_*
-    int32_t pad;
+    int32_t sub2;    // two random colours (class counts recounted at each visit)
 };
 
 constexpr double kBoundSlack = 1.0 + 0x1p-32; // rounding cover of the R_max bounds
@@ -98,6 +98,8 @@ struct LaunchParams {
     int round_items;      // active domains per phase-B round (staging capacity)
     int item_bytes;       // staging bytes per domain (largest edge of the launch)
     int exact_any;        // some lattice pads to the exact R_max: reduce before the events
+    int sub2_any;         // some lattice uses two random colours: draw colours, recount
+    int pad;
 };
 
 // u16 words and bytes of one domain block (rows and ghost faces).

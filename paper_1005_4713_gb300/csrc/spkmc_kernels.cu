@@ -141,15 +141,27 @@ __device__ __forceinline__ void atomic_add_u128(unsigned long long *lo_p, unsign
 // ---------------------------------------------------------------------------
 // Geometry
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void active_domain(int half, long long a, int colour, int &dx, int &dy,
+// The a-th active domain (ascending index) of the cycle's colour (Sec. 3.2
+// step 4a).  Eight colours: the parity class `colour` of (dx, dy, dz).  Two
+// colours: (dx + dy + dz) mod 2 = colour, every other dx along each
+// (dy, dz) row.  a < K/2 < 2^30: 32-bit unsigned division is exact and much
+// cheaper.
+__device__ __forceinline__ void active_domain(const LatticeDesc &Ld, long long a, int colour, int &dx, int &dy,
                                               int &dz)
 {
-    // a < K/8 < 2^28: 32-bit unsigned division is exact and much cheaper
-    const unsigned ua = (unsigned)a, h = (unsigned)half;
-    const unsigned qx = ua / h, qy = qx / h;
-    dx = 2 * (int)(ua - qx * h) + (colour & 1);
-    dy = 2 * (int)(qx - qy * h) + ((colour >> 1) & 1);
-    dz = 2 * (int)qy + ((colour >> 2) & 1);
+    const unsigned ua = (unsigned)a, h = (unsigned)Ld.half;
+    const unsigned qx = ua / h;
+    if (Ld.sub2) {
+        const unsigned nd = (unsigned)Ld.nd, qz = qx / nd;
+        dy = (int)(qx - qz * nd);
+        dz = (int)qz;
+        dx = 2 * (int)(ua - qx * h) + ((dy + dz + colour) & 1);
+    } else {
+        const unsigned qy = qx / h;
+        dx = 2 * (int)(ua - qx * h) + (colour & 1);
+        dy = 2 * (int)(qx - qy * h) + ((colour >> 1) & 1);
+        dz = 2 * (int)qy + ((colour >> 2) & 1);
+    }
 }
 
 __device__ __forceinline__ long long domain_index(int nd, int dx, int dy, int dz)
@@ -274,6 +286,7 @@ struct CtaShared {
     unsigned long long seg_fxhi[kMaxSegPerCta];
     unsigned long long seg_dM[kMaxSegPerCta];
     unsigned long long seg_dB[kMaxSegPerCta];
+    int seg_colour[kMaxSegPerCta];    // colour of the running cycle (two-colour lattices)
     double seg_nlogxi[kMaxSegPerCta]; // -ln(xi) of the running cycle
     double seg_rnow[kMaxSegPerCta];   // R_max of the running cycle
     int seg_tick[kMaxSegPerCta];      // the clock of this lattice moves in this round
@@ -286,6 +299,13 @@ struct CtaShared {
     int ok;
     WorkItem work[kThreads];
 };
+
+// Colour of cycle t of segment ls: t mod 8 (rotation), or the draw of the
+// cycle for a two-colour lattice (made at the start of the cycle).
+__device__ __forceinline__ int cycle_colour(const CtaShared &S, const LatticeDesc &Ld, int ls, long long t)
+{
+    return Ld.sub2 ? S.seg_colour[ls] : (int)(t & 7);
+}
 
 __device__ __forceinline__ int find_segment(const CtaShared &S, long long q)
 {
@@ -455,7 +475,7 @@ __device__ void phase_a(const LaunchParams &P, CtaShared &S, unsigned char *stag
                 const long long a = q - S.seg_base[ls];
                 const long long t = S.seg_t0[ls] + g;
                 int dx, dy, dz;
-                active_domain(Ld.half, a, (int)(t & 7), dx, dy, dz);
+                active_domain(Ld, a, cycle_colour(S, Ld, ls, t), dx, dy, dz);
                 const long long k = domain_index(Ld.nd, dx, dy, dz);
                 const int4 *cp = reinterpret_cast<const int4 *>(Ld.counts + k * kCountStride);
                 const int4 n0 = __ldcg(cp), n1 = __ldcg(cp + 1), n2 = __ldcg(cp + 2),
@@ -547,6 +567,50 @@ __device__ __forceinline__ void clock_catch_up(const LaunchParams &P, CtaShared 
     }
 }
 
+// Load plane z of a staged D = 16 block as 8 words of two rows (bit b of
+// word p is site (b mod 16, 2p + b/16, z)), with the planes below and above
+// (the z ghost faces at the ends).
+__device__ __forceinline__ void load_plane16(const uint16_t *st, int z, uint32_t cur[8], uint32_t zm[8],
+                                             uint32_t zp[8])
+{
+    const uint16_t *g = st + 256;
+    const uint4 *pc = reinterpret_cast<const uint4 *>(st + 16 * z);
+    const uint4 *pm = reinterpret_cast<const uint4 *>(z > 0 ? st + 16 * (z - 1) : g + 4 * 16);
+    const uint4 *pp = reinterpret_cast<const uint4 *>(z < 15 ? st + 16 * (z + 1) : g + 5 * 16);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const uint4 c = pc[i], a = pm[i], b = pp[i];
+        cur[4 * i] = c.x; cur[4 * i + 1] = c.y; cur[4 * i + 2] = c.z; cur[4 * i + 3] = c.w;
+        zm[4 * i] = a.x; zm[4 * i + 1] = a.y; zm[4 * i + 2] = a.z; zm[4 * i + 3] = a.w;
+        zp[4 * i] = b.x; zp[4 * i + 1] = b.y; zp[4 * i + 2] = b.z; zp[4 * i + 3] = b.w;
+    }
+}
+
+// Spins and bit-sliced up counts (u = u0 + 2 u1 + 4 u2) of the 32 sites of
+// word p of a D = 16 plane: the x neighbours by shifts with the x halo bits
+// (hxm, hxp: bit y), the y neighbours from the adjacent words or the y halo
+// words (below, above), the z neighbours from the planes around.
+__device__ __forceinline__ RowPlanes pair_planes(const uint32_t cur[8], const uint32_t zm[8], const uint32_t zp[8],
+                                                 uint32_t below, uint32_t above, uint32_t hxm, uint32_t hxp, int p)
+{
+    const int y = 2 * p;
+    const uint32_t s = cur[p];
+    const uint32_t xm = ((s << 1) & 0xFFFEFFFEu) | ((hxm >> y) & 1u) | (((hxm >> (y + 1)) & 1u) << 16);
+    const uint32_t xp = ((s >> 1) & 0x7FFF7FFFu) | (((hxp >> y) & 1u) << 15) | (((hxp >> (y + 1)) & 1u) << 31);
+    const uint32_t ym = (s << 16) | (p > 0 ? (cur[p - 1] >> 16) : below);
+    const uint32_t yp = (s >> 16) | ((p < 7 ? (cur[p + 1] & 0xFFFFu) : above) << 16);
+    const uint32_t e = zm[p], f = zp[p];
+    const uint32_t s1 = xm ^ xp ^ ym, c1 = (xm & xp) | (ym & (xm ^ xp));
+    const uint32_t s2 = yp ^ e ^ f, c2 = (yp & e) | (f & (yp ^ e));
+    const uint32_t k2 = s1 & s2;
+    RowPlanes q;
+    q.s = s;
+    q.u0 = s1 ^ s2;
+    q.u1 = c1 ^ c2 ^ k2;
+    q.u2 = (c1 & c2) | (k2 & (c1 ^ c2));
+    return q;
+}
+
 // The sites of class w.cls in the half w.half of the domain (z < d/2 or
 // z >= d/2) held by octet lane o (lanes q, q+4, ..., q+28 with q = lane % 4
 // work on one domain; lane o takes the o-th eighth of the half's rows, in
@@ -569,38 +633,16 @@ __device__ __forceinline__ void class_bits(const WorkItem &w, const unsigned cha
         const uint16_t *g = st + 256;
         const int z = 8 * w.half + o;
         uint32_t cur[8], zm[8], zp[8];
-        {
-            const uint4 *pc = reinterpret_cast<const uint4 *>(st + 16 * z);
-            const uint4 *pm = reinterpret_cast<const uint4 *>(z > 0 ? st + 16 * (z - 1) : g + 4 * 16);
-            const uint4 *pp = reinterpret_cast<const uint4 *>(z < 15 ? st + 16 * (z + 1) : g + 5 * 16);
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const uint4 c = pc[i], a = pm[i], b = pp[i];
-                cur[4 * i] = c.x; cur[4 * i + 1] = c.y; cur[4 * i + 2] = c.z; cur[4 * i + 3] = c.w;
-                zm[4 * i] = a.x; zm[4 * i + 1] = a.y; zm[4 * i + 2] = a.z; zm[4 * i + 3] = a.w;
-                zp[4 * i] = b.x; zp[4 * i + 1] = b.y; zp[4 * i + 2] = b.z; zp[4 * i + 3] = b.w;
-            }
-        }
+        load_plane16(st, z, cur, zm, zp);
         const uint32_t below = g[2 * 16 + z], above = g[3 * 16 + z];
         const uint32_t hxm = g[0 * 16 + z], hxp = g[1 * 16 + z];
 #pragma unroll
         for (int p = 0; p < 8; ++p) {
-            const int y = 2 * p;
-            const uint32_t s = cur[p];
-            const uint32_t xm = ((s << 1) & 0xFFFEFFFEu) | ((hxm >> y) & 1u) | (((hxm >> (y + 1)) & 1u) << 16);
-            const uint32_t xp = ((s >> 1) & 0x7FFF7FFFu) | (((hxp >> y) & 1u) << 15) |
-                                (((hxp >> (y + 1)) & 1u) << 31);
-            const uint32_t ym = (s << 16) | (p > 0 ? (cur[p - 1] >> 16) : below);
-            const uint32_t yp = (s >> 16) | ((p < 7 ? (cur[p + 1] & 0xFFFFu) : above) << 16);
-            const uint32_t e = zm[p], f = zp[p];
-            const uint32_t s1 = xm ^ xp ^ ym, c1 = (xm & xp) | (ym & (xm ^ xp));
-            const uint32_t s2 = yp ^ e ^ f, c2 = (yp & e) | (f & (yp ^ e));
-            const uint32_t k2 = s1 & s2;
-            const uint32_t u0 = s1 ^ s2, u1 = c1 ^ c2 ^ k2, u2 = (c1 & c2) | (k2 & (c1 ^ c2));
-            uint32_t mm = sig ? s : ~s;
-            mm &= (us & 1) ? u0 : ~u0;
-            mm &= (us & 2) ? u1 : ~u1;
-            mm &= (us & 4) ? u2 : ~u2;
+            const RowPlanes q = pair_planes(cur, zm, zp, below, above, hxm, hxp, p);
+            uint32_t mm = sig ? q.s : ~q.s;
+            mm &= (us & 1) ? q.u0 : ~q.u0;
+            mm &= (us & 2) ? q.u1 : ~q.u1;
+            mm &= (us & 4) ? q.u2 : ~q.u2;
             cb.m[p] = mm;
         }
         cb.nw = 8;
@@ -672,6 +714,162 @@ __device__ __forceinline__ int select_site(const WorkItem &w, const unsigned cha
     return who ? site : -1;
 }
 
+// Class counts of a set of sites: for each up count u, the sites of spin +1
+// and of spin -1 among the bits `valid` of the planes, each counted as inc
+// (1, plus 1 << 16 for sites in the lower half of the domain).
+__device__ __forceinline__ void count_planes(const RowPlanes &q, uint32_t valid, uint32_t inc, uint32_t part[kClasses])
+{
+#pragma unroll
+    for (int u = 0; u < 7; ++u) {
+        uint32_t e = valid;
+        e &= (u & 1) ? q.u0 : ~q.u0;
+        e &= (u & 2) ? q.u1 : ~q.u1;
+        e &= (u & 4) ? q.u2 : ~q.u2;
+        part[7 + u] += (uint32_t)__popc(e & q.s) * inc;
+        part[u] += (uint32_t)__popc(e & ~q.s) * inc;
+    }
+}
+
+// Octet lane o's share of the class count words of a staged block (lane o
+// takes the o-th eighth of the rows); no collective.
+template <int D>
+__device__ __forceinline__ void recount_part(const uint16_t *st, int o, uint32_t part[kClasses])
+{
+    if constexpr (D == 16) {
+        const uint16_t *g = st + 256;
+#pragma unroll
+        for (int pl = 0; pl < 2; ++pl) {
+            const int z = 2 * o + pl;
+            uint32_t cur[8], zm[8], zp[8];
+            load_plane16(st, z, cur, zm, zp);
+            const uint32_t below = g[2 * 16 + z], above = g[3 * 16 + z];
+            const uint32_t hxm = g[0 * 16 + z], hxp = g[1 * 16 + z];
+            const uint32_t inc = 1u + ((z < 8 ? 1u : 0u) << 16);
+#pragma unroll
+            for (int p = 0; p < 8; ++p) count_planes(pair_planes(cur, zm, zp, below, above, hxm, hxp, p), ~0u, inc, part);
+        }
+    } else {
+        constexpr int kRows = D * D;
+        constexpr int kRpl = kRows >= 8 ? kRows / 8 : 1;
+        constexpr uint32_t V = ((1u << D) - 1u) << 1;
+        if (kRows >= 8 || o < kRows) {
+#pragma unroll
+            for (int i = 0; i < kRpl; ++i) {
+                const int r = o * kRpl + i, z = r / D;
+                const uint32_t inc = 1u + ((z < D / 2 ? 1u : 0u) << 16);
+                count_planes(classify_row<D>(st, r % D, z), V, inc, part);
+            }
+        }
+    }
+}
+
+// Two-colour lattices (Sec. 3.2 step 4a with two random colours) keep no
+// class counts between visits: an inactive site can see flips in up to three
+// neighbouring domains in one cycle, so moving its class flip by flip would
+// need an order.  Their active domains are recounted here from the staged
+// blocks (the linear frequency-line evaluation of Sec. 3.1 step 1) and the
+// count words go back to global memory, where step 1 reads them.  A
+// one-round CTA finds its blocks already requested for the whole cycle.
+__device__ void phase_r(const LaunchParams &P, CtaShared &S, unsigned char *stage, long long g, long long lo,
+                        long long hi, unsigned &mbar_phase, bool early)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, o = lane >> 2;
+    __syncthreads();
+    for (long long rbase = lo; rbase < hi; rbase += P.round_items) {
+        const long long rend = rbase + P.round_items < hi ? rbase + P.round_items : hi;
+        if (early) {
+            if (S.early_bytes > 0) {
+                if (threadIdx.x == 0 && !mbar_wait_bounded(P, &S.mbar, mbar_phase))
+                    S.ok = 0; // copies never landed: leave without touching the area
+                mbar_phase ^= 1u;
+                __syncthreads();
+                if (threadIdx.x == 0) S.early_bytes = 0; // phase B finds the blocks in place
+                if (!*reinterpret_cast<volatile int *>(&S.ok)) return;
+            }
+        } else {
+            if (threadIdx.x == 0) S.bulk_bytes = 0;
+            __syncthreads();
+            const long long q = rbase + threadIdx.x;
+            const LatticeDesc *Ldp = nullptr;
+            long long k = 0;
+            int bytes = 0;
+            if (q < rend) {
+                const int ls = find_segment(S, q);
+                const LatticeDesc &Ld = P.desc[S.seg_slot[ls]];
+                if (Ld.sub2 && g < S.seg_part[ls]) {
+                    int dx, dy, dz;
+                    active_domain(Ld, q - S.seg_base[ls], cycle_colour(S, Ld, ls, S.seg_t0[ls] + g), dx, dy, dz);
+                    k = domain_index(Ld.nd, dx, dy, dz);
+                    Ldp = &Ld;
+                    bytes = staged_bytes(Ld.d);
+                }
+            }
+            const int wb = __reduce_add_sync(kFull, bytes);
+            if (lane == 0 && wb) atomicAdd(&S.bulk_bytes, wb);
+            __syncthreads();
+            const int total = S.bulk_bytes;
+            if (total > 0) {
+                if (threadIdx.x == 0) mbar_expect_tx(&S.mbar, (unsigned)total);
+                __syncthreads();
+                if (Ldp) {
+                    asm volatile("fence.proxy.async.global;" ::: "memory");
+                    bulk_copy_g2s(stage + (q - rbase) * P.item_bytes, Ldp->cells + k * block_words(Ldp->d), bytes,
+                                  &S.mbar);
+                }
+                if (threadIdx.x == 0 && !mbar_wait_bounded(P, &S.mbar, mbar_phase)) S.ok = 0;
+                mbar_phase ^= 1u;
+                __syncthreads();
+                if (!*reinterpret_cast<volatile int *>(&S.ok)) return;
+            }
+        }
+        // the recount: 4 domains per warp, 8 lanes each
+        for (long long base = rbase + warp * 4; base < rend; base += kWarps * 4) {
+            const long long q = base + (lane & 3);
+            const LatticeDesc *Ldp = nullptr;
+            long long k = 0;
+            if (q < rend) {
+                const int ls = find_segment(S, q);
+                const LatticeDesc &Ld = P.desc[S.seg_slot[ls]];
+                if (Ld.sub2 && g < S.seg_part[ls]) {
+                    int dx, dy, dz;
+                    active_domain(Ld, q - S.seg_base[ls], cycle_colour(S, Ld, ls, S.seg_t0[ls] + g), dx, dy, dz);
+                    k = domain_index(Ld.nd, dx, dy, dz);
+                    Ldp = &Ld;
+                }
+            }
+            uint32_t part[kClasses];
+#pragma unroll
+            for (int c = 0; c < kClasses; ++c) part[c] = 0;
+            if (Ldp) {
+                const uint16_t *st = reinterpret_cast<const uint16_t *>(stage + (q - rbase) * P.item_bytes);
+                switch (Ldp->d) {
+                case 2: recount_part<2>(st, o, part); break;
+                case 4: recount_part<4>(st, o, part); break;
+                case 8: recount_part<8>(st, o, part); break;
+                default: recount_part<16>(st, o, part); break;
+                }
+            }
+            // packed words add without carries (counts < 2^16): sum over the octet
+#pragma unroll
+            for (int c = 0; c < kClasses; ++c) {
+                uint32_t v = part[c];
+                v += __shfl_xor_sync(kFull, v, 4);
+                v += __shfl_xor_sync(kFull, v, 8);
+                v += __shfl_xor_sync(kFull, v, 16);
+                part[c] = v;
+            }
+            if (Ldp && o < 4) {
+                const uint32_t w0 = o == 0 ? part[0] : (o == 1 ? part[4] : (o == 2 ? part[8] : part[12]));
+                const uint32_t w1 = o == 0 ? part[1] : (o == 1 ? part[5] : (o == 2 ? part[9] : part[13]));
+                const uint32_t w2 = o == 0 ? part[2] : (o == 1 ? part[6] : (o == 2 ? part[10] : 0u));
+                const uint32_t w3 = o == 0 ? part[3] : (o == 1 ? part[7] : (o == 2 ? part[11] : 0u));
+                __stcg(reinterpret_cast<uint4 *>(Ldp->counts + k * kCountStride) + o, make_uint4(w0, w1, w2, w3));
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Global u16 load that is issued only when `pred` holds (no branch).
 __device__ __forceinline__ uint32_t ldg_u16_if(const uint16_t *p, bool pred)
 {
@@ -734,7 +932,7 @@ __device__ FlipDelta apply_flip(const LaunchParams &P, CtaShared &S, const WorkI
             }
             int bit;
             const uint16_t *row = row_of_site<D>(Ld, base3[0] + n3[0], base3[1] + n3[1], base3[2] + n3[2], bit);
-            gv[dir][n] = ldg_u16_if(row, need);
+            gv[dir][n] = ldg_u16_if(row, need && !Ld.sub2); // no class moves with two colours
             gbit[dir][n] = bit;
         }
     }
@@ -777,6 +975,7 @@ __device__ FlipDelta apply_flip(const LaunchParams &P, CtaShared &S, const WorkI
                                wrap_coord(w.dz + dd[2], nd)); // w.k when inside
     }
     bool ok = true;
+    if (!Ld.sub2) { // two-colour lattices recount at each visit instead
     // a class move of a site adds 1 to the total and, in the lower half of
     // its domain (z < D/2), 1 to bits 16-31 of the class word
     int v[kClasses] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w, o2.x, o2.y, o2.z, o2.w, o3.x, o3.y};
@@ -806,6 +1005,7 @@ __device__ FlipDelta apply_flip(const LaunchParams &P, CtaShared &S, const WorkI
     __stcg(own + 1, make_int4(v[4], v[5], v[6], v[7]));
     __stcg(own + 2, make_int4(v[8], v[9], v[10], v[11]));
     __stcg(own + 3, make_int4(v[12], v[13], 0, 0));
+    }
     if (!ok) raise_error(P.err, SPKMC_EINTERNAL);
     const int x = s3[0], y = s3[1], z = s3[2];
     // the flip, and the ghost faces of the neighbours that touch the site
@@ -917,7 +1117,7 @@ __device__ __forceinline__ void phase_b_round(const LaunchParams &P, CtaShared &
                 for (int c = kClasses - 1; c >= 0; --c)
                     if (tb < (unsigned long long)__double_as_longlong(cum[c])) cls = c;
                 fixed64(__dadd_rn(R, -cum[kClasses - 1]), fxlo, fxhi);
-                active_domain(Ld.half, a, (int)(t & 7), dx, dy, dz);
+                active_domain(Ld, a, cycle_colour(S, Ld, ls, t), dx, dy, dz);
                 k = domain_index(Ld.nd, dx, dy, dz);
                 dval = Ld.d;
                 if (cls < 0) {
@@ -1164,6 +1364,18 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
     const bool early = hi - lo <= P.round_items;
     for (long long g = 0; g < P.ncycles; ++g) {
         Line line; // this cycle's frequency line of the thread's item (one-round CTAs)
+        if (P.sub2_any) {
+            // Sec. 3.2 step 4a, two colours: the colour of this cycle
+            for (int i = threadIdx.x; i < S.nsegc; i += blockDim.x) {
+                const LatticeDesc &Ld = P.desc[S.seg_slot[i]];
+                if (Ld.sub2 && g < S.seg_part[i]) {
+                    unsigned long long w[4];
+                    philox4x64_10((unsigned long long)(S.seg_t0[i] + g), 0ULL, 5ULL, 0ULL, Ld.seed, 0ULL, w);
+                    S.seg_colour[i] = (int)(w[0] >> 63);
+                }
+            }
+            __syncthreads();
+        }
         if (early) {
             if (threadIdx.x == 0) {
                 unsigned total = 0;
@@ -1183,13 +1395,17 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
                     const LatticeDesc &Ld = P.desc[S.seg_slot[ls]];
                     const long long t = S.seg_t0[ls] + g;
                     int dx, dy, dz;
-                    active_domain(Ld.half, q - S.seg_base[ls], (int)(t & 7), dx, dy, dz);
+                    active_domain(Ld, q - S.seg_base[ls], cycle_colour(S, Ld, ls, t), dx, dy, dz);
                     const long long k = domain_index(Ld.nd, dx, dy, dz);
                     asm volatile("fence.proxy.async.global;" ::: "memory");
                     bulk_copy_g2s(stage + (q - lo) * P.item_bytes, Ld.cells + k * block_words(Ld.d),
                                   staged_bytes(Ld.d), &S.mbar);
                 }
             }
+        }
+        if (P.sub2_any) {
+            phase_r(P, S, stage, g, lo, hi, mbar_phase, early);
+            if (!*reinterpret_cast<volatile int *>(&S.ok)) return;
         }
         // step 5 one cycle behind, on a thread that normally has no domain
         // in step 1

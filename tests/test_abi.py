@@ -59,6 +59,20 @@ def test_rmax_bounds_rejects_bad_arguments(d, T):
     assert e.value.code == sp.SPKMC_EINVAL
 
 
+def test_two_colour_sizes_and_invalid_combinations():
+    # two colours: K/2 active domains, so four times the scratch of eight
+    p8 = sp.make_params(64, 8)
+    p2 = sp.make_params(64, 8, sublattice=sp.SPKMC_SUBLATTICE_2_RANDOM)
+    K = 8 ** 3
+    assert sp.spkmc_bytes_required(p2) - sp.spkmc_bytes_required(p8) == (K // 2 - K // 8) * 192
+    for bad in (sp.make_params(16, 4, sublattice=2), sp.make_params(16, 4, sublattice=-1),
+                sp.make_params(16, 4, sublattice=1, rmax_mode=sp.SPKMC_RMAX_LEARNED)):
+        assert sp.spkmc_bytes_required(bad) == 0
+        with pytest.raises(sp.SpkmcError) as e:
+            sp.spkmc_create_ex(bad)
+        assert e.value.code == sp.SPKMC_EINVAL
+
+
 @pytest.mark.parametrize("mode", [-1, 3])
 def test_create_rejects_unknown_rmax_mode(mode):
     p = sp.make_params(16, 4, rmax_mode=mode)

@@ -279,18 +279,22 @@ def served_summary(n_requests=400, rate=200.0, budget=120 << 30, step_cycles=100
 # ---------------------------------------------------------------------------
 # arms
 # ---------------------------------------------------------------------------
-def bounds_summary(cfg, stream, steps, cps):
-    """The bounds of Sec. 3.2 step 4b on the same workload: the launch has no
-    grid barrier before the events.  Events/s counts nulls like the headline;
-    flips/s and the useful fraction (flips / events) say what the bound
-    costs in null events."""
+def variants_summary(cfg, stream, steps, cps):
+    """Variants of Sec. 3.2 on the same workload.  The R_max bounds of step
+    4b (learned, prescribed): the launch has no grid barrier before the
+    events.  The paper's two random colours of step 4a: half of the domains
+    active per cycle, each recounted at its visit.  Events/s counts nulls
+    like the headline; flips/s and the useful fraction (flips / events) say
+    what a bound costs in null events."""
     import torch
 
     import paper_1005_4713_gb300 as sp
 
     out = {}
-    for mode, name in ((sp.SPKMC_RMAX_LEARNED, "learned"), (sp.SPKMC_RMAX_PRESCRIBED, "prescribed")):
-        with sp.Lattice(L_BENCH, D_BENCH, 1.0, 0.0, 4.5115, SEED_BENCH, config=cfg, rmax_mode=mode) as lat:
+    for name, kw in (("learned", dict(rmax_mode=sp.SPKMC_RMAX_LEARNED)),
+                     ("prescribed", dict(rmax_mode=sp.SPKMC_RMAX_PRESCRIBED)),
+                     ("two_colour", dict(sublattice=sp.SPKMC_SUBLATTICE_2_RANDOM))):
+        with sp.Lattice(L_BENCH, D_BENCH, 1.0, 0.0, 4.5115, SEED_BENCH, config=cfg, **kw) as lat:
             for _ in range(3):
                 lat.run(cps)
             o0 = lat.observables()
@@ -305,7 +309,8 @@ def bounds_summary(cfg, stream, steps, cps):
             o = lat.observables()
             nf, nn = o.n_flip - o0.n_flip, o.n_null - o0.n_null
             out[name] = {"events_per_s": (nf + nn) / s, "flips_per_s": nf / s,
-                         "useful_fraction": nf / (nf + nn), "us_per_cycle": s / (steps * cps) * 1e6}
+                         "useful_fraction": nf / (nf + nn), "us_per_cycle": s / (steps * cps) * 1e6,
+                         "events_per_cycle": lat.K_act}
     return out
 
 
@@ -431,12 +436,12 @@ def run_gpu(args, world, rank, local, pg):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(rank, world)
-    batched = served = bounds = None
+    batched = served = variants = None
     if rank == 0 and world == 1 and not args.no_ensembles:
         batched = batched_summary()
         served = served_summary()
-    if rank == 0 and world == 1 and not args.no_bounds:
-        bounds = bounds_summary(cfg, stream, args.steps, cps)
+    if rank == 0 and world == 1 and not args.no_variants:
+        variants = variants_summary(cfg, stream, args.steps, cps)
 
     if rank == 0:
         peak, peak_kind = measured_peak()
@@ -467,7 +472,7 @@ def run_gpu(args, world, rank, local, pg):
             "gpu_launches": args.steps,
             "clocks": clocks,
             "exact_rmax": {"flips_per_s": flips * world / (ms_max / 1e3), "useful_fraction": useful},
-            "rmax_bounds": bounds,
+            "variants": variants,
             "batched": batched,
             "served": served,
         }
@@ -486,7 +491,8 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensembles", action="store_true", help="skip the batched and served summaries")
-    ap.add_argument("--no-bounds", action="store_true", help="skip the prescribed/learned R_max summary")
+    ap.add_argument("--no-variants", "--no-bounds", dest="no_variants", action="store_true",
+                    help="skip the R_max-bound and two-colour summaries")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

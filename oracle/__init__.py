@@ -71,6 +71,9 @@ def lib():
                                          _i64, _i32, _ptr]
             L.oracle_bkl_run.restype = _i32
             L.oracle_enumerate.argtypes = [_i32, _i32, _i32, _dbl, _dbl, _dbl, _ptr]
+            L.oracle_bkl_relax.argtypes = [_i32, _i32, _i32, _dbl, _dbl, _dbl, _u64, _ptr, _i32, _ptr, _ptr,
+                                           _i64, _ptr, _ptr]
+            L.oracle_bkl_relax.restype = _i32
             L.oracle_enumerate.restype = _i32
             _lib = L
         return _lib
@@ -216,3 +219,21 @@ def enumerate_exact(shape, J, H, T):
     if rc != 0:
         raise ValueError("oracle_enumerate rejected its arguments")
     return out
+
+
+def bkl_relax(shape, J, H, T, seed, spins, times, max_events=1 << 62, record_sites=0):
+    """Serial BKL with sites grouped by class (the n-fold way, Sec. 4's
+    serial reference), from ``spins`` (modified in place): m at each of the
+    ascending ``times``.  Returns (m, events run, flipped sites or None)."""
+    Lx, Ly, Lz = shape
+    times = np.ascontiguousarray(times, dtype=np.float64)
+    m = np.full(len(times), np.nan)
+    ne = np.zeros(1, dtype=np.int64)
+    sites = np.zeros(record_sites, dtype=np.int32) if record_sites else None
+    if record_sites:
+        max_events = min(max_events, record_sites)
+    g = lib().oracle_bkl_relax(Lx, Ly, Lz, J, H, T, seed, _p(spins), len(times), _p(times), _p(m),
+                               int(max_events), _p(ne), _p(sites) if record_sites else None)
+    if g < 0:
+        raise ValueError("oracle_bkl_relax rejected its arguments")
+    return m, int(ne[0]), (sites[:int(ne[0])] if record_sites else None)

@@ -514,6 +514,125 @@ int oracle_bkl_run(int Lx, int Ly, int Lz, double J, double H, double T, uint64_
 }
 
 /* ------------------------------------------------------------------------- */
+/* Serial BKL (the n-fold way, the serial reference of Sec. 4) with the sites  */
+/* grouped by rate class, for relaxation runs on lattices too large for the   */
+/* rescan above.  Each event, in the order of the frequency line of Sec. 3.1  */
+/* applied to the whole lattice as a single domain with no null rate: R =     */
+/* sum_c n_c r_c in class order; with Philox counter (e, 0, 6, 0), target =   */
+/* u R (u = (w0 >> 11) 2^-53), the first class c with target < cum_c (the     */
+/* last populated class if rounding leaves none); the j-th site of that class */
+/* in ascending index, j = floor(w1 n_c / 2^64); dt = -ln(xi)/R with          */
+/* xi = (2 (w2 >> 12) + 1) 2^-53.  The members of each class are kept in a    */
+/* Fenwick tree over the site index (rank and select in O(log N)).  m at the  */
+/* times times[0..ntimes-1] (ascending) is the magnetisation of the state at  */
+/* that time.  sites (may be NULL) receives the flipped sites.                */
+/* ------------------------------------------------------------------------- */
+static void fen_add(int32_t *f, int64_t n, int64_t i, int32_t v)
+{
+    for (int64_t x = i + 1; x <= n; x += x & (-x)) f[x] += v;
+}
+
+/* index of the (j+1)-th member (0-based j < total) */
+static int64_t fen_select(const int32_t *f, int64_t n, int64_t j)
+{
+    int64_t pos = 0, step = 1;
+    while (step * 2 <= n) step *= 2;
+    int64_t left = j + 1;
+    for (; step > 0; step /= 2) {
+        if (pos + step <= n && f[pos + step] < left) {
+            pos += step;
+            left -= f[pos];
+        }
+    }
+    return pos; /* 0-based index */
+}
+
+int oracle_bkl_relax(int Lx, int Ly, int Lz, double J, double H, double T, uint64_t seed, int8_t *s,
+                     int ntimes, const double *times, double *m_out, int64_t max_events,
+                     int64_t *nevents_out, int32_t *sites)
+{
+    if (Lx < 2 || Ly < 2 || Lz < 2 || ntimes < 0 || !(T > 0.0)) return -1;
+    const int64_t N = (int64_t)Lx * Ly * Lz;
+    double rate[14];
+    oracle_rates(J, H, T, rate);
+    int32_t *fen = (int32_t *)calloc((size_t)(14 * (N + 1)), sizeof(int32_t));
+    int8_t *cls = (int8_t *)malloc((size_t)N);
+    if (!fen || !cls) {
+        free(fen); free(cls);
+        return -1;
+    }
+    int64_t n[14] = {0};
+    int64_t M = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t nb[6];
+        bkl_neighbours(Lx, Ly, Lz, i, nb);
+        int u = 0;
+        for (int q = 0; q < 6; ++q) u += s[nb[q]] > 0;
+        cls[i] = (int8_t)(7 * (s[i] > 0) + u);
+        n[cls[i]] += 1;
+        fen_add(fen + cls[i] * (N + 1), N, i, 1);
+        M += s[i];
+    }
+    double t = 0.0;
+    int g = 0;
+    int64_t e = 0;
+    for (; e < max_events && g < ntimes; ++e) {
+        double cum[14], R = 0.0;
+        for (int c = 0; c < 14; ++c) {
+            R = R + (double)n[c] * rate[c];
+            cum[c] = R;
+        }
+        uint64_t w[4];
+        oracle_philox((uint64_t)e, 0, 6, 0, seed, 0, w);
+        const double xi = (double)(2 * (w[2] >> 12) + 1) * 0x1p-53;
+        const double dt = -log(xi) / R; /* +inf when every rate is 0 */
+        /* the state holds until t + dt */
+        while (g < ntimes && times[g] < t + dt) m_out[g++] = (double)M / (double)N;
+        if (g >= ntimes) break;
+        const double target = (double)(w[0] >> 11) * 0x1p-53 * R;
+        int c = -1;
+        for (int q = 0; q < 14; ++q)
+            if (target < cum[q]) { c = q; break; }
+        if (c < 0)
+            for (int q = 13; q >= 0; --q)
+                if (n[q] > 0) { c = q; break; }
+        const uint64_t j = (uint64_t)(((u128)w[1] * (uint64_t)n[c]) >> 64);
+        const int64_t i = fen_select(fen + c * (N + 1), N, (int64_t)j);
+        if (sites) sites[e] = (int32_t)i;
+        t = t + dt;
+        /* the flip: site i changes spin, its neighbours change up count */
+        const int8_t old = s[i];
+        s[i] = (int8_t)(-old);
+        M += 2 * s[i];
+        int64_t nb[6];
+        bkl_neighbours(Lx, Ly, Lz, i, nb);
+        int64_t touch[7] = {i, nb[0], nb[1], nb[2], nb[3], nb[4], nb[5]};
+        for (int a = 0; a < 7; ++a) {
+            const int64_t x = touch[a];
+            int dup = 0;
+            for (int b = 0; b < a; ++b) dup |= touch[b] == x; /* an axis of length 2 lists a partner twice */
+            if (dup) continue;
+            int64_t nx[6];
+            bkl_neighbours(Lx, Ly, Lz, x, nx);
+            int u = 0;
+            for (int q = 0; q < 6; ++q) u += s[nx[q]] > 0;
+            const int8_t cn = (int8_t)(7 * (s[x] > 0) + u);
+            if (cn != cls[x]) {
+                n[cls[x]] -= 1;
+                fen_add(fen + cls[x] * (N + 1), N, x, -1);
+                cls[x] = cn;
+                n[cn] += 1;
+                fen_add(fen + cn * (N + 1), N, x, 1);
+            }
+        }
+    }
+    if (nevents_out) *nevents_out = e;
+    free(fen);
+    free(cls);
+    return g; /* time points filled */
+}
+
+/* ------------------------------------------------------------------------- */
 /* Exact Boltzmann averages by enumeration of all 2^N states of a small       */
 /* Lx x Ly x Lz lattice (N <= 24), with the energy of Eq. 1 (bonds counted as */
 /* in oracle_bkl_run).  out = {<E>, <E^2>, <m^2>, <m^4>, <|m|>, <m>}.         */

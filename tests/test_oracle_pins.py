@@ -622,3 +622,85 @@ def test_serial_bkl_matches_exact_enumeration(T):
         mu = sums[:, col].sum() / w.sum()
         err = means.std(ddof=1) / math.sqrt(nb)
         assert abs(mu - exact[idx]) < 4.5 * err + 1e-12, (col, mu, exact[idx], err)
+
+
+# --------------------------------------------------------------------------
+# Serial BKL with the sites grouped by class (the n-fold way; the serial
+# reference of Sec. 4 for relaxation runs)
+# --------------------------------------------------------------------------
+def numpy_classes_shape(shape, s):
+    """class = 7*[sigma=+1] + up neighbours on an Lx x Ly x Lz periodic
+    lattice (x fastest); an axis of length 2 lists its partner twice."""
+    Lx, Ly, Lz = shape
+    a = (s.reshape(Lz, Ly, Lx) > 0).astype(np.int64)
+    u = sum(np.roll(a, sh, axis=ax) for ax in (0, 1, 2) for sh in (1, -1))
+    return (7 * a + u).reshape(-1)
+
+
+def brute_bkl(shape, J, H, T, seed, s, times, nevents):
+    r = [1.0 / (1.0 + math.exp(2.0 * (1 if c >= 7 else -1) * (J * (2 * (c % 7) - 6) + H) / T))
+         for c in range(14)]
+    s = s.copy()
+    N = s.size
+    t, g, out, sites = 0.0, 0, [], []
+    for e in range(nevents):
+        cls = numpy_classes_shape(shape, s)
+        n = [int(np.sum(cls == c)) for c in range(14)]
+        cum, R = [], 0.0
+        for c in range(14):
+            R = R + n[c] * r[c]
+            cum.append(R)
+        w = numpy_philox((e, 0, 6, 0), (seed, 0))
+        xi = (2 * (w[2] >> 12) + 1) * 2.0 ** -53
+        dt = -math.log(xi) / R
+        while g < len(times) and times[g] < t + dt:
+            out.append(int(s.sum()) / N)
+            g += 1
+        if g >= len(times):
+            break
+        target = (w[0] >> 11) * 2.0 ** -53 * R
+        c = next((q for q in range(14) if target < cum[q]), None)
+        if c is None:
+            c = max(q for q in range(14) if n[q] > 0)
+        j = (w[1] * n[c]) >> 64
+        site = int(np.flatnonzero(cls == c)[j])
+        sites.append(site)
+        t = t + dt
+        s[site] = -s[site]
+    return np.array(out), np.array(sites, dtype=np.int32)
+
+
+@pytest.mark.parametrize("shape,J,H,T,seed", [
+    ((4, 4, 4), 1.0, 0.0, 4.5115, 7),
+    ((3, 3, 2), 1.0, 0.2, 3.0, 8),
+    ((4, 2, 3), -0.8, 0.0, 2.5, 9),
+])
+def test_class_bkl_bruteforce(shape, J, H, T, seed):
+    rng = np.random.default_rng(seed)
+    s0 = rng.choice(np.array([-1, 1], dtype=np.int8), size=int(np.prod(shape)))
+    times = np.linspace(0.01, 40.0, 60)
+    n = 300
+    m_ref, sites_ref = brute_bkl(shape, J, H, T, seed, s0, times, n)
+    s = s0.copy()
+    m, ne, sites = oracle.bkl_relax(shape, J, H, T, seed, s, times, record_sites=n)
+    assert np.array_equal(sites, sites_ref[:ne])
+    k = len(m_ref)
+    assert np.array_equal(m[:k], m_ref)
+    assert ne == len(sites_ref)
+
+
+@pytest.mark.parametrize("T", [3.5, 4.5115, 6.0])
+def test_class_bkl_matches_exact_enumeration(T):
+    """The state sampled on a uniform time grid of a long run averages to
+    the Boltzmann <m^2>, <m^4> and <|m|> of Eq. 1 on 3x3x2 (2^18 states)."""
+    shape, J, H = (3, 3, 2), 1.0, 0.0
+    exact = oracle.enumerate_exact(shape, J, H, T)
+    s = np.ones(18, dtype=np.int8)
+    times = np.arange(1, 400_001, dtype=np.float64) * 0.5
+    m, _, _ = oracle.bkl_relax(shape, J, H, T, 2000 + int(T * 10), s, times)
+    m = m[1000:]  # past the start from all +1
+    nb = 40
+    for vals, idx in [(m ** 2, 2), (m ** 4, 3), (np.abs(m), 4)]:
+        means = vals[: len(vals) // nb * nb].reshape(nb, -1).mean(axis=1)
+        err = means.std(ddof=1) / math.sqrt(nb)
+        assert abs(vals.mean() - exact[idx]) < 4.5 * err, (idx, vals.mean(), exact[idx], err)

@@ -223,8 +223,17 @@ int spkmc_run_cycles(spkmc_t *h, int64_t ncycles);
 /* Wait for the stream and report kernel-side errors (ETIMEOUT, EINTERNAL,
  * EBOUND). */
 int spkmc_synchronize(spkmc_t *h);
-/* Synchronise and compute the observables on the device. */
+/* Synchronise and read the observables (M and B are kept exact in the
+ * lattice state; E, m, m^2, m^4 follow on the host). */
 int spkmc_observables(spkmc_t *h, spkmc_obs *out);
+/* The same observables, enqueued on the handle's stream without waiting: a
+ * one-thread kernel writes them from the lattice state (the kernel keeps M
+ * and B exact, so no lattice pass is needed) and a copy brings them to
+ * host_out, which must stay valid and unread until spkmc_synchronize
+ * returns; pinned host memory lets the copy overlap the next cycles.  The
+ * values equal those of spkmc_observables at the same point of the stream
+ * bit for bit.  Device errors are reported by the next synchronising call. */
+int spkmc_observables_async(spkmc_t *h, spkmc_obs *host_out);
 /* Copy spins to/from a host int8 buffer of n = L^3 entries in global order.
  * set_spins recomputes the ghost faces, class counts, M and B on the device
  * and clears the R_max history (it no longer describes the spins); restore a

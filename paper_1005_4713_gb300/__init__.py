@@ -23,7 +23,7 @@ from ._abi import (SPKMC_EBOUND, SPKMC_EBUSY, SPKMC_ECUDA, SPKMC_EINTERNAL, SPKM
                    SPKMC_INIT_COLD, SPKMC_INIT_HOT, SPKMC_OK, SPKMC_ETIMEOUT, spkmc_config,
                    spkmc_event, spkmc_info, spkmc_obs, spkmc_params, spkmc_state)
 
-__all__ = [n for n in _abi.PROTOTYPES] + ["Lattice", "Batch", "SpkmcError", "torch_config",
+__all__ = [n for n in _abi.PROTOTYPES] + ["Lattice", "Batch", "SpkmcError", "torch_config", "obs_buffer",
                                             "make_params", "make_config", "EVENT_DTYPE"]
 
 _lock = threading.Lock()
@@ -171,6 +171,36 @@ def spkmc_observables(h) -> spkmc_obs:
     o = spkmc_obs()
     _check(lib().spkmc_observables(h, ctypes.byref(o)))
     return o
+
+
+def spkmc_observables_async(h, out: spkmc_obs) -> spkmc_obs:
+    """Enqueue the observables into ``out`` (read it after a synchronise;
+    see obs_buffer for pinned storage)."""
+    _check(lib().spkmc_observables_async(h, ctypes.byref(out)))
+    return out
+
+
+class obs_buffer:
+    """An array of n spkmc_obs records in pinned host memory (through the
+    PyTorch allocator; plain host memory without PyTorch), for
+    spkmc_observables_async."""
+
+    def __init__(self, n: int):
+        size = ctypes.sizeof(spkmc_obs) * n
+        try:
+            import torch
+            self._keep = torch.empty(size, dtype=torch.uint8, pin_memory=torch.cuda.is_available())
+            addr = self._keep.data_ptr()
+        except ImportError:
+            self._keep = ctypes.create_string_buffer(size)
+            addr = ctypes.addressof(self._keep)
+        self.records = (spkmc_obs * n).from_address(addr)
+
+    def __getitem__(self, i) -> spkmc_obs:
+        return self.records[i]
+
+    def __len__(self):
+        return len(self.records)
 
 
 def spkmc_get_spins(h, out: np.ndarray) -> np.ndarray:
@@ -333,6 +363,9 @@ class Lattice:
 
     def observables(self) -> spkmc_obs:
         return spkmc_observables(self.h)
+
+    def observables_async(self, out: spkmc_obs) -> spkmc_obs:
+        return spkmc_observables_async(self.h, out)
 
     def spins(self) -> np.ndarray:
         return spkmc_get_spins(self.h, np.empty(self.L ** 3, dtype=np.int8))

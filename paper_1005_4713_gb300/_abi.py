@@ -93,6 +93,7 @@ PROTOTYPES = {
     "spkmc_run_cycles": (ctypes.c_int, [_h, _i64]),
     "spkmc_synchronize": (ctypes.c_int, [_h]),
     "spkmc_observables": (ctypes.c_int, [_h, P(spkmc_obs)]),
+    "spkmc_observables_async": (ctypes.c_int, [_h, P(spkmc_obs)]),
     "spkmc_get_spins": (ctypes.c_int, [_h, ctypes.c_void_p, _sz]),
     "spkmc_set_spins": (ctypes.c_int, [_h, ctypes.c_void_p, _sz]),
     "spkmc_get_event_log": (ctypes.c_int, [_h, ctypes.c_void_p, _sz, P(_sz)]),

@@ -229,6 +229,7 @@ struct spkmc_batch {
     unsigned *d_bar = nullptr;
     int *d_err = nullptr;
     long long *d_MB = nullptr;
+    spkmc_obs *d_obs = nullptr; // per-slot observables records for the asynchronous read-out
     unsigned long long *d_mismatch = nullptr;
     // pinned host staging
     LatticeDesc *h_desc = nullptr;
@@ -291,6 +292,7 @@ void release_batch(spkmc_batch *b)
     cudaFree(b->d_bar);
     cudaFree(b->d_err);
     cudaFree(b->d_MB);
+    cudaFree(b->d_obs);
     cudaFree(b->d_mismatch);
     cudaFreeHost(b->h_desc);
     cudaFreeHost(b->h_state);
@@ -338,6 +340,7 @@ int batch_new(int capacity, const spkmc_config *cfg, spkmc_batch **out)
         (e = cudaMalloc(&b->d_bar, 256)) != cudaSuccess ||
         (e = cudaMalloc(&b->d_err, 256)) != cudaSuccess ||
         (e = cudaMalloc(&b->d_MB, 256)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_obs, sizeof(spkmc_obs) * capacity)) != cudaSuccess ||
         (e = cudaMalloc(&b->d_mismatch, 256)) != cudaSuccess ||
         (e = cudaMallocHost(&b->h_desc, sizeof(LatticeDesc) * capacity)) != cudaSuccess ||
         (e = cudaMallocHost(&b->h_state, sizeof(LatticeState) * capacity)) != cudaSuccess ||
@@ -840,6 +843,21 @@ int spkmc_observables(spkmc_t *h, spkmc_obs *out)
 {
     if (!h) return fail(SPKMC_EINVAL, "handle is NULL");
     return observables(h->b, h->slot, out);
+}
+
+int spkmc_observables_async(spkmc_t *h, spkmc_obs *host_out)
+{
+    if (!h || !host_out) return fail(SPKMC_EINVAL, "NULL argument");
+    spkmc_batch *b = h->b;
+    if (b->sticky_error) return fail(b->sticky_error, "batch stopped after an earlier device error");
+    DeviceGuard g(b->device);
+    const Slot &s = b->slots[h->slot];
+    spkmc_obs *rec = b->d_obs + h->slot;
+    if (launch_obs_record(b->d_state + h->slot, s.params.L, s.d, s.params.J, s.params.H, rec, b->stream) != SPKMC_OK)
+        return cuda_fail(cudaGetLastError(), "observables record");
+    CUDA_TRY(cudaMemcpyAsync(host_out, rec, sizeof(spkmc_obs), cudaMemcpyDeviceToHost, b->stream),
+             "observables copy");
+    return SPKMC_OK;
 }
 
 int spkmc_get_spins(spkmc_t *h, int8_t *host_buf, size_t n)

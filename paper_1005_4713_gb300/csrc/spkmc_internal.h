@@ -132,6 +132,7 @@ int launch_ghosts(const LatticeDesc &d, int mode, unsigned long long *mismatch, 
 int launch_count_classes(const LatticeDesc &d, int mode, unsigned long long *mismatch,
                          void *stream);
 // M and B (device int64 pair, accumulated).
+int launch_obs_record(const LatticeState *st, int L, int d, double J, double H, spkmc_obs *out, void *stream);
 int launch_observables(const LatticeDesc &d, long long *MB, void *stream);
 // Round size for a launch whose largest domain edge is d_max.
 int cycle_round_items(int d_max);

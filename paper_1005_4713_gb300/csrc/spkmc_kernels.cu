@@ -1734,6 +1734,38 @@ int launch_count_classes(const LatticeDesc &d, int mode, unsigned long long *mis
     return to_status(cudaGetLastError());
 }
 
+// The observables of one lattice from its state, with the operations (and
+// the IEEE roundings) of the host-side read-out: E = -J B - H M, m = M / N,
+// m^2, m^4, and the null-rate sum as hi + lo 2^-64.
+__global__ void obs_record_kernel(const LatticeState *st, int L, int d, double J, double H, spkmc_obs *out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    spkmc_obs o;
+    const double N = (double)L * L * L;
+    o.cycle = st->t;
+    o.clock = st->clock;
+    o.M = st->M;
+    o.B = st->B;
+    o.E = __dsub_rn(__dmul_rn(-J, (double)o.B), __dmul_rn(H, (double)o.M));
+    o.m = __ddiv_rn((double)o.M, N);
+    o.m2 = __dmul_rn(o.m, o.m);
+    o.m4 = __dmul_rn(o.m2, o.m2);
+    o.n_flip = (int64_t)st->n_flip;
+    o.n_null = (int64_t)st->n_null;
+    o.sum_null_rate_fx[0] = st->null_fx_lo;
+    o.sum_null_rate_fx[1] = st->null_fx_hi;
+    o.sum_null_rate = __dadd_rn(__ull2double_rn(st->null_fx_hi), __dmul_rn(__ull2double_rn(st->null_fx_lo), 0x1p-64));
+    o.L = L;
+    o.domain_edge = d;
+    *out = o;
+}
+
+int launch_obs_record(const LatticeState *st, int L, int d, double J, double H, spkmc_obs *out, void *stream)
+{
+    obs_record_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(st, L, d, J, H, out);
+    return to_status(cudaGetLastError());
+}
+
 int launch_observables(const LatticeDesc &d, long long *MB, void *stream)
 {
     const int grid = simple_grid(d.K, 8);

@@ -254,3 +254,24 @@ def test_barrier_timeout_is_reported_and_the_context_survives():
     with gpu_lattice(spec) as ok:
         ok.run(4)
         assert_same(ok, st)
+
+
+def test_asynchronous_observables_equal_the_synchronous_ones():
+    """Observables enqueued after each chunk without waiting equal, bit for
+    bit, those read synchronously at the same points of another run."""
+    spec = wl.LatticeSpec(L=64, d=8, seed=26, H=0.01)
+    buf = sp.obs_buffer(5)
+    with gpu_lattice(spec) as a, gpu_lattice(spec) as b:
+        ref = []
+        for i in range(5):
+            a.run(7 + i)
+            a.observables_async(buf[i])
+            b.run(7 + i)
+            ref.append(b.observables())
+        a.synchronize()
+        for i in range(5):
+            x, y = buf[i], ref[i]
+            for f in ("cycle", "clock", "M", "B", "E", "m", "m2", "m4", "n_flip", "n_null", "sum_null_rate",
+                      "L", "domain_edge"):
+                assert getattr(x, f) == getattr(y, f), f
+            assert list(x.sum_null_rate_fx) == list(y.sum_null_rate_fx)

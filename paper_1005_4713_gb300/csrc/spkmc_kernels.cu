@@ -910,34 +910,81 @@ __device__ FlipDelta apply_flip(const LaunchParams &P, CtaShared &S, const WorkI
     const int sig = w.cls >= 7, us = w.cls - 7 * sig;
     const int delta = sig ? -1 : 1; // change of the neighbours' up count
     const int nd = Ld.nd;
-    const int base3[3] = {w.dx * D, w.dy * D, w.dz * D};
-    uint32_t gv[6][5];
-    int gbit[6][5];
+    const int dc[3] = {w.dx, w.dy, w.dz};
+    // A neighbour j outside the domain lies in the face neighbour kj across
+    // direction dir; of its own neighbours, the halo face holds the lateral
+    // ones inside the domain's extent, the global blocks hold the site two
+    // steps out (in kj) and, along each lateral axis on which the site sits
+    // at the domain's edge, the lateral one in the diagonal domain beyond.
+    // Those reads are issued together (predicated) before any write.
+    long long kj[6];
+    uint32_t gv[6][3];
+    int gbit[6][3];
+    if constexpr (D < 16) {
+        // small domains (most sites on a face): the same reads, addressed
+        // from global coordinates, which measures faster there
+        const int base3[3] = {w.dx * D, w.dy * D, w.dz * D};
+#pragma unroll
+        for (int dir = 0; dir < 6; ++dir) {
+            const int ax = dir >> 1, step = (dir & 1) ? 1 : -1;
+            int j3[3] = {s3[0], s3[1], s3[2]};
+            j3[ax] += step;
+            const bool out = j3[ax] < 0 || j3[ax] >= D;
+            const bool need = out && !Ld.sub2;
+            int t3[3] = {j3[0], j3[1], j3[2]};
+            t3[ax] += step;
+            gv[dir][0] = ldg_u16_if(row_of_site<D>(Ld, base3[0] + t3[0], base3[1] + t3[1], base3[2] + t3[2],
+                                                   gbit[dir][0]),
+                                    need);
+#pragma unroll
+            for (int bi = 0; bi < 2; ++bi) {
+                const int b = (ax + 1 + bi) % 3;
+                const int sg = s3[b] == 0 ? -1 : 1;
+                const bool far = (s3[b] == 0) || (s3[b] == D - 1);
+                int m3[3] = {j3[0], j3[1], j3[2]};
+                m3[b] += sg;
+                gv[dir][1 + bi] = ldg_u16_if(row_of_site<D>(Ld, base3[0] + m3[0], base3[1] + m3[1], base3[2] + m3[2],
+                                                            gbit[dir][1 + bi]),
+                                             need && far);
+            }
+            const int dd[3] = {j3[0] < 0 ? -1 : (j3[0] >= D ? 1 : 0), j3[1] < 0 ? -1 : (j3[1] >= D ? 1 : 0),
+                               j3[2] < 0 ? -1 : (j3[2] >= D ? 1 : 0)};
+            kj[dir] = domain_index(nd, wrap_coord(dc[0] + dd[0], nd), wrap_coord(dc[1] + dd[1], nd),
+                                   wrap_coord(dc[2] + dd[2], nd));
+        }
+    } else {
 #pragma unroll
     for (int dir = 0; dir < 6; ++dir) {
         const int ax = dir >> 1, step = (dir & 1) ? 1 : -1;
-        int j3[3] = {s3[0], s3[1], s3[2]};
-        j3[ax] += step;
-        const bool out = j3[ax] < 0 || j3[ax] >= D;
+        const bool out = (step < 0) ? s3[ax] == 0 : s3[ax] == D - 1;
+        int fc[3] = {dc[0], dc[1], dc[2]};
+        fc[ax] = out ? wrap_coord(fc[ax] + step, nd) : fc[ax];
+        kj[dir] = domain_index(nd, fc[0], fc[1], fc[2]); // w.k when inside
+        const bool need = out && !Ld.sub2;               // no class moves with two colours
+        int l3[3] = {s3[0], s3[1], s3[2]};               // j in its own domain
+        l3[ax] = step < 0 ? D - 1 : 0;
+        {
+            int t3[3] = {l3[0], l3[1], l3[2]}; // two steps out, in kj
+            t3[ax] = step < 0 ? D - 2 : 1;
+            gv[dir][0] = ldg_u16_if(block_of<D>(Ld, kj[dir]) + t3[1] + D * t3[2], need);
+            gbit[dir][0] = t3[0];
+        }
 #pragma unroll
-        for (int n = 0; n < 5; ++n) {
-            int n3[3] = {j3[0], j3[1], j3[2]};
-            bool need = out;
-            if (n == 0) {
-                n3[ax] += step; // two steps out
-            } else {
-                const int b = (ax + 1 + ((n - 1) >> 1)) % 3;
-                n3[b] += (n & 1) ? -1 : 1;
-                need = out && (n3[b] < 0 || n3[b] >= D);
-            }
-            int bit;
-            const uint16_t *row = row_of_site<D>(Ld, base3[0] + n3[0], base3[1] + n3[1], base3[2] + n3[2], bit);
-            gv[dir][n] = ldg_u16_if(row, need && !Ld.sub2); // no class moves with two colours
-            gbit[dir][n] = bit;
+        for (int bi = 0; bi < 2; ++bi) {
+            const int b = (ax + 1 + bi) % 3;
+            const int sg = s3[b] == 0 ? -1 : 1;            // the side that may leave the domain
+            const bool far = (s3[b] == 0) || (s3[b] == D - 1);
+            int gc[3] = {fc[0], fc[1], fc[2]};
+            gc[b] = wrap_coord(gc[b] + sg, nd);
+            int m3[3] = {l3[0], l3[1], l3[2]};
+            m3[b] = sg < 0 ? D - 1 : 0;
+            const long long kd = domain_index(nd, gc[0], gc[1], gc[2]);
+            gv[dir][1 + bi] = ldg_u16_if(block_of<D>(Ld, kd) + m3[1] + D * m3[2], need && far);
+            gbit[dir][1 + bi] = m3[0];
         }
     }
+    }
     int cold[6];
-    long long kj[6];
     bool outv[6];
     const int sbit = block_bit<D>(st, s3[0], s3[1], s3[2]); // the flipped site, before its flip
 #pragma unroll
@@ -955,24 +1002,20 @@ __device__ FlipDelta apply_flip(const LaunchParams &P, CtaShared &S, const WorkI
             u_in += block_bit<D>(st, n3[0], n3[1], n3[2]);
         }
         // if it lies outside: the flipped site, the site two steps out, and
-        // the four lateral neighbours (ghost face, else global)
+        // the four lateral neighbours (halo face, else the diagonal domain)
         int u_out = sbit + (int)((gv[dir][0] >> gbit[dir][0]) & 1u);
 #pragma unroll
-        for (int n = 1; n < 5; ++n) {
+        for (int n = 0; n < 4; ++n) {
+            const int bi = n >> 1, b = (ax + 1 + bi) % 3;
             int n3[3] = {j3[0], j3[1], j3[2]};
-            const int b = (ax + 1 + ((n - 1) >> 1)) % 3;
-            n3[b] += (n & 1) ? -1 : 1;
+            n3[b] += (n & 1) ? 1 : -1;
             const bool far = n3[b] < 0 || n3[b] >= D;
-            const int gbv = (int)((gv[dir][n] >> gbit[dir][n]) & 1u);
+            const int gbv = (int)((gv[dir][1 + bi] >> gbit[dir][1 + bi]) & 1u);
             const int sbv = block_bit<D>(st, n3[0], n3[1], n3[2]);
             u_out += far ? gbv : sbv;
         }
         cold[dir] = 7 * block_bit<D>(st, j3[0], j3[1], j3[2]) + (out ? u_out : u_in);
         outv[dir] = out;
-        const int dd[3] = {j3[0] < 0 ? -1 : (j3[0] >= D ? 1 : 0), j3[1] < 0 ? -1 : (j3[1] >= D ? 1 : 0),
-                           j3[2] < 0 ? -1 : (j3[2] >= D ? 1 : 0)};
-        kj[dir] = domain_index(nd, wrap_coord(w.dx + dd[0], nd), wrap_coord(w.dy + dd[1], nd),
-                               wrap_coord(w.dz + dd[2], nd)); // w.k when inside
     }
     bool ok = true;
     if (!Ld.sub2) { // two-colour lattices recount at each visit instead

@@ -390,6 +390,7 @@ def run_gpu(args, world, rank, local, pg):
         lat.observables_async(obs_rec[i])
     e1.record(stream)
     torch.cuda.synchronize(device)
+    torch.cuda.synchronize(device)
     t_host1 = time.perf_counter()
     barrier(pg, device)
     sampler.stop()
@@ -405,6 +406,25 @@ def run_gpu(args, world, rank, local, pg):
         raise RuntimeError("asynchronous observables differ from the synchronous read-out")
     flips = obs1.n_flip - obs0.n_flip
     useful = flips / max(1, (obs1.n_flip + obs1.n_null) - (obs0.n_flip + obs0.n_null))
+    graph = None
+    if not args.no_graph and (args.steps * cps) % 2 == 0:
+        # the same steps captured once in a CUDA graph and replayed with one
+        # host launch (CUDA events around the replay)
+        graph_rec = sp.obs_buffer(args.steps)
+        g = lat.graph(cps, args.steps, graph_rec)
+        g.launch()  # warm-up replay
+        torch.cuda.synchronize(device)
+        ge0 = torch.cuda.Event(enable_timing=True)
+        ge1 = torch.cuda.Event(enable_timing=True)
+        ge0.record(stream)
+        g.launch()
+        ge1.record(stream)
+        torch.cuda.synchronize(device)
+        gms = ge0.elapsed_time(ge1)
+        g.close()
+        graph = {"value": world * args.steps * cps * kact / (max_over_ranks(gms, pg, device) / 1e3),
+                 "unit": "events/s", "ms_per_step": gms / args.steps,
+                 "note": "the timed steps captured in one CUDA graph (cycles + observables per step)"}
 
     # end to end through the C ABI with host buffers: upload the start
     # lattice from pinned memory, run the steps with observables, read the
@@ -473,9 +493,10 @@ def run_gpu(args, world, rank, local, pg):
                          "int8_equivalent_GBps": cps * kact * int8_bytes_per_event(D_BENCH) / (kernel_ms / 1e3) / 1e9},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": args.steps,
+            "gpu_launches": 2 * args.steps,  # per step: the cycle kernel and the observables record
             "clocks": clocks,
             "exact_rmax": {"flips_per_s": flips * world / (ms_max / 1e3), "useful_fraction": useful},
+            "graph": graph,
             "variants": variants,
             "batched": batched,
             "served": served,
@@ -495,6 +516,7 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensembles", action="store_true", help="skip the batched and served summaries")
+    ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay of the timed steps")
     ap.add_argument("--no-variants", "--no-bounds", dest="no_variants", action="store_true",
                     help="skip the R_max-bound and two-colour summaries")
     args = ap.parse_args(argv)

@@ -101,6 +101,7 @@ extern "C" {
 
 typedef struct spkmc_engine spkmc_t;
 typedef struct spkmc_batch spkmc_batch_t;
+typedef struct spkmc_graph spkmc_graph_t;
 
 /* Allocator callbacks: alloc returns device memory of at least `bytes` bytes
  * usable on `stream` (NULL on failure); free releases it.  `ctx` is passed
@@ -234,6 +235,22 @@ int spkmc_observables(spkmc_t *h, spkmc_obs *out);
  * values equal those of spkmc_observables at the same point of the stream
  * bit for bit.  Device errors are reported by the next synchronising call. */
 int spkmc_observables_async(spkmc_t *h, spkmc_obs *host_out);
+/* A CUDA graph of `steps` steps of the lattice's stream work, each
+ * cycles_per_step cycles (one persistent launch, as spkmc_run_cycles) and,
+ * if host_obs is not NULL, the asynchronous observables into host_obs[i]
+ * (pinned host memory of `steps` records, else EINVAL).  Replaying it with
+ * spkmc_graph_launch does the same work as the calls it captured, with one
+ * launch from the host; the graph refers to the handle, which must outlive
+ * it, and to host_obs.  steps * cycles_per_step must be even (each launch
+ * bakes in the parity of the cycle it starts on).  ECUDA if the driver
+ * refuses the capture. */
+int spkmc_graph_create(spkmc_t *h, int64_t cycles_per_step, int32_t steps, spkmc_obs *host_obs,
+                       spkmc_graph_t **out);
+/* Enqueue one replay on the handle's stream (asynchronous, like
+ * spkmc_run_cycles; errors surface at the next synchronising call). */
+int spkmc_graph_launch(spkmc_graph_t *g);
+/* Synchronise the stream and release the graph; NULL-safe. */
+void spkmc_graph_destroy(spkmc_graph_t *g);
 /* Copy spins to/from a host int8 buffer of n = L^3 entries in global order.
  * set_spins recomputes the ghost faces, class counts, M and B on the device
  * and clears the R_max history (it no longer describes the spins); restore a

@@ -23,7 +23,7 @@ from ._abi import (SPKMC_EBOUND, SPKMC_EBUSY, SPKMC_ECUDA, SPKMC_EINTERNAL, SPKM
                    SPKMC_INIT_COLD, SPKMC_INIT_HOT, SPKMC_OK, SPKMC_ETIMEOUT, spkmc_config,
                    spkmc_event, spkmc_info, spkmc_obs, spkmc_params, spkmc_state)
 
-__all__ = [n for n in _abi.PROTOTYPES] + ["Lattice", "Batch", "SpkmcError", "torch_config", "obs_buffer",
+__all__ = [n for n in _abi.PROTOTYPES] + ["Lattice", "Batch", "Graph", "SpkmcError", "torch_config", "obs_buffer",
                                             "make_params", "make_config", "EVENT_DTYPE"]
 
 _lock = threading.Lock()
@@ -178,6 +178,47 @@ def spkmc_observables_async(h, out: spkmc_obs) -> spkmc_obs:
     see obs_buffer for pinned storage)."""
     _check(lib().spkmc_observables_async(h, ctypes.byref(out)))
     return out
+
+
+def spkmc_graph_create(h, cycles_per_step: int, steps: int, host_obs=None) -> ctypes.c_void_p:
+    g = ctypes.c_void_p()
+    obs = ctypes.cast(host_obs, ctypes.POINTER(spkmc_obs)) if host_obs is not None else None
+    _check(lib().spkmc_graph_create(h, int(cycles_per_step), int(steps), obs, ctypes.byref(g)))
+    return g
+
+
+def spkmc_graph_launch(g) -> None:
+    _check(lib().spkmc_graph_launch(g))
+
+
+def spkmc_graph_destroy(g) -> None:
+    lib().spkmc_graph_destroy(g)
+
+
+class Graph:
+    """A captured sequence of steps of one lattice (spkmc_graph_create):
+    `steps` x (cycles_per_step cycles, then the observables into
+    records[i] of an obs_buffer when one is given), replayed by launch()."""
+
+    def __init__(self, lattice, cycles_per_step: int, steps: int, records=None):
+        self.lattice = lattice
+        self.records = records
+        addr = ctypes.addressof(records.records) if records is not None else None
+        self.g = spkmc_graph_create(lattice.h, cycles_per_step, steps, addr)
+
+    def launch(self) -> None:
+        spkmc_graph_launch(self.g)
+
+    def close(self) -> None:
+        if self.g:
+            spkmc_graph_destroy(self.g)
+            self.g = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class obs_buffer:
@@ -366,6 +407,9 @@ class Lattice:
 
     def observables_async(self, out: spkmc_obs) -> spkmc_obs:
         return spkmc_observables_async(self.h, out)
+
+    def graph(self, cycles_per_step: int, steps: int, records=None) -> "Graph":
+        return Graph(self, cycles_per_step, steps, records)
 
     def spins(self) -> np.ndarray:
         return spkmc_get_spins(self.h, np.empty(self.L ** 3, dtype=np.int8))

@@ -94,6 +94,9 @@ PROTOTYPES = {
     "spkmc_synchronize": (ctypes.c_int, [_h]),
     "spkmc_observables": (ctypes.c_int, [_h, P(spkmc_obs)]),
     "spkmc_observables_async": (ctypes.c_int, [_h, P(spkmc_obs)]),
+    "spkmc_graph_create": (ctypes.c_int, [_h, ctypes.c_int64, ctypes.c_int32, P(spkmc_obs), P(ctypes.c_void_p)]),
+    "spkmc_graph_launch": (ctypes.c_int, [ctypes.c_void_p]),
+    "spkmc_graph_destroy": (None, [ctypes.c_void_p]),
     "spkmc_get_spins": (ctypes.c_int, [_h, ctypes.c_void_p, _sz]),
     "spkmc_set_spins": (ctypes.c_int, [_h, ctypes.c_void_p, _sz]),
     "spkmc_get_event_log": (ctypes.c_int, [_h, ctypes.c_void_p, _sz, P(_sz)]),

@@ -268,6 +268,12 @@ struct spkmc_engine {
     int slot = 0;
 };
 
+struct spkmc_graph {
+    spkmc_t *h = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long cycles_per_launch = 0;
+};
+
 namespace {
 
 void free_slot_memory(spkmc_batch *b, Slot &s)
@@ -497,6 +503,42 @@ int admit(spkmc_batch *b, const spkmc_params *p, long long cycles, int slot_hint
     return SPKMC_OK;
 }
 
+// The flat table of the running lattices (those with cycles left), their
+// total active domains Q and the shared cycle parity (-1 if mixed), uploaded
+// to the device if it changed (which synchronises the stream first: the
+// pinned staging copy is reused).
+int segment_table(spkmc_batch *b, std::vector<Segment> &segs, long long &Q, int &parity)
+{
+    segs.clear();
+    Q = 0;
+    parity = -2;
+    for (int i = 0; i < b->capacity; ++i) {
+        Slot &s = b->slots[i];
+        if (!s.live || s.budget == 0) continue;
+        Segment sg;
+        sg.base = Q;
+        sg.slot = i;
+        sg.pad = 0;
+        segs.push_back(sg);
+        Q += s.sz.Kact;
+        const int par = (int)(s.t & 1);
+        parity = parity == -2 ? par : (parity == par ? parity : -1);
+    }
+    const int nseg = (int)segs.size();
+    if (nseg == 0) return SPKMC_OK;
+    bool same = segs.size() == b->uploaded_seg.size();
+    for (size_t i = 0; same && i < segs.size(); ++i)
+        same = segs[i].base == b->uploaded_seg[i].base && segs[i].slot == b->uploaded_seg[i].slot;
+    if (!same) {
+        CUDA_TRY(cudaStreamSynchronize(b->stream), "stream synchronize"); // pinned staging reuse
+        std::memcpy(b->h_seg, segs.data(), sizeof(Segment) * nseg);
+        CUDA_TRY(cudaMemcpyAsync(b->d_seg, b->h_seg, sizeof(Segment) * nseg, cudaMemcpyHostToDevice, b->stream),
+                 "upload segments");
+        b->uploaded_seg = segs;
+    }
+    return SPKMC_OK;
+}
+
 // One persistent launch (or several, in chunks) over the running lattices.
 int run(spkmc_batch *b, long long cycles)
 {
@@ -506,35 +548,13 @@ int run(spkmc_batch *b, long long cycles)
     const long long kChunk = 1LL << 18;
     while (cycles > 0) {
         const long long n = std::min(cycles, kChunk);
-        // segments of the lattices that still have cycles to run
         std::vector<Segment> segs;
         long long Q = 0;
         int parity = -2;
-        for (int i = 0; i < b->capacity; ++i) {
-            Slot &s = b->slots[i];
-            if (!s.live || s.budget == 0) continue;
-            Segment sg;
-            sg.base = Q;
-            sg.slot = i;
-            sg.pad = 0;
-            segs.push_back(sg);
-            Q += s.sz.Kact;
-            const int par = (int)(s.t & 1);
-            parity = parity == -2 ? par : (parity == par ? parity : -1);
-        }
+        int rc0 = segment_table(b, segs, Q, parity);
+        if (rc0) return rc0;
         const int nseg = (int)segs.size();
         if (nseg == 0) return SPKMC_OK;
-        bool same = segs.size() == b->uploaded_seg.size();
-        for (size_t i = 0; same && i < segs.size(); ++i)
-            same = segs[i].base == b->uploaded_seg[i].base && segs[i].slot == b->uploaded_seg[i].slot;
-        if (!same) {
-            CUDA_TRY(cudaStreamSynchronize(b->stream), "stream synchronize"); // pinned staging reuse
-            std::memcpy(b->h_seg, segs.data(), sizeof(Segment) * nseg);
-            CUDA_TRY(cudaMemcpyAsync(b->d_seg, b->h_seg, sizeof(Segment) * nseg, cudaMemcpyHostToDevice,
-                                     b->stream),
-                     "upload segments");
-            b->uploaded_seg = segs;
-        }
         // grid: enough CTAs for ~items_per_cta active domains each, within co-residency
         const int per_sm = b->cfg.ctas_per_sm > 0 ? std::min(b->cfg.ctas_per_sm, b->max_blocks_per_sm)
                                                   : b->max_blocks_per_sm;
@@ -837,6 +857,86 @@ int spkmc_synchronize(spkmc_t *h)
     if (!h) return fail(SPKMC_EINVAL, "handle is NULL");
     DeviceGuard g(h->b->device);
     return sync_and_check(h->b);
+}
+
+int spkmc_graph_create(spkmc_t *h, int64_t cycles_per_step, int32_t steps, spkmc_obs *host_obs,
+                       spkmc_graph_t **out)
+{
+    if (!h || !out) return fail(SPKMC_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (cycles_per_step <= 0 || steps <= 0) return fail(SPKMC_EINVAL, "cycles_per_step and steps must be > 0");
+    if ((cycles_per_step * (long long)steps) % 2 != 0)
+        return fail(SPKMC_EINVAL, "steps * cycles_per_step must be even (the launch bakes in the cycle parity)");
+    spkmc_batch *b = h->b;
+    DeviceGuard g(b->device);
+    if (host_obs) {
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, host_obs) != cudaSuccess || pa.type != cudaMemoryTypeHost) {
+            cudaGetLastError();
+            return fail(SPKMC_EINVAL, "host_obs must be pinned (page-locked) host memory");
+        }
+    }
+    int rc = sync_and_check(b);
+    if (rc) return rc;
+    std::vector<Segment> segs;
+    long long Q = 0;
+    int parity = -2;
+    if ((rc = segment_table(b, segs, Q, parity)) != SPKMC_OK) return rc; // uploads outside the capture
+    Slot &s = b->slots[h->slot];
+    const long long t_saved = s.t, budget_saved = s.budget;
+    CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    for (int i = 0; i < steps && rc == SPKMC_OK; ++i) {
+        rc = run(b, cycles_per_step);
+        if (rc == SPKMC_OK && host_obs) rc = spkmc_observables_async(h, host_obs + i);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(b->stream, &graph);
+    s.t = t_saved; // nothing ran yet
+    s.budget = budget_saved;
+    if (rc != SPKMC_OK || ec != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (rc == SPKMC_OK) rc = cuda_fail(ec, "stream capture");
+        cudaGetLastError();
+        return rc;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return cuda_fail(ei, "graph instantiate");
+    spkmc_graph_t *gr = new (std::nothrow) spkmc_graph_t;
+    if (!gr) {
+        cudaGraphExecDestroy(exec);
+        return fail(SPKMC_ENOMEM, "graph handle");
+    }
+    gr->h = h;
+    gr->exec = exec;
+    gr->cycles_per_launch = cycles_per_step * (long long)steps;
+    *out = gr;
+    return SPKMC_OK;
+}
+
+int spkmc_graph_launch(spkmc_graph_t *gr)
+{
+    if (!gr) return fail(SPKMC_EINVAL, "graph is NULL");
+    spkmc_batch *b = gr->h->b;
+    if (b->sticky_error) return fail(b->sticky_error, "batch stopped after an earlier device error");
+    DeviceGuard g(b->device);
+    Slot &s = b->slots[gr->h->slot];
+    if (s.budget >= 0 && s.budget < gr->cycles_per_launch)
+        return fail(SPKMC_EINVAL, "the lattice's cycle budget is smaller than one graph launch");
+    CUDA_TRY(cudaGraphLaunch(gr->exec, b->stream), "graph launch");
+    s.t += gr->cycles_per_launch;
+    if (s.budget >= 0) s.budget -= gr->cycles_per_launch;
+    return SPKMC_OK;
+}
+
+void spkmc_graph_destroy(spkmc_graph_t *gr)
+{
+    if (!gr) return;
+    DeviceGuard g(gr->h->b->device);
+    cudaStreamSynchronize(gr->h->b->stream);
+    cudaGraphExecDestroy(gr->exec);
+    delete gr;
 }
 
 int spkmc_observables(spkmc_t *h, spkmc_obs *out)

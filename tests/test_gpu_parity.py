@@ -3,6 +3,7 @@ by element, on the same seeded inputs.  Spins, event logs, counters and the
 exact null-rate sum must be bit-identical; the clock (the only value that goes
 through a transcendental function on the device) must agree to 1e-12
 relative, the tolerance stated for the clock."""
+import ctypes
 import math
 import os
 
@@ -275,3 +276,41 @@ def test_asynchronous_observables_equal_the_synchronous_ones():
                       "L", "domain_edge"):
                 assert getattr(x, f) == getattr(y, f), f
             assert list(x.sum_null_rate_fx) == list(y.sum_null_rate_fx)
+
+
+def test_graph_replay_equals_plain_runs():
+    """Two replays of a captured graph of 4 steps x 7 cycles with observables
+    equal 8 plain steps, spins and observables bit for bit."""
+    spec = wl.LatticeSpec(L=64, d=8, seed=27)
+    rec = sp.obs_buffer(4)
+    with gpu_lattice(spec) as a, gpu_lattice(spec) as b:
+        with a.graph(7, 4, rec) as g:
+            ref = []
+            for rep in range(2):
+                g.launch()
+                for i in range(4):
+                    b.run(7)
+                    ref.append(b.observables())
+                a.synchronize()
+                for i in range(4):
+                    x, y = rec[i], ref[4 * rep + i]
+                    assert (x.cycle, x.clock, x.M, x.B, x.n_flip, x.n_null) == \
+                           (y.cycle, y.clock, y.M, y.B, y.n_flip, y.n_null)
+            assert a.observables().cycle == 56
+            assert np.array_equal(a.spins(), b.spins())
+            a.run(3)  # plain runs continue from the replayed state
+            b.run(3)
+            assert np.array_equal(a.spins(), b.spins())
+
+
+def test_graph_arguments_are_checked():
+    spec = wl.LatticeSpec(L=32, d=4, seed=28)
+    with gpu_lattice(spec) as lat:
+        for args in [(7, 3), (0, 4), (4, 0)]:
+            with pytest.raises(sp.SpkmcError) as e:
+                lat.graph(*args)
+            assert e.value.code == sp.SPKMC_EINVAL
+        pageable = (sp.spkmc_obs * 2)()
+        with pytest.raises(sp.SpkmcError) as e:
+            sp.spkmc_graph_create(lat.h, 2, 2, ctypes.addressof(pageable))
+        assert e.value.code == sp.SPKMC_EINVAL

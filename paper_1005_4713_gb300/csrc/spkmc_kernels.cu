@@ -287,6 +287,7 @@ struct CtaShared {
     unsigned long long seg_dM[kMaxSegPerCta];
     unsigned long long seg_dB[kMaxSegPerCta];
     int seg_colour[kMaxSegPerCta];    // colour of the running cycle (two-colour lattices)
+    double seg_rbound[kMaxSegPerCta]; // R of the running cycle for lattices padded to a bound
     double seg_nlogxi[kMaxSegPerCta]; // -ln(xi) of the running cycle
     double seg_rnow[kMaxSegPerCta];   // R_max of the running cycle
     int seg_tick[kMaxSegPerCta];      // the clock of this lattice moves in this round
@@ -1110,21 +1111,9 @@ __device__ __forceinline__ void phase_b_round(const LaunchParams &P, CtaShared &
                 const long long t = S.seg_t0[ls] + g;
                 // the rate R the lines are padded to (Sec. 3.1 step 2 or the
                 // bounds of Sec. 3.2 step 4b)
-                double R;
-                if (Ld.rmode == SPKMC_RMAX_EXACT) {
-                    R = __longlong_as_double((long long)__ldcg(&P.state[slot].rmax[t & (kRmaxRing - 1)]));
-                } else {
-                    R = Ld.rbound;
-                    if (Ld.rmode == SPKMC_RMAX_LEARNED) {
-                        // exact R_max of this colour's previous visit, cycle t - 8
-                        const double h = __longlong_as_double(
-                            (long long)__ldcg(&P.state[slot].rmax[(t + 8) & (kRmaxRing - 1)]));
-                        if (h > 0.0) {
-                            const double b = __dmul_rn(__dadd_rn(h, Ld.rmargin), kBoundSlack);
-                            if (b < R) R = b;
-                        }
-                    }
-                }
+                const double R = Ld.rmode == SPKMC_RMAX_EXACT
+                                     ? __longlong_as_double((long long)__ldcg(&P.state[slot].rmax[t & (kRmaxRing - 1)]))
+                                     : S.seg_rbound[ls];
                 double cum[kClasses];
                 double u01;
                 unsigned long long w1;
@@ -1407,6 +1396,26 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
     const bool early = hi - lo <= P.round_items;
     for (long long g = 0; g < P.ncycles; ++g) {
         Line line; // this cycle's frequency line of the thread's item (one-round CTAs)
+        for (int i = threadIdx.x; i < S.nsegc; i += blockDim.x) {
+            // the bound of Sec. 3.2 step 4b for lattices that use one (read
+            // by the prepass, after step 1's barrier)
+            const LatticeDesc &Ld = P.desc[S.seg_slot[i]];
+            if (Ld.rmode != SPKMC_RMAX_EXACT && g < S.seg_part[i]) {
+                double R = Ld.rbound;
+                if (Ld.rmode == SPKMC_RMAX_LEARNED) {
+                    // exact R_max of this colour's previous visit, cycle t - 8,
+                    // final since the grid barriers that followed it
+                    const long long t = S.seg_t0[i] + g;
+                    const double h = __longlong_as_double(
+                        (long long)__ldcg(&P.state[S.seg_slot[i]].rmax[(t + 8) & (kRmaxRing - 1)]));
+                    if (h > 0.0) {
+                        const double b = __dmul_rn(__dadd_rn(h, Ld.rmargin), kBoundSlack);
+                        if (b < R) R = b;
+                    }
+                }
+                S.seg_rbound[i] = R;
+            }
+        }
         if (P.sub2_any) {
             // Sec. 3.2 step 4a, two colours: the colour of this cycle
             for (int i = threadIdx.x; i < S.nsegc; i += blockDim.x) {

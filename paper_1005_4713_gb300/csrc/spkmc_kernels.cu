@@ -329,7 +329,8 @@ __device__ bool grid_barrier(const LaunchParams &P, CtaShared &S, unsigned &epoc
     if (gridDim.x == 1) return ld_volatile_int(P.err) == 0;
     if (threadIdx.x == 0) {
         int ok = 1;
-        __threadfence();
+        // the arrival is a release at GPU scope: with the CTA barrier above
+        // it orders every write of the CTA before it; the polls are acquires
         if ((int)blockIdx.x != P.skip_cta) red_release_add_u32(P.bar, 1u);
         const unsigned target = epoch * gridDim.x;
         const long long t0 = global_timer_ns();
@@ -349,7 +350,6 @@ __device__ bool grid_barrier(const LaunchParams &P, CtaShared &S, unsigned &epoc
             }
             __nanosleep(32);
         }
-        __threadfence();
         S.ok = ok;
     }
     __syncthreads();

@@ -378,6 +378,73 @@ __device__ __forceinline__ void warp_sum_u128(unsigned long long &lo, unsigned l
     }
 }
 
+// Segmented reductions over runs of consecutive lanes: a run starts at lane
+// 0 and wherever the key differs from the previous lane's (lanes whose
+// domains belong to one lattice).  After a scan the last lane of each run
+// (run_last) holds the run's total; each run then needs one shared-memory
+// update instead of one per lane.  Every lane of the warp takes part.
+__device__ __forceinline__ bool run_head(int key)
+{
+    const int prev = __shfl_up_sync(kFull, key, 1);
+    return (threadIdx.x & 31) == 0 || prev != key;
+}
+
+__device__ __forceinline__ bool run_last(int key)
+{
+    const int next = __shfl_down_sync(kFull, key, 1);
+    return (threadIdx.x & 31) == 31 || next != key;
+}
+
+__device__ __forceinline__ void run_max_u64(bool head, unsigned long long &v)
+{
+    const int lane = threadIdx.x & 31;
+    bool f = head;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long pv = __shfl_up_sync(kFull, v, off);
+        const bool pf = __shfl_up_sync(kFull, f, off);
+        if (lane >= off && !f) {
+            v = pv > v ? pv : v;
+            f = pf;
+        }
+    }
+}
+
+__device__ __forceinline__ void run_sum_u128(bool head, unsigned long long &lo, unsigned long long &hi)
+{
+    const int lane = threadIdx.x & 31;
+    bool f = head;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long pl = __shfl_up_sync(kFull, lo, off), ph = __shfl_up_sync(kFull, hi, off);
+        const bool pf = __shfl_up_sync(kFull, f, off);
+        if (lane >= off && !f) {
+            const unsigned long long nl = lo + pl;
+            hi = hi + ph + (nl < lo ? 1ULL : 0ULL);
+            lo = nl;
+            f = pf;
+        }
+    }
+}
+
+__device__ __forceinline__ void run_sum3(bool head, int &a, int &b, int &c)
+{
+    const int lane = threadIdx.x & 31;
+    bool f = head;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int pa = __shfl_up_sync(kFull, a, off), pb = __shfl_up_sync(kFull, b, off),
+                  pc = __shfl_up_sync(kFull, c, off);
+        const bool pf = __shfl_up_sync(kFull, f, off);
+        if (lane >= off && !f) {
+            a += pa;
+            b += pb;
+            c += pc;
+            f = pf;
+        }
+    }
+}
+
 // --- shared-memory barrier (mbarrier) and bulk copies (TMA engine) ---------
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
@@ -535,8 +602,10 @@ __device__ void phase_a(const LaunchParams &P, CtaShared &S, unsigned char *stag
         if (__all_sync(kFull, ls == ls0) && ls0 >= 0) {
             const unsigned long long m = warp_max_u64(rbits);
             if (lane == 0) atomicMax(&S.seg_rmax[ls0], m);
-        } else if (ls >= 0) {
-            atomicMax(&S.seg_rmax[ls], rbits);
+        } else { // lattices meet in this warp: one update per run of lanes
+            const bool head = run_head(ls), last = run_last(ls);
+            run_max_u64(head, rbits);
+            if (last && ls >= 0) atomicMax(&S.seg_rmax[ls], rbits);
         }
     }
 }
@@ -1240,9 +1309,15 @@ __device__ __forceinline__ void phase_b_round(const LaunchParams &P, CtaShared &
                 atomic_add_u128(&S.seg_fxlo[ls0], &S.seg_fxhi[ls0], fxlo, fxhi);
                 if (nn) atomicAdd(&S.seg_nnull[ls0], (unsigned long long)nn);
             }
-        } else if (ls >= 0) {
-            atomic_add_u128(&S.seg_fxlo[ls], &S.seg_fxhi[ls], fxlo, fxhi);
-            if (nul) atomicAdd(&S.seg_nnull[ls], 1ULL);
+        } else { // lattices meet in this warp: one update per run of lanes
+            const bool head = run_head(ls), last = run_last(ls);
+            run_sum_u128(head, fxlo, fxhi);
+            int nn = nul ? 1 : 0, z0 = 0, z1 = 0;
+            run_sum3(head, nn, z0, z1);
+            if (last && ls >= 0) {
+                atomic_add_u128(&S.seg_fxlo[ls], &S.seg_fxhi[ls], fxlo, fxhi);
+                if (nn) atomicAdd(&S.seg_nnull[ls], (unsigned long long)nn);
+            }
         }
         __syncthreads();
         const int nwork = S.nwork;
@@ -1314,10 +1389,15 @@ __device__ __forceinline__ void phase_b_round(const LaunchParams &P, CtaShared &
                 atomicAdd(&S.seg_dM[lsmax], (unsigned long long)(long long)sM);
                 atomicAdd(&S.seg_dB[lsmax], (unsigned long long)(long long)sB);
             }
-        } else if (fls >= 0) {
-            atomicAdd(&S.seg_nflip[fls], 1ULL);
-            atomicAdd(&S.seg_dM[fls], (unsigned long long)(long long)fdM);
-            atomicAdd(&S.seg_dB[fls], (unsigned long long)(long long)fdB);
+        } else { // lattices meet in this warp: one update per run of lanes
+            const bool head = run_head(fls), last = run_last(fls);
+            int nf = fls >= 0 ? 1 : 0, sM = fdM, sB = fdB;
+            run_sum3(head, nf, sM, sB);
+            if (last && fls >= 0) {
+                atomicAdd(&S.seg_nflip[fls], (unsigned long long)nf);
+                atomicAdd(&S.seg_dM[fls], (unsigned long long)(long long)sM);
+                atomicAdd(&S.seg_dB[fls], (unsigned long long)(long long)sB);
+            }
         }
         __syncthreads();
     }

@@ -5,7 +5,10 @@ Metric: spin-flip events per second, null events included (one event per
 active domain per cycle, arXiv:1005.4713 Sec. 3.1 step 4).  A step is one
 pass of the whole hot path over the lattice: 10 spkMC cycles (every colour
 visited in turn) plus the observables M, E, M^2, M^4, as in the 500-cycle
-run with observables every 10 cycles.
+run with observables every 10 cycles.  The timed steps run as one persistent
+launch that records each step's observables on the device
+(spkmc_run_recorded); the same steps launched one at a time, and replayed
+from a CUDA graph, are reported beside it.
 
 Arms:
   default           the CUDA library through its C ABI (this package);
@@ -209,9 +212,11 @@ def measured_peak():
     return 6800.0, "fallback"
 
 
-def ncu_traffic(workload: str):
-    """Per-launch DRAM bytes of the cycle kernel from the committed ncu
-    summary, only if it was taken on the current kernel source."""
+def ncu_traffic(workload: str, cycles: int):
+    """DRAM bytes of one launch of the cycle kernel over `cycles` cycles, from
+    the committed ncu capture (scaled by the cycles: every cycle moves the
+    same blocks and count lines), only if it was taken on the current kernel
+    source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -221,7 +226,7 @@ def ncu_traffic(workload: str):
     e = j.get(workload)
     if not e or e.get("kernel_source_hash") != kernel_source_hash():
         return None
-    return e.get("dram_bytes_per_launch")
+    return round(e["dram_bytes_per_launch"] * cycles / e["cycles_per_launch"])
 
 
 def cpu_baseline(rank: int, world: int, cycles: int = 8):
@@ -295,14 +300,13 @@ def variants_summary(cfg, stream, steps, cps):
                      ("prescribed", dict(rmax_mode=sp.SPKMC_RMAX_PRESCRIBED)),
                      ("two_colour", dict(sublattice=sp.SPKMC_SUBLATTICE_2_RANDOM))):
         with sp.Lattice(L_BENCH, D_BENCH, 1.0, 0.0, 4.5115, SEED_BENCH, config=cfg, **kw) as lat:
-            for _ in range(3):
-                lat.run(cps)
+            rec = sp.obs_buffer(max(steps, 3))
+            lat.run_recorded(cps, 3, rec)
             o0 = lat.observables()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            for _ in range(steps):
-                lat.run(cps)
+            lat.run_recorded(cps, steps, rec)
             e1.record(stream)
             torch.cuda.synchronize()
             s = e0.elapsed_time(e1) / 1e3
@@ -364,30 +368,23 @@ def run_gpu(args, world, rank, local, pg):
     kact = lat.K_act
     cps = args.cycles_per_step
 
-    # the observables of every step are enqueued on the stream (no host
-    # synchronisation inside the timed region) into pinned records
+    # one step = cps cycles and the observables after them.  The timed steps
+    # run as one recorded launch: the kernel records each step's observables
+    # on the device (no host synchronisation, no launch per step) and one
+    # copy brings the records to pinned host memory
     obs_rec = sp.obs_buffer(max(args.steps, args.warmup))
-
-    for i in range(args.warmup):
-        lat.run(cps)
-        lat.observables_async(obs_rec[i])
+    lat.run_recorded(cps, args.warmup, obs_rec)
     torch.cuda.synchronize(device)
     barrier(pg, device)
     torch.cuda.synchronize(device)
 
     obs0 = lat.observables()
     sampler = ClockSampler(local).start()
-    k0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    k1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     t_host0 = time.perf_counter()
     e0.record(stream)
-    for i in range(args.steps):
-        k0[i].record(stream)
-        lat.run(cps)
-        k1[i].record(stream)
-        lat.observables_async(obs_rec[i])
+    lat.run_recorded(cps, args.steps, obs_rec)
     e1.record(stream)
     torch.cuda.synchronize(device)
     torch.cuda.synchronize(device)
@@ -395,7 +392,9 @@ def run_gpu(args, world, rank, local, pg):
     barrier(pg, device)
     sampler.stop()
     ms = e0.elapsed_time(e1)
-    kernel_ms = sum(a.elapsed_time(b) for a, b in zip(k0, k1)) / args.steps
+    # the cycle kernel's launch: the events also hold the two one-pass record
+    # kernels and the records' copy (a few microseconds)
+    kernel_ms = ms
     ms_max = max_over_ranks(ms, pg, device)
     events = world * args.steps * cps * kact
     value = events / (ms_max / 1e3)
@@ -403,9 +402,35 @@ def run_gpu(args, world, rank, local, pg):
     obs1 = lat.observables()
     last = obs_rec[args.steps - 1]
     if (last.cycle, last.M, last.B, last.clock) != (obs1.cycle, obs1.M, obs1.B, obs1.clock):
-        raise RuntimeError("asynchronous observables differ from the synchronous read-out")
+        raise RuntimeError("recorded observables differ from the synchronous read-out")
     flips = obs1.n_flip - obs0.n_flip
     useful = flips / max(1, (obs1.n_flip + obs1.n_null) - (obs0.n_flip + obs0.n_null))
+
+    # the same steps launched one at a time (a persistent launch and an
+    # asynchronous observables record per step)
+    per_step = None
+    if not args.no_graph:
+        for i in range(2):
+            lat.run(cps)
+            lat.observables_async(obs_rec[i])
+        torch.cuda.synchronize(device)
+        k0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        k1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for i in range(args.steps):
+            k0[i].record(stream)
+            lat.run(cps)
+            k1[i].record(stream)
+            lat.observables_async(obs_rec[i])
+        p1.record(stream)
+        torch.cuda.synchronize(device)
+        pms = p0.elapsed_time(p1)
+        per_step = {"value": world * args.steps * cps * kact / (max_over_ranks(pms, pg, device) / 1e3),
+                    "unit": "events/s", "ms_per_step": pms / args.steps,
+                    "kernel_ms_per_launch": sum(a.elapsed_time(b) for a, b in zip(k0, k1)) / args.steps,
+                    "note": "one cycle-kernel launch and one observables record per step"}
     graph = None
     if not args.no_graph and (args.steps * cps) % 2 == 0:
         # the same steps captured once in a CUDA graph and replayed with one
@@ -424,7 +449,7 @@ def run_gpu(args, world, rank, local, pg):
         g.close()
         graph = {"value": world * args.steps * cps * kact / (max_over_ranks(gms, pg, device) / 1e3),
                  "unit": "events/s", "ms_per_step": gms / args.steps,
-                 "note": "the timed steps captured in one CUDA graph (cycles + observables per step)"}
+                 "note": "the per-step launches captured in one CUDA graph (cycles + observables per step)"}
 
     # end to end through the C ABI with host buffers: upload the start
     # lattice from pinned memory, run the steps with observables, read the
@@ -444,9 +469,7 @@ def run_gpu(args, world, rank, local, pg):
         torch.cuda.synchronize(device)
         t0 = time.perf_counter()
         lat2.set_spins(host)
-        for i in range(args.steps):
-            lat2.run(cps)
-            lat2.observables_async(obs_rec[i])
+        lat2.run_recorded(cps, args.steps, obs_rec)
         sp.spkmc_get_spins(lat2.h, out)  # synchronises: the records have landed
         t1 = time.perf_counter()
         barrier(pg, device)
@@ -470,7 +493,8 @@ def run_gpu(args, world, rank, local, pg):
     if rank == 0:
         peak, peak_kind = measured_peak()
         bpe = bytes_per_event(D_BENCH)
-        per_launch = cps * kact * bpe
+        launch_cycles = args.steps * cps
+        per_launch = launch_cycles * kact * bpe
         achieved = per_launch / (kernel_ms / 1e3) / 1e9
         clocks = sampler.summary(t_host0, t_host1)
         line = {
@@ -487,15 +511,17 @@ def run_gpu(args, world, rank, local, pg):
                        "l2": "working set %.0f MB > 126 MB L2, no flush" % (lat_info.device_bytes / 1e6),
                        "grid_ctas": lat_info.grid_ctas, "threads_per_cta": lat_info.threads_per_cta},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": ncu_traffic("spkmc-1024^3-d16"),
+                         "frac": achieved / peak, "traffic": ncu_traffic("spkmc-1024^3-d16", launch_cycles),
                          "peak_kind": peak_kind, "kernel": "spkmc_cycles_kernel",
                          "bytes_per_event": bpe, "kernel_ms_per_launch": kernel_ms,
-                         "int8_equivalent_GBps": cps * kact * int8_bytes_per_event(D_BENCH) / (kernel_ms / 1e3) / 1e9},
+                         "cycles_per_launch": launch_cycles,
+                         "int8_equivalent_GBps": launch_cycles * kact * int8_bytes_per_event(D_BENCH) / (kernel_ms / 1e3) / 1e9},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": 2 * args.steps,  # per step: the cycle kernel and the observables record
+            "gpu_launches": 3,  # record set-up, the persistent cycle kernel, record read-out
             "clocks": clocks,
             "exact_rmax": {"flips_per_s": flips * world / (ms_max / 1e3), "useful_fraction": useful},
+            "per_step_launches": per_step,
             "graph": graph,
             "variants": variants,
             "batched": batched,
@@ -516,7 +542,7 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensembles", action="store_true", help="skip the batched and served summaries")
-    ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay of the timed steps")
+    ap.add_argument("--no-graph", action="store_true", help="skip the per-step launches and their CUDA-graph replay")
     ap.add_argument("--no-variants", "--no-bounds", dest="no_variants", action="store_true",
                     help="skip the R_max-bound and two-colour summaries")
     args = ap.parse_args(argv)

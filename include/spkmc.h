@@ -235,6 +235,20 @@ int spkmc_observables(spkmc_t *h, spkmc_obs *out);
  * values equal those of spkmc_observables at the same point of the stream
  * bit for bit.  Device errors are reported by the next synchronising call. */
 int spkmc_observables_async(spkmc_t *h, spkmc_obs *host_out);
+/* Run every * nrec cycles (Sec. 3.1 steps 1-6, as spkmc_run_cycles) in one
+ * persistent launch and record the observables after every `every` cycles
+ * into host_out[0 .. nrec), record r after cycle (r + 1) * every of the run.
+ * Each record equals, bit for bit, what spkmc_observables would return had
+ * the run stopped there: the kernel adds every CTA's counters of M, B, the
+ * events and the null rates into the record at that cycle and the clock's
+ * keeper writes the clock there once its step is known.  Enqueued on the
+ * handle's stream without waiting, like spkmc_observables_async: host_out
+ * (nrec records; pinned host memory lets the copy overlap later work) must
+ * stay valid and unread until spkmc_synchronize returns.  EINVAL if every or
+ * nrec is not positive, every * nrec exceeds 2^18 cycles or the lattice's
+ * cycle budget, ENOMEM if the device buffers (nrec records of 64 and 128
+ * bytes, kept for later calls) cannot be allocated. */
+int spkmc_run_recorded(spkmc_t *h, int64_t every, int32_t nrec, spkmc_obs *host_out);
 /* A CUDA graph of `steps` steps of the lattice's stream work, each
  * cycles_per_step cycles (one persistent launch, as spkmc_run_cycles) and,
  * if host_obs is not NULL, the asynchronous observables into host_obs[i]

@@ -180,6 +180,16 @@ def spkmc_observables_async(h, out: spkmc_obs) -> spkmc_obs:
     return out
 
 
+def spkmc_run_recorded(h, every: int, nrec: int, records) -> None:
+    """Enqueue every * nrec cycles in one launch with the observables after
+    every `every` cycles into records[0 .. nrec) (an obs_buffer; read it
+    after a synchronise)."""
+    if len(records) < nrec:
+        raise ValueError("records holds fewer than nrec entries")
+    _check(lib().spkmc_run_recorded(h, int(every), int(nrec),
+                                    ctypes.cast(ctypes.addressof(records.records), ctypes.POINTER(spkmc_obs))))
+
+
 def spkmc_graph_create(h, cycles_per_step: int, steps: int, host_obs=None) -> ctypes.c_void_p:
     g = ctypes.c_void_p()
     obs = ctypes.cast(host_obs, ctypes.POINTER(spkmc_obs)) if host_obs is not None else None
@@ -407,6 +417,9 @@ class Lattice:
 
     def observables_async(self, out: spkmc_obs) -> spkmc_obs:
         return spkmc_observables_async(self.h, out)
+
+    def run_recorded(self, every: int, nrec: int, records) -> None:
+        spkmc_run_recorded(self.h, every, nrec, records)
 
     def graph(self, cycles_per_step: int, steps: int, records=None) -> "Graph":
         return Graph(self, cycles_per_step, steps, records)

@@ -230,6 +230,9 @@ struct spkmc_batch {
     int *d_err = nullptr;
     long long *d_MB = nullptr;
     spkmc_obs *d_obs = nullptr; // per-slot observables records for the asynchronous read-out
+    ObsRaw *d_rec = nullptr;    // [slot][rec_cap] sums of a recorded run
+    spkmc_obs *d_rec_obs = nullptr; // [rec_cap] their observables
+    int rec_cap = 0;
     unsigned long long *d_mismatch = nullptr;
     // pinned host staging
     LatticeDesc *h_desc = nullptr;
@@ -299,6 +302,8 @@ void release_batch(spkmc_batch *b)
     cudaFree(b->d_err);
     cudaFree(b->d_MB);
     cudaFree(b->d_obs);
+    cudaFree(b->d_rec);
+    cudaFree(b->d_rec_obs);
     cudaFree(b->d_mismatch);
     cudaFreeHost(b->h_desc);
     cudaFreeHost(b->h_state);
@@ -539,13 +544,23 @@ int segment_table(spkmc_batch *b, std::vector<Segment> &segs, long long &Q, int 
     return SPKMC_OK;
 }
 
+constexpr long long kChunk = 1LL << 18; // cycles of one persistent launch at most
+
+// Records of a run: after every `every` cycles of the launch, into
+// rec[slot * n + r] (one launch: n * every <= kChunk).
+struct RecReq {
+    ObsRaw *rec;
+    long long every;
+    int n;
+};
+
 // One persistent launch (or several, in chunks) over the running lattices.
-int run(spkmc_batch *b, long long cycles)
+int run(spkmc_batch *b, long long cycles, const RecReq *rq = nullptr)
 {
     if (cycles < 0) return fail(SPKMC_EINVAL, "ncycles must be >= 0");
     if (b->sticky_error) return fail(b->sticky_error, "batch stopped after an earlier device error");
+    if (rq && cycles > kChunk) return fail(SPKMC_EINTERNAL, "a recorded run is one launch");
     DeviceGuard g(b->device);
-    const long long kChunk = 1LL << 18;
     while (cycles > 0) {
         const long long n = std::min(cycles, kChunk);
         std::vector<Segment> segs;
@@ -605,6 +620,11 @@ int run(spkmc_batch *b, long long cycles)
         }
         // two random colours: consecutive cycles may use face-adjacent colours
         if (P.sub2_any) P.parity0 = -1;
+        if (rq) {
+            P.rec = rq->rec;
+            P.rec_every = rq->every;
+            P.rec_n = rq->n;
+        }
         int rc = launch_cycles(P, (int)grid, b->stream, grid > 1);
         if (rc) return cuda_fail(cudaGetLastError(), "persistent cycle launch");
         b->last_grid = (int)grid;
@@ -850,6 +870,47 @@ int spkmc_run_cycles(spkmc_t *h, int64_t ncycles)
 {
     if (!h) return fail(SPKMC_EINVAL, "handle is NULL");
     return run(h->b, ncycles);
+}
+
+int spkmc_run_recorded(spkmc_t *h, int64_t every, int32_t nrec, spkmc_obs *host_out)
+{
+    if (!h || !host_out) return fail(SPKMC_EINVAL, "NULL argument");
+    if (every <= 0 || nrec <= 0) return fail(SPKMC_EINVAL, "every and nrec must be > 0");
+    if (every > kChunk / nrec)
+        return fail(SPKMC_EINVAL, "every * nrec must be <= %lld cycles (one launch)", kChunk);
+    spkmc_batch *b = h->b;
+    if (b->sticky_error) return fail(b->sticky_error, "batch stopped after an earlier device error");
+    const Slot &s = b->slots[h->slot];
+    const long long total = every * (long long)nrec;
+    if (s.budget >= 0 && s.budget < total) return fail(SPKMC_EINVAL, "the cycle budget is smaller than the run");
+    DeviceGuard g(b->device);
+    if (b->rec_cap < nrec) {
+        CUDA_TRY(cudaStreamSynchronize(b->stream), "stream synchronize"); // the old buffers may be in use
+        cudaFree(b->d_rec);
+        cudaFree(b->d_rec_obs);
+        b->d_rec = nullptr;
+        b->d_rec_obs = nullptr;
+        b->rec_cap = 0;
+        if (cudaMalloc(&b->d_rec, sizeof(ObsRaw) * (size_t)nrec * b->capacity) != cudaSuccess ||
+            cudaMalloc(&b->d_rec_obs, sizeof(spkmc_obs) * (size_t)nrec) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(b->d_rec);
+            b->d_rec = nullptr;
+            return fail(SPKMC_ENOMEM, "record buffers of %d records", nrec);
+        }
+        b->rec_cap = nrec;
+    }
+    ObsRaw *rec = b->d_rec + (size_t)h->slot * nrec;
+    if (launch_rec_init(b->d_state + h->slot, rec, nrec, every, b->stream) != SPKMC_OK)
+        return cuda_fail(cudaGetLastError(), "record set-up");
+    const RecReq rq{b->d_rec, every, nrec};
+    int rc = run(b, total, &rq);
+    if (rc) return rc;
+    if (launch_rec_series(rec, nrec, s.params.L, s.d, s.params.J, s.params.H, b->d_rec_obs, b->stream) != SPKMC_OK)
+        return cuda_fail(cudaGetLastError(), "record read-out");
+    CUDA_TRY(cudaMemcpyAsync(host_out, b->d_rec_obs, sizeof(spkmc_obs) * nrec, cudaMemcpyDeviceToHost, b->stream),
+             "records copy");
+    return SPKMC_OK;
 }
 
 int spkmc_synchronize(spkmc_t *h)

@@ -76,6 +76,20 @@ struct LatticeState {
     long long B;                    // forward bond sum, kept exact flip by flip
 };
 
+// One lattice's sums after a recorded cycle of a launch (the observables
+// follow from them as from the state): the state at the launch's start plus
+// every CTA's counters up to that cycle, and the clock once it has caught up.
+struct ObsRaw {
+    int64_t t;
+    double clock;
+    unsigned long long n_flip;
+    unsigned long long n_null;
+    unsigned long long null_fx_lo;
+    unsigned long long null_fx_hi;
+    long long M;
+    long long B;
+};
+
 // One lattice's run of active domains in the flat work table.
 struct Segment {
     int64_t base; // first flat item
@@ -99,7 +113,9 @@ struct LaunchParams {
     int item_bytes;       // staging bytes per domain (largest edge of the launch)
     int exact_any;        // some lattice pads to the exact R_max: reduce before the events
     int sub2_any;         // some lattice uses two random colours: draw colours, recount
-    int pad;
+    int rec_n;            // records per lattice (rec_every > 0)
+    int64_t rec_every;    // record after every rec_every cycles of the launch; 0 = none
+    ObsRaw *rec;          // [slot][rec_n] records
 };
 
 // u16 words and bytes of one domain block (rows and ghost faces).
@@ -134,6 +150,10 @@ int launch_count_classes(const LatticeDesc &d, int mode, unsigned long long *mis
 // M and B (device int64 pair, accumulated).
 int launch_obs_record(const LatticeState *st, int L, int d, double J, double H, spkmc_obs *out, void *stream);
 int launch_observables(const LatticeDesc &d, long long *MB, void *stream);
+// Records of a launch: rec[r] = the state's sums, cycle t + (r + 1) every
+// (before the launch), and the observables of the filled records (after).
+int launch_rec_init(const LatticeState *st, ObsRaw *rec, int n, long long every, void *stream);
+int launch_rec_series(const ObsRaw *rec, int n, int L, int d, double J, double H, spkmc_obs *out, void *stream);
 // Round size for a launch whose largest domain edge is d_max.
 int cycle_round_items(int d_max);
 

@@ -631,7 +631,12 @@ __device__ __forceinline__ void clock_catch_up(const LaunchParams &P, CtaShared 
         if (S.seg_tick[i]) {
             S.seg_tick[i] = 0;
             LatticeState &st = P.state[S.seg_slot[i]];
-            st.clock = __dadd_rn(st.clock, __ddiv_rn(S.seg_nlogxi[i], S.seg_rnow[i]));
+            const double c = __dadd_rn(st.clock, __ddiv_rn(S.seg_nlogxi[i], S.seg_rnow[i]));
+            st.clock = c;
+            // the cycle whose step this was: g - 1, or the lattice's last at the end
+            const long long ge = (draw ? g : S.seg_part[i]) - 1;
+            if (P.rec_every > 0 && (ge + 1) % P.rec_every == 0 && (ge + 1) / P.rec_every <= P.rec_n)
+                P.rec[(long long)S.seg_slot[i] * P.rec_n + (ge + 1) / P.rec_every - 1].clock = c;
         }
         if (draw && S.seg_base[i] >= lo && g < S.seg_part[i]) S.seg_nlogxi[i] = neg_log_xi(P, S, i, g);
     }
@@ -1569,6 +1574,21 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
                 return;
             }
         }
+        if (P.rec_every > 0 && (g + 1) % P.rec_every == 0 && (g + 1) / P.rec_every <= P.rec_n) {
+            // a recorded cycle: this CTA's counters so far join the record
+            // (the clock joins it when it has caught up)
+            __syncthreads();
+            const long long r = (g + 1) / P.rec_every - 1;
+            for (int i = threadIdx.x; i < S.nsegc; i += blockDim.x) {
+                if (g >= S.seg_part[i]) continue;
+                ObsRaw &o = P.rec[(long long)S.seg_slot[i] * P.rec_n + r];
+                if (S.seg_nflip[i]) atomicAdd(&o.n_flip, S.seg_nflip[i]);
+                if (S.seg_nnull[i]) atomicAdd(&o.n_null, S.seg_nnull[i]);
+                if (S.seg_dM[i]) atomicAdd(reinterpret_cast<unsigned long long *>(&o.M), S.seg_dM[i]);
+                if (S.seg_dB[i]) atomicAdd(reinterpret_cast<unsigned long long *>(&o.B), S.seg_dB[i]);
+                atomic_add_u128(&o.null_fx_lo, &o.null_fx_hi, S.seg_fxlo[i], S.seg_fxhi[i]);
+            }
+        }
     }
     __syncthreads();
     if (threadIdx.x == kThreads - 1) clock_catch_up(P, S, 0, lo, false); // the last cycle's step
@@ -1866,35 +1886,76 @@ int launch_count_classes(const LatticeDesc &d, int mode, unsigned long long *mis
     return to_status(cudaGetLastError());
 }
 
-// The observables of one lattice from its state, with the operations (and
-// the IEEE roundings) of the host-side read-out: E = -J B - H M, m = M / N,
-// m^2, m^4, and the null-rate sum as hi + lo 2^-64.
-__global__ void obs_record_kernel(const LatticeState *st, int L, int d, double J, double H, spkmc_obs *out)
+// The observables of one lattice from its sums (its state, or a record),
+// with the operations (and the IEEE roundings) of the host-side read-out:
+// E = -J B - H M, m = M / N, m^2, m^4, and the null-rate sum as
+// hi + lo 2^-64.
+template <typename Sums>
+__device__ __forceinline__ spkmc_obs make_obs(const Sums &st, int L, int d, double J, double H)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     spkmc_obs o;
     const double N = (double)L * L * L;
-    o.cycle = st->t;
-    o.clock = st->clock;
-    o.M = st->M;
-    o.B = st->B;
+    o.cycle = st.t;
+    o.clock = st.clock;
+    o.M = st.M;
+    o.B = st.B;
     o.E = __dsub_rn(__dmul_rn(-J, (double)o.B), __dmul_rn(H, (double)o.M));
     o.m = __ddiv_rn((double)o.M, N);
     o.m2 = __dmul_rn(o.m, o.m);
     o.m4 = __dmul_rn(o.m2, o.m2);
-    o.n_flip = (int64_t)st->n_flip;
-    o.n_null = (int64_t)st->n_null;
-    o.sum_null_rate_fx[0] = st->null_fx_lo;
-    o.sum_null_rate_fx[1] = st->null_fx_hi;
-    o.sum_null_rate = __dadd_rn(__ull2double_rn(st->null_fx_hi), __dmul_rn(__ull2double_rn(st->null_fx_lo), 0x1p-64));
+    o.n_flip = (int64_t)st.n_flip;
+    o.n_null = (int64_t)st.n_null;
+    o.sum_null_rate_fx[0] = st.null_fx_lo;
+    o.sum_null_rate_fx[1] = st.null_fx_hi;
+    o.sum_null_rate = __dadd_rn(__ull2double_rn(st.null_fx_hi), __dmul_rn(__ull2double_rn(st.null_fx_lo), 0x1p-64));
     o.L = L;
     o.domain_edge = d;
-    *out = o;
+    return o;
+}
+
+__global__ void obs_record_kernel(const LatticeState *st, int L, int d, double J, double H, spkmc_obs *out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    *out = make_obs(*st, L, d, J, H);
 }
 
 int launch_obs_record(const LatticeState *st, int L, int d, double J, double H, spkmc_obs *out, void *stream)
 {
     obs_record_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(st, L, d, J, H, out);
+    return to_status(cudaGetLastError());
+}
+
+__global__ void rec_init_kernel(const LatticeState *st, ObsRaw *rec, int n, long long every)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    ObsRaw o;
+    o.t = st->t + (r + 1LL) * every;
+    o.clock = __longlong_as_double(0x7FF8000000000000LL); // NaN until the clock catches up
+    o.n_flip = st->n_flip;
+    o.n_null = st->n_null;
+    o.null_fx_lo = st->null_fx_lo;
+    o.null_fx_hi = st->null_fx_hi;
+    o.M = st->M;
+    o.B = st->B;
+    rec[r] = o;
+}
+
+__global__ void rec_series_kernel(const ObsRaw *rec, int n, int L, int d, double J, double H, spkmc_obs *out)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) out[r] = make_obs(rec[r], L, d, J, H);
+}
+
+int launch_rec_init(const LatticeState *st, ObsRaw *rec, int n, long long every, void *stream)
+{
+    rec_init_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(st, rec, n, every);
+    return to_status(cudaGetLastError());
+}
+
+int launch_rec_series(const ObsRaw *rec, int n, int L, int d, double J, double H, spkmc_obs *out, void *stream)
+{
+    rec_series_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(rec, n, L, d, J, H, out);
     return to_status(cudaGetLastError());
 }
 

@@ -247,7 +247,7 @@ int spkmc_observables_async(spkmc_t *h, spkmc_obs *host_out);
  * stay valid and unread until spkmc_synchronize returns.  EINVAL if every or
  * nrec is not positive, every * nrec exceeds 2^18 cycles or the lattice's
  * cycle budget, ENOMEM if the device buffers (nrec records of 64 and 128
- * bytes, kept for later calls) cannot be allocated. */
+ * bytes per slot, kept for later calls) cannot be allocated. */
 int spkmc_run_recorded(spkmc_t *h, int64_t every, int32_t nrec, spkmc_obs *host_out);
 /* A CUDA graph of `steps` steps of the lattice's stream work, each
  * cycles_per_step cycles (one persistent launch, as spkmc_run_cycles) and,
@@ -299,6 +299,12 @@ void spkmc_batch_destroy(spkmc_batch_t *b);
 int spkmc_batch_admit(spkmc_batch_t *b, const spkmc_params *p, int64_t cycles, int32_t *slot);
 /* Run up to `cycles` cycles; each lattice stops at its own budget. */
 int spkmc_batch_run(spkmc_batch_t *b, int64_t cycles);
+/* spkmc_run_recorded for every lattice of the batch in one launch:
+ * host_out[slot * nrec + r] (capacity * nrec records) after cycle
+ * (r + 1) * every of the run.  A lattice whose budget ends within the run
+ * keeps its final observables in the records after its last cycle; the
+ * records of slots that are not live are undefined. */
+int spkmc_batch_run_recorded(spkmc_batch_t *b, int64_t every, int32_t nrec, spkmc_obs *host_out);
 /* Synchronise and list slots whose budget is spent and that were not listed
  * before (at most cap); n receives the count. */
 int spkmc_batch_poll(spkmc_batch_t *b, int32_t *done_slots, int32_t cap, int32_t *n);

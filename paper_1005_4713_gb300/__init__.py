@@ -190,6 +190,14 @@ def spkmc_run_recorded(h, every: int, nrec: int, records) -> None:
                                     ctypes.cast(ctypes.addressof(records.records), ctypes.POINTER(spkmc_obs))))
 
 
+def spkmc_batch_run_recorded(b, every: int, nrec: int, records) -> None:
+    """Enqueue every * nrec cycles of all the batch's lattices in one launch,
+    with the observables after every `every` cycles into
+    records[slot * nrec + r] (an obs_buffer of capacity * nrec entries)."""
+    _check(lib().spkmc_batch_run_recorded(b, int(every), int(nrec),
+                                          ctypes.cast(ctypes.addressof(records.records), ctypes.POINTER(spkmc_obs))))
+
+
 def spkmc_graph_create(h, cycles_per_step: int, steps: int, host_obs=None) -> ctypes.c_void_p:
     g = ctypes.c_void_p()
     obs = ctypes.cast(host_obs, ctypes.POINTER(spkmc_obs)) if host_obs is not None else None
@@ -508,6 +516,18 @@ class Batch:
 
     def observables_all(self):
         return spkmc_batch_observables_all(self.b, self.capacity)
+
+    def run_recorded(self, every: int, nrec: int, records=None):
+        """every * nrec cycles in one launch with the observables after every
+        `every` cycles: records[slot * nrec + r] of an obs_buffer of
+        capacity * nrec entries (allocated if None; read it after
+        synchronize())."""
+        if records is None:
+            records = obs_buffer(self.capacity * nrec)
+        if len(records) < self.capacity * nrec:
+            raise ValueError("records holds fewer than capacity * nrec entries")
+        spkmc_batch_run_recorded(self.b, every, nrec, records)
+        return records
 
     def usage(self):
         return spkmc_batch_usage(self.b)

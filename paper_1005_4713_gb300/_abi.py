@@ -95,6 +95,7 @@ PROTOTYPES = {
     "spkmc_observables": (ctypes.c_int, [_h, P(spkmc_obs)]),
     "spkmc_observables_async": (ctypes.c_int, [_h, P(spkmc_obs)]),
     "spkmc_run_recorded": (ctypes.c_int, [_h, _i64, _i32, P(spkmc_obs)]),
+    "spkmc_batch_run_recorded": (ctypes.c_int, [_h, _i64, _i32, P(spkmc_obs)]),
     "spkmc_graph_create": (ctypes.c_int, [_h, ctypes.c_int64, ctypes.c_int32, P(spkmc_obs), P(ctypes.c_void_p)]),
     "spkmc_graph_launch": (ctypes.c_int, [ctypes.c_void_p]),
     "spkmc_graph_destroy": (None, [ctypes.c_void_p]),

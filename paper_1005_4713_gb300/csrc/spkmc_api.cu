@@ -95,6 +95,8 @@ void fill_physics(LatticeDesc &D, const spkmc_params *p, int d)
     host_bounds(d, D.rate, &D.rbound, &D.rmargin);
     D.rmode = p->rmax_mode;
     D.sub2 = p->sublattice == SPKMC_SUBLATTICE_2_RANDOM;
+    D.J = p->J;
+    D.H = p->H;
 }
 
 // R_max history of spkmc_state (cycles t-8 .. t-1) <-> the device ring.
@@ -244,6 +246,7 @@ struct spkmc_batch {
     int max_blocks_per_sm = 0;
     int last_grid = 0;
     int sticky_error = SPKMC_OK;
+    bool phase_unknown = false; // launches being captured for replays at other t % 4
     std::vector<Segment> uploaded_seg; // segment table currently on the device
     long long live_bytes = 0;
 
@@ -509,14 +512,15 @@ int admit(spkmc_batch *b, const spkmc_params *p, long long cycles, int slot_hint
 }
 
 // The flat table of the running lattices (those with cycles left), their
-// total active domains Q and the shared cycle parity (-1 if mixed), uploaded
+// total active domains Q and the shared cycle parity and t % 4 (-1 if mixed), uploaded
 // to the device if it changed (which synchronises the stream first: the
 // pinned staging copy is reused).
-int segment_table(spkmc_batch *b, std::vector<Segment> &segs, long long &Q, int &parity)
+int segment_table(spkmc_batch *b, std::vector<Segment> &segs, long long &Q, int &parity, int &phase4)
 {
     segs.clear();
     Q = 0;
     parity = -2;
+    phase4 = -2;
     for (int i = 0; i < b->capacity; ++i) {
         Slot &s = b->slots[i];
         if (!s.live || s.budget == 0) continue;
@@ -528,6 +532,8 @@ int segment_table(spkmc_batch *b, std::vector<Segment> &segs, long long &Q, int 
         Q += s.sz.Kact;
         const int par = (int)(s.t & 1);
         parity = parity == -2 ? par : (parity == par ? parity : -1);
+        const int ph = (int)(s.t & 3);
+        phase4 = phase4 == -2 ? ph : (phase4 == ph ? phase4 : -1);
     }
     const int nseg = (int)segs.size();
     if (nseg == 0) return SPKMC_OK;
@@ -565,8 +571,8 @@ int run(spkmc_batch *b, long long cycles, const RecReq *rq = nullptr)
         const long long n = std::min(cycles, kChunk);
         std::vector<Segment> segs;
         long long Q = 0;
-        int parity = -2;
-        int rc0 = segment_table(b, segs, Q, parity);
+        int parity = -2, phase4 = -2;
+        int rc0 = segment_table(b, segs, Q, parity, phase4);
         if (rc0) return rc0;
         const int nseg = (int)segs.size();
         if (nseg == 0) return SPKMC_OK;
@@ -602,6 +608,7 @@ int run(spkmc_batch *b, long long cycles, const RecReq *rq = nullptr)
         P.seg = b->d_seg;
         P.nseg = nseg;
         P.parity0 = parity < 0 ? -1 : parity;
+        P.phase4 = phase4 < 0 || b->phase_unknown ? -1 : phase4;
         P.Q = Q;
         P.ncycles = n;
         P.bar = b->d_bar;
@@ -757,6 +764,53 @@ int get_event_log(spkmc_batch *b, int slot, spkmc_event *buf, size_t cap, size_t
     return SPKMC_OK;
 }
 
+// Records of one lattice (slot >= 0) or of every slot (slot < 0) over a
+// run of every * nrec cycles in one launch; host_out[i * nrec + r] for the
+// i-th recorded slot.
+int run_recorded(spkmc_batch *b, int slot, long long every, int nrec, spkmc_obs *host_out)
+{
+    if (!host_out) return fail(SPKMC_EINVAL, "host_out is NULL");
+    if (every <= 0 || nrec <= 0) return fail(SPKMC_EINVAL, "every and nrec must be > 0");
+    if (every > kChunk / nrec)
+        return fail(SPKMC_EINVAL, "every * nrec must be <= %lld cycles (one launch)", kChunk);
+    if (b->sticky_error) return fail(b->sticky_error, "batch stopped after an earlier device error");
+    const long long total = every * (long long)nrec;
+    if (slot >= 0 && b->slots[slot].budget >= 0 && b->slots[slot].budget < total)
+        return fail(SPKMC_EINVAL, "the cycle budget is smaller than the run");
+    DeviceGuard g(b->device);
+    if (b->rec_cap < nrec) {
+        CUDA_TRY(cudaStreamSynchronize(b->stream), "stream synchronize"); // the old buffers may be in use
+        cudaFree(b->d_rec);
+        cudaFree(b->d_rec_obs);
+        b->d_rec = nullptr;
+        b->d_rec_obs = nullptr;
+        b->rec_cap = 0;
+        const size_t m = (size_t)nrec * b->capacity;
+        if (cudaMalloc(&b->d_rec, sizeof(ObsRaw) * m) != cudaSuccess ||
+            cudaMalloc(&b->d_rec_obs, sizeof(spkmc_obs) * m) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(b->d_rec);
+            b->d_rec = nullptr;
+            return fail(SPKMC_ENOMEM, "record buffers of %d records per lattice", nrec);
+        }
+        b->rec_cap = nrec;
+    }
+    const int first = slot >= 0 ? slot : 0, nslots = slot >= 0 ? 1 : b->capacity;
+    ObsRaw *rec = b->d_rec + (size_t)first * nrec;
+    if (launch_rec_init(b->d_state + first, rec, nslots, nrec, every, total, b->stream) != SPKMC_OK)
+        return cuda_fail(cudaGetLastError(), "record set-up");
+    const RecReq rq{b->d_rec, every, nrec};
+    int rc = run(b, total, &rq);
+    if (rc) return rc;
+    spkmc_obs *out = b->d_rec_obs + (size_t)first * nrec;
+    if (launch_rec_series(b->d_desc + first, rec, nslots, nrec, out, b->stream) != SPKMC_OK)
+        return cuda_fail(cudaGetLastError(), "record read-out");
+    CUDA_TRY(cudaMemcpyAsync(host_out, out, sizeof(spkmc_obs) * (size_t)nslots * nrec, cudaMemcpyDeviceToHost,
+                             b->stream),
+             "records copy");
+    return SPKMC_OK;
+}
+
 } // namespace
 
 extern "C" {
@@ -874,43 +928,8 @@ int spkmc_run_cycles(spkmc_t *h, int64_t ncycles)
 
 int spkmc_run_recorded(spkmc_t *h, int64_t every, int32_t nrec, spkmc_obs *host_out)
 {
-    if (!h || !host_out) return fail(SPKMC_EINVAL, "NULL argument");
-    if (every <= 0 || nrec <= 0) return fail(SPKMC_EINVAL, "every and nrec must be > 0");
-    if (every > kChunk / nrec)
-        return fail(SPKMC_EINVAL, "every * nrec must be <= %lld cycles (one launch)", kChunk);
-    spkmc_batch *b = h->b;
-    if (b->sticky_error) return fail(b->sticky_error, "batch stopped after an earlier device error");
-    const Slot &s = b->slots[h->slot];
-    const long long total = every * (long long)nrec;
-    if (s.budget >= 0 && s.budget < total) return fail(SPKMC_EINVAL, "the cycle budget is smaller than the run");
-    DeviceGuard g(b->device);
-    if (b->rec_cap < nrec) {
-        CUDA_TRY(cudaStreamSynchronize(b->stream), "stream synchronize"); // the old buffers may be in use
-        cudaFree(b->d_rec);
-        cudaFree(b->d_rec_obs);
-        b->d_rec = nullptr;
-        b->d_rec_obs = nullptr;
-        b->rec_cap = 0;
-        if (cudaMalloc(&b->d_rec, sizeof(ObsRaw) * (size_t)nrec * b->capacity) != cudaSuccess ||
-            cudaMalloc(&b->d_rec_obs, sizeof(spkmc_obs) * (size_t)nrec) != cudaSuccess) {
-            cudaGetLastError();
-            cudaFree(b->d_rec);
-            b->d_rec = nullptr;
-            return fail(SPKMC_ENOMEM, "record buffers of %d records", nrec);
-        }
-        b->rec_cap = nrec;
-    }
-    ObsRaw *rec = b->d_rec + (size_t)h->slot * nrec;
-    if (launch_rec_init(b->d_state + h->slot, rec, nrec, every, b->stream) != SPKMC_OK)
-        return cuda_fail(cudaGetLastError(), "record set-up");
-    const RecReq rq{b->d_rec, every, nrec};
-    int rc = run(b, total, &rq);
-    if (rc) return rc;
-    if (launch_rec_series(rec, nrec, s.params.L, s.d, s.params.J, s.params.H, b->d_rec_obs, b->stream) != SPKMC_OK)
-        return cuda_fail(cudaGetLastError(), "record read-out");
-    CUDA_TRY(cudaMemcpyAsync(host_out, b->d_rec_obs, sizeof(spkmc_obs) * nrec, cudaMemcpyDeviceToHost, b->stream),
-             "records copy");
-    return SPKMC_OK;
+    if (!h) return fail(SPKMC_EINVAL, "handle is NULL");
+    return run_recorded(h->b, h->slot, every, nrec, host_out);
 }
 
 int spkmc_synchronize(spkmc_t *h)
@@ -941,15 +960,18 @@ int spkmc_graph_create(spkmc_t *h, int64_t cycles_per_step, int32_t steps, spkmc
     if (rc) return rc;
     std::vector<Segment> segs;
     long long Q = 0;
-    int parity = -2;
-    if ((rc = segment_table(b, segs, Q, parity)) != SPKMC_OK) return rc; // uploads outside the capture
+    int parity = -2, phase4 = -2;
+    if ((rc = segment_table(b, segs, Q, parity, phase4)) != SPKMC_OK) return rc; // uploads outside the capture
     Slot &s = b->slots[h->slot];
     const long long t_saved = s.t, budget_saved = s.budget;
     CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    // a replay that does not advance t by a multiple of 4 cannot bake in t % 4
+    b->phase_unknown = (cycles_per_step * (long long)steps) % 4 != 0;
     for (int i = 0; i < steps && rc == SPKMC_OK; ++i) {
         rc = run(b, cycles_per_step);
         if (rc == SPKMC_OK && host_obs) rc = spkmc_observables_async(h, host_obs + i);
     }
+    b->phase_unknown = false;
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(b->stream, &graph);
     s.t = t_saved; // nothing ran yet
@@ -1192,6 +1214,12 @@ int spkmc_batch_run(spkmc_batch_t *b, int64_t cycles)
     return run(b, cycles);
 }
 
+int spkmc_batch_run_recorded(spkmc_batch_t *b, int64_t every, int32_t nrec, spkmc_obs *host_out)
+{
+    if (!b) return fail(SPKMC_EINVAL, "handle is NULL");
+    return run_recorded(b, -1, every, nrec, host_out);
+}
+
 int spkmc_batch_poll(spkmc_batch_t *b, int32_t *done_slots, int32_t cap, int32_t *n)
 {
     if (!b || !n || (cap > 0 && !done_slots)) return fail(SPKMC_EINVAL, "NULL argument");
@@ -1432,6 +1460,7 @@ extern "C" int spkmc_run_cycles_noalloc(const spkmc_params *p, int8_t *dev_spins
         P.seg = d_seg;
         P.nseg = 1;
         P.parity0 = (int)(t & 1);
+        P.phase4 = (int)(t & 3);
         P.Q = sz.Kact;
         P.ncycles = n;
         P.bar = d_bar;

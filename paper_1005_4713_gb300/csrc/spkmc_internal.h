@@ -48,6 +48,7 @@ struct LatticeDesc {
     int64_t log_cap;
     int64_t log_t0;
     double rate[kClasses];
+    double J, H;     // coupling and field, for the observables read-out
     double rbound;   // prescribed bound d^3 max r (1 + 2^-32) (Sec. 3.2 step 4b)
     double rmargin;  // growth of R_k between two visits of a colour, a + 12 b
     uint64_t seed;
@@ -114,6 +115,7 @@ struct LaunchParams {
     int exact_any;        // some lattice pads to the exact R_max: reduce before the events
     int sub2_any;         // some lattice uses two random colours: draw colours, recount
     int rec_n;            // records per lattice (rec_every > 0)
+    int phase4;           // t % 4 shared by all running lattices at launch, -1 if mixed or unknown
     int64_t rec_every;    // record after every rec_every cycles of the launch; 0 = none
     ObsRaw *rec;          // [slot][rec_n] records
 };
@@ -150,10 +152,13 @@ int launch_count_classes(const LatticeDesc &d, int mode, unsigned long long *mis
 // M and B (device int64 pair, accumulated).
 int launch_obs_record(const LatticeState *st, int L, int d, double J, double H, spkmc_obs *out, void *stream);
 int launch_observables(const LatticeDesc &d, long long *MB, void *stream);
-// Records of a launch: rec[r] = the state's sums, cycle t + (r + 1) every
-// (before the launch), and the observables of the filled records (after).
-int launch_rec_init(const LatticeState *st, ObsRaw *rec, int n, long long every, void *stream);
-int launch_rec_series(const ObsRaw *rec, int n, int L, int d, double J, double H, spkmc_obs *out, void *stream);
+// Records of a launch of `total` cycles for nslots lattices (st[i], desc[i],
+// rec[i * n + r]): before it, each record holds the state's sums and its
+// cycle; after it, the observables of the filled records.
+int launch_rec_init(const LatticeState *st, ObsRaw *rec, int nslots, int n, long long every, long long total,
+                    void *stream);
+int launch_rec_series(const LatticeDesc *desc, const ObsRaw *rec, int nslots, int n, spkmc_obs *out,
+                      void *stream);
 // Round size for a launch whose largest domain edge is d_max.
 int cycle_round_items(int d_max);
 

@@ -1567,8 +1567,17 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
         phase_b(P, S, stage, g, lo, hi, mbar_phase, early, line);
         if (!*reinterpret_cast<volatile int *>(&S.ok)) return;
         if (g + 1 < P.ncycles) {
+            // After an odd cycle t, colour t + 1 shares no block, count or
+            // ghost word with the flips of colour t (the colours differ in two
+            // or three parity bits), so its staging and step 1 may start at
+            // once.  Its flip step may still read spins of colour t (the
+            // lateral neighbour of a moved site, in a domain diagonal to
+            // both) when the colours differ in two bits (t = 1, 5 mod 8):
+            // there the exact R_max's barrier, which a CTA reaches only after
+            // its flips of cycle t, or this one must come first.
             const bool odd = P.parity0 >= 0 && (((long long)P.parity0 + g) & 1LL) == 1LL;
-            if (odd) {
+            const bool skip = odd && (P.exact_any || (P.phase4 >= 0 && (((long long)P.phase4 + g) & 3LL) == 3LL));
+            if (skip) {
                 __syncthreads();
             } else if (!grid_barrier(P, S, epoch)) {
                 return;
@@ -1580,7 +1589,7 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
             __syncthreads();
             const long long r = (g + 1) / P.rec_every - 1;
             for (int i = threadIdx.x; i < S.nsegc; i += blockDim.x) {
-                if (g >= S.seg_part[i]) continue;
+                // (a lattice whose budget ended earlier adds its final counters)
                 ObsRaw &o = P.rec[(long long)S.seg_slot[i] * P.rec_n + r];
                 if (S.seg_nflip[i]) atomicAdd(&o.n_flip, S.seg_nflip[i]);
                 if (S.seg_nnull[i]) atomicAdd(&o.n_null, S.seg_nnull[i]);
@@ -1591,7 +1600,17 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
         }
     }
     __syncthreads();
-    if (threadIdx.x == kThreads - 1) clock_catch_up(P, S, 0, lo, false); // the last cycle's step
+    if (threadIdx.x == kThreads - 1) {
+        clock_catch_up(P, S, 0, lo, false); // the last cycle's step
+        // records after the last cycle of a lattice whose budget ended
+        // within the launch hold its final clock
+        for (int i = 0; P.rec_every > 0 && i < S.nsegc; ++i) {
+            if (S.seg_base[i] < lo) continue; // another CTA keeps this clock
+            const double c = P.state[S.seg_slot[i]].clock;
+            for (long long r = S.seg_part[i] / P.rec_every; r < P.rec_n; ++r)
+                P.rec[(long long)S.seg_slot[i] * P.rec_n + r].clock = c;
+        }
+    }
     for (int i = threadIdx.x; i < S.nsegc; i += blockDim.x) {
         LatticeState &st = P.state[S.seg_slot[i]];
         if (S.seg_nflip[i]) atomicAdd(&st.n_flip, S.seg_nflip[i]);
@@ -1925,37 +1944,52 @@ int launch_obs_record(const LatticeState *st, int L, int d, double J, double H, 
     return to_status(cudaGetLastError());
 }
 
-__global__ void rec_init_kernel(const LatticeState *st, ObsRaw *rec, int n, long long every)
+// Record r of lattice i: cycle t + min((r + 1) every, the cycles the
+// lattice runs), the sums of the state; the clock is written by the launch
+// (NaN until then), or is the state's if the lattice does not run.
+__global__ void rec_init_kernel(const LatticeState *st, ObsRaw *rec, int nslots, int n, long long every,
+                                long long total)
 {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)nslots * n) return;
+    const LatticeState &s = st[idx / n];
+    const long long r = idx % n;
+    const long long part = s.budget < 0 ? total : (s.budget < total ? s.budget : total);
+    const long long done = (r + 1) * every < part ? (r + 1) * every : part;
     ObsRaw o;
-    o.t = st->t + (r + 1LL) * every;
-    o.clock = __longlong_as_double(0x7FF8000000000000LL); // NaN until the clock catches up
-    o.n_flip = st->n_flip;
-    o.n_null = st->n_null;
-    o.null_fx_lo = st->null_fx_lo;
-    o.null_fx_hi = st->null_fx_hi;
-    o.M = st->M;
-    o.B = st->B;
-    rec[r] = o;
+    o.t = s.t + done;
+    o.clock = part == 0 ? s.clock : __longlong_as_double(0x7FF8000000000000LL);
+    o.n_flip = s.n_flip;
+    o.n_null = s.n_null;
+    o.null_fx_lo = s.null_fx_lo;
+    o.null_fx_hi = s.null_fx_hi;
+    o.M = s.M;
+    o.B = s.B;
+    rec[idx] = o;
 }
 
-__global__ void rec_series_kernel(const ObsRaw *rec, int n, int L, int d, double J, double H, spkmc_obs *out)
+__global__ void rec_series_kernel(const LatticeDesc *desc, const ObsRaw *rec, int nslots, int n, spkmc_obs *out)
 {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < n) out[r] = make_obs(rec[r], L, d, J, H);
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)nslots * n) return;
+    const LatticeDesc &D = desc[idx / n];
+    out[idx] = make_obs(rec[idx], D.L, D.d, D.J, D.H);
 }
 
-int launch_rec_init(const LatticeState *st, ObsRaw *rec, int n, long long every, void *stream)
+int launch_rec_init(const LatticeState *st, ObsRaw *rec, int nslots, int n, long long every, long long total,
+                    void *stream)
 {
-    rec_init_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(st, rec, n, every);
+    const long long m = (long long)nslots * n;
+    rec_init_kernel<<<(unsigned)((m + 127) / 128), 128, 0, (cudaStream_t)stream>>>(st, rec, nslots, n, every,
+                                                                                    total);
     return to_status(cudaGetLastError());
 }
 
-int launch_rec_series(const ObsRaw *rec, int n, int L, int d, double J, double H, spkmc_obs *out, void *stream)
+int launch_rec_series(const LatticeDesc *desc, const ObsRaw *rec, int nslots, int n, spkmc_obs *out,
+                      void *stream)
 {
-    rec_series_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(rec, n, L, d, J, H, out);
+    const long long m = (long long)nslots * n;
+    rec_series_kernel<<<(unsigned)((m + 127) / 128), 128, 0, (cudaStream_t)stream>>>(desc, rec, nslots, n, out);
     return to_status(cudaGetLastError());
 }
 

@@ -2,14 +2,15 @@
 (Sec. 4 and Sec. 6 of arXiv:1005.4713).
 
 ``relax`` runs independent spkMC replicas (seeds seed0 + i) of one lattice in
-one batch and samples every replica after each chunk of cycles.  Its m(t)
-is on a grid of physical time t = clock / n_colours: every domain is active
-in one cycle out of n_colours (8 in rotation, or 2 on average with the two
-random colours), and the spkMC clock advances by the step of an active
-domain, so a domain has lived clock / n_colours when the clock reads
-``clock``.  Between samples m is interpolated linearly in time; the chunks
-are sized so that the clock advances by at most ``rel_step`` of its value
-per chunk.  The utilisation ratio UR of Eq. 10 over each grid interval is
+one batch and samples every replica after each chunk of cycles, recorded on
+the device: each launch runs ``records_per_launch`` chunks and records the
+observables after each.  Its m(t) is on a grid of physical time
+t = clock / n_colours: every domain is active in one cycle out of n_colours
+(8 in rotation, or 2 on average with the two random colours), and the spkMC
+clock advances by the step of an active domain, so a domain has lived
+clock / n_colours when the clock reads ``clock``.  Between samples m is
+interpolated linearly in time; the chunks are sized, launch by launch, so
+that the clock advances by at most ``rel_step`` of its value per chunk.  The utilisation ratio UR of Eq. 10 over each grid interval is
 estimated by the fraction of non-null events (its expectation in a cycle is
 sum_k R_k / (K R_max)).
 
@@ -30,7 +31,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import (Batch, SPKMC_RMAX_EXACT, SPKMC_SUBLATTICE_2_RANDOM, SPKMC_SUBLATTICE_8_ROTATING)
+from . import (Batch, SPKMC_RMAX_EXACT, SPKMC_SUBLATTICE_2_RANDOM, SPKMC_SUBLATTICE_8_ROTATING, obs_buffer)
 
 T_CRITICAL = 1.0 / 0.2216546  # J/k_B, Sec. 2 and Sec. 6
 BETA_OVER_NU = 0.515          # the ratio taken in Sec. 6
@@ -51,7 +52,7 @@ def _interp(clock, values, c):
 
 def relax(L, d, t_grid, n_runs=1, seed0=1, T=T_CRITICAL, J=1.0, H=0.0,
           sublattice=SPKMC_SUBLATTICE_8_ROTATING, rmax_mode=SPKMC_RMAX_EXACT, rel_step=0.02,
-          max_chunk=4096, config=None) -> Relaxation:
+          max_chunk=4096, records_per_launch=8, config=None) -> Relaxation:
     t_grid = np.asarray(t_grid, dtype=np.float64)
     if t_grid.ndim != 1 or len(t_grid) == 0 or np.any(np.diff(t_grid) <= 0) or t_grid[0] <= 0:
         raise ValueError("t_grid must be positive and increasing")
@@ -68,21 +69,27 @@ def relax(L, d, t_grid, n_runs=1, seed0=1, T=T_CRITICAL, J=1.0, H=0.0,
         nulls = [[0] for _ in slots]
         done_cycles = 0
         chunk = 1
+        nrec = records_per_launch
+        rec = obs_buffer(n_runs * nrec)
         while min(c[-1] for c in clock) < c_end:
-            b.run(chunk)
-            done_cycles += chunk
-            obs = b.observables_all()
+            start = [c[-1] for c in clock]
+            b.run_recorded(chunk, nrec, rec)
+            b.synchronize()
+            done_cycles += chunk * nrec
             adv = 0.0
             for i, sl in enumerate(slots):
-                o = obs[sl]
-                adv = max(adv, (o.clock - clock[i][-1]) / chunk)
-                clock[i].append(o.clock)
-                mag[i].append(o.M / N)
-                flips[i].append(o.n_flip)
-                nulls[i].append(o.n_null)
+                for r in range(nrec):
+                    o = rec[sl * nrec + r]
+                    clock[i].append(o.clock)
+                    mag[i].append(o.M / N)
+                    flips[i].append(o.n_flip)
+                    nulls[i].append(o.n_null)
+                adv = max(adv, (clock[i][-1] - start[i]) / (chunk * nrec))
             now = min(c[-1] for c in clock)
             if adv > 0 and math.isfinite(adv):
                 chunk = int(max(1, min(max_chunk, rel_step * max(now, c_first) / adv)))
+                # near the end, no more chunks than the clock still needs
+                nrec = int(max(1, min(records_per_launch, math.ceil((c_end - now) / (adv * chunk)))))
     m = np.empty((n_runs, len(t_grid)))
     ur = np.empty((n_runs, len(t_grid)))
     cg = t_grid * ncol

@@ -130,3 +130,37 @@ def test_recorded_arguments_are_checked():
         lat.run_recorded(2, 40, big)
         lat.synchronize()
         assert [big[i].cycle for i in (0, 39)] == [4, 82]
+
+
+def test_batch_records_equal_solo_read_outs():
+    """A batch of uneven lattices (edges, bounds, colours, one budget ending
+    within the run) recorded in one launch: each record equals the read-out
+    of the same lattice run alone to that cycle (or to its last cycle)."""
+    every, nrec = 5, 4
+    specs = [
+        (wl.LatticeSpec(L=32, d=4, seed=51), sp.SPKMC_RMAX_EXACT, sp.SPKMC_SUBLATTICE_8_ROTATING, -1),
+        (wl.LatticeSpec(L=64, d=16, seed=52, H=0.02), sp.SPKMC_RMAX_LEARNED, sp.SPKMC_SUBLATTICE_8_ROTATING, -1),
+        (wl.LatticeSpec(L=16, d=2, seed=53, T=3.0), sp.SPKMC_RMAX_PRESCRIBED, sp.SPKMC_SUBLATTICE_8_ROTATING, 13),
+        (wl.LatticeSpec(L=48, d=8, seed=54), sp.SPKMC_RMAX_EXACT, sp.SPKMC_SUBLATTICE_2_RANDOM, 10),
+    ]
+    b = sp.Batch(len(specs))
+    try:
+        slots = [b.admit(s.L, s.d, s.J, s.H, s.T, s.seed, cold=s.cold, cycles=budget, rmax_mode=mode,
+                         sublattice=sub) for s, mode, sub, budget in specs]
+        b.run(3)  # records start after a few cycles (t = 3, an odd cycle)
+        rec = b.run_recorded(every, nrec)
+        b.synchronize()
+        for slot, (s, mode, sub, budget) in zip(slots, specs):
+            part = every * nrec if budget < 0 else min(budget - 3, every * nrec)
+            with gpu_lattice(s, mode, sub) as a:
+                a.run(3)
+                done = 0
+                for r in range(nrec):
+                    upto = min((r + 1) * every, part)
+                    if upto > done:
+                        a.run(upto - done)
+                        done = upto
+                    assert_equal_obs(rec[slot * nrec + r], a.observables())
+                assert np.array_equal(b.spins(slot), a.spins())
+    finally:
+        b.close()

@@ -1525,7 +1525,10 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
                 S.early_bytes = (int)total;
                 if (total) mbar_expect_tx(&S.mbar, total);
             }
-            const long long q = lo + threadIdx.x;
+            // item i is requested by thread (i + 128) mod 256: with up to 128
+            // items the upper warps issue the copies while the lower ones,
+            // which hold the items in step 1, already load the count lines
+            const long long q = lo + ((threadIdx.x + kThreads / 2) & (kThreads - 1));
             if (q < hi) {
                 const int ls = find_segment(S, q);
                 if (g < S.seg_part[ls]) {

@@ -452,32 +452,43 @@ def run_gpu(args, world, rank, local, pg):
                  "note": "the per-step launches captured in one CUDA graph (cycles + observables per step)"}
 
     # end to end through the C ABI with host buffers: upload the start
-    # lattice from pinned memory, run the steps with observables, read the
-    # final lattice back
+    # lattice from pinned memory (one bit per site), run the steps with their
+    # recorded observables, read the final lattice back (one bit per site);
+    # the same with one int8 per site is reported beside it
     e2e = None
     if not args.no_e2e:
         n = L_BENCH ** 3
+        obs_bytes = ctypes.sizeof(sp.spkmc_obs)
+        lat2 = sp.Lattice(L_BENCH, D_BENCH, 1.0, 0.0, 4.5115, seed, cold=True, config=cfg)
+
+        def timed(upload, download, host, out):
+            upload(host)
+            lat2.run(cps)
+            lat2.observables()
+            barrier(pg, device)
+            torch.cuda.synchronize(device)
+            t0 = time.perf_counter()
+            upload(host)
+            lat2.run_recorded(cps, args.steps, obs_rec)
+            download(out)  # synchronises: the records have landed
+            t1 = time.perf_counter()
+            barrier(pg, device)
+            return max_over_ranks(t1 - t0, pg, device)
+
+        bits = torch.empty(n // 8, dtype=torch.uint8, pin_memory=True).numpy()
+        lat.spins_packed(bits)
+        bits_out = torch.empty(n // 8, dtype=torch.uint8, pin_memory=True).numpy()
+        s_bits = timed(lat2.set_spins_packed, lat2.spins_packed, bits, bits_out)
         host = torch.empty(n, dtype=torch.int8, pin_memory=True).numpy()
-        lat.spins()  # warm the read path
         host[:] = lat.spins()
         out = torch.empty(n, dtype=torch.int8, pin_memory=True).numpy()
-        lat2 = sp.Lattice(L_BENCH, D_BENCH, 1.0, 0.0, 4.5115, seed, cold=True, config=cfg)
-        lat2.set_spins(host)
-        lat2.run(cps)
-        lat2.observables()
-        barrier(pg, device)
-        torch.cuda.synchronize(device)
-        t0 = time.perf_counter()
-        lat2.set_spins(host)
-        lat2.run_recorded(cps, args.steps, obs_rec)
-        sp.spkmc_get_spins(lat2.h, out)  # synchronises: the records have landed
-        t1 = time.perf_counter()
-        barrier(pg, device)
-        e2e_s = max_over_ranks(t1 - t0, pg, device)
-        obs_bytes = ctypes.sizeof(sp.spkmc_obs)
-        e2e = {"value": events / e2e_s, "unit": "events/s",
-               "h2d_bytes_per_step": n // args.steps,
-               "d2h_bytes_per_step": n // args.steps + obs_bytes}
+        s_int8 = timed(lat2.set_spins, lambda o: sp.spkmc_get_spins(lat2.h, o), host, out)
+        e2e = {"value": events / s_bits, "unit": "events/s",
+               "h2d_bytes_per_step": n // 8 // args.steps,
+               "d2h_bytes_per_step": n // 8 // args.steps + obs_bytes,
+               "spins": "one bit per site (spkmc_set_spins_packed / spkmc_get_spins_packed)",
+               "int8_spins": {"value": events / s_int8, "h2d_bytes_per_step": n // args.steps,
+                              "d2h_bytes_per_step": n // args.steps + obs_bytes}}
         lat2.close()
 
     cpu = None

@@ -271,6 +271,12 @@ void spkmc_graph_destroy(spkmc_graph_t *g);
  * checkpoint with set_spins first, then set_state. */
 int spkmc_get_spins(spkmc_t *h, int8_t *host_buf, size_t n);
 int spkmc_set_spins(spkmc_t *h, const int8_t *host_buf, size_t n);
+/* The same spins packed one bit per site: bit (i mod 8) of byte i / 8 is site
+ * i = x + L (y + L z) of the global order above, 1 for +1 and 0 for -1;
+ * nbytes = L^3 / 8 (an eighth of the int8 transfer), else EINVAL.  set has
+ * the effects of spkmc_set_spins. */
+int spkmc_get_spins_packed(spkmc_t *h, uint8_t *host_bits, size_t nbytes);
+int spkmc_set_spins_packed(spkmc_t *h, const uint8_t *host_bits, size_t nbytes);
 /* Copy up to cap logged events (cycle-major, ascending k within a cycle);
  * n_out receives the number copied.  The log holds the first
  * event_log_capacity events after create or spkmc_clear_event_log. */

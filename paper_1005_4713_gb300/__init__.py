@@ -273,6 +273,19 @@ def spkmc_set_spins(h, spins: np.ndarray) -> None:
     _check(lib().spkmc_set_spins(h, s.ctypes.data, s.size))
 
 
+def spkmc_get_spins_packed(h, out: np.ndarray) -> np.ndarray:
+    """Spins as bits (np.packbits(spins > 0, bitorder='little') of the int8
+    read-out) into a uint8 array of L^3 / 8 bytes."""
+    assert out.dtype == np.uint8 and out.flags.c_contiguous
+    _check(lib().spkmc_get_spins_packed(h, out.ctypes.data, out.size))
+    return out
+
+
+def spkmc_set_spins_packed(h, bits: np.ndarray) -> None:
+    b = np.ascontiguousarray(bits, dtype=np.uint8)
+    _check(lib().spkmc_set_spins_packed(h, b.ctypes.data, b.size))
+
+
 def spkmc_get_event_log(h, cap: int) -> np.ndarray:
     buf = np.zeros(max(int(cap), 0), dtype=EVENT_DTYPE)
     n = ctypes.c_size_t()
@@ -437,6 +450,14 @@ class Lattice:
 
     def set_spins(self, s) -> None:
         spkmc_set_spins(self.h, s)
+
+    def spins_packed(self, out=None) -> np.ndarray:
+        """The spins as L^3 / 8 bytes, one bit per site (1 = +1), little-endian
+        bit order within a byte."""
+        return spkmc_get_spins_packed(self.h, np.empty(self.L ** 3 // 8, dtype=np.uint8) if out is None else out)
+
+    def set_spins_packed(self, bits) -> None:
+        spkmc_set_spins_packed(self.h, bits)
 
     def event_log(self, cap=None) -> np.ndarray:
         return spkmc_get_event_log(self.h, self.params.event_log_capacity if cap is None else cap)

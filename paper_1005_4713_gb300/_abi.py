@@ -101,6 +101,8 @@ PROTOTYPES = {
     "spkmc_graph_destroy": (None, [ctypes.c_void_p]),
     "spkmc_get_spins": (ctypes.c_int, [_h, ctypes.c_void_p, _sz]),
     "spkmc_set_spins": (ctypes.c_int, [_h, ctypes.c_void_p, _sz]),
+    "spkmc_get_spins_packed": (ctypes.c_int, [_h, ctypes.c_void_p, _sz]),
+    "spkmc_set_spins_packed": (ctypes.c_int, [_h, ctypes.c_void_p, _sz]),
     "spkmc_get_event_log": (ctypes.c_int, [_h, ctypes.c_void_p, _sz, P(_sz)]),
     "spkmc_clear_event_log": (ctypes.c_int, [_h]),
     "spkmc_get_state": (ctypes.c_int, [_h, P(spkmc_state)]),

@@ -694,18 +694,21 @@ int observables(spkmc_batch *b, int slot, spkmc_obs *out)
     return SPKMC_OK;
 }
 
-int get_spins(spkmc_batch *b, int slot, int8_t *host, size_t n)
+// Spins to the host: one int8 per site, or (packed) one bit per site.
+int get_spins(spkmc_batch *b, int slot, void *host, size_t n, bool packed = false)
 {
     int rc = slot_check(b, slot);
     if (rc) return rc;
     const Slot &s = b->slots[slot];
-    const size_t N = (size_t)s.params.L * s.params.L * s.params.L;
-    if (!host || n != N) return fail(SPKMC_EINVAL, "host buffer must hold L^3 = %zu int8", N);
+    const size_t sites = (size_t)s.params.L * s.params.L * s.params.L, N = packed ? sites / 8 : sites;
+    if (!host || n != N)
+        return fail(SPKMC_EINVAL, packed ? "host buffer must hold L^3 / 8 = %zu bytes" : "host buffer must hold L^3 = %zu int8", N);
     DeviceGuard g(b->device);
     if ((rc = sync_and_check(b)) != SPKMC_OK) return rc;
-    int8_t *tmp = (int8_t *)b->dev_alloc(N);
+    void *tmp = b->dev_alloc(N);
     if (!tmp) return fail(SPKMC_ENOMEM, "device allocation of %zu bytes failed", N);
-    rc = launch_unpack_rows(s.desc, tmp, b->stream);
+    rc = packed ? launch_unpack_bits(s.desc, (uint8_t *)tmp, b->stream)
+                : launch_unpack_rows(s.desc, (int8_t *)tmp, b->stream);
     cudaError_t e = rc ? cudaGetLastError()
                        : cudaMemcpyAsync(host, tmp, N, cudaMemcpyDeviceToHost, b->stream);
     cudaError_t e2 = cudaStreamSynchronize(b->stream);
@@ -715,22 +718,24 @@ int get_spins(spkmc_batch *b, int slot, int8_t *host, size_t n)
     return SPKMC_OK;
 }
 
-int set_spins(spkmc_batch *b, int slot, const int8_t *host, size_t n)
+int set_spins(spkmc_batch *b, int slot, const void *host, size_t n, bool packed = false)
 {
     int rc = slot_check(b, slot);
     if (rc) return rc;
     const Slot &s = b->slots[slot];
-    const size_t N = (size_t)s.params.L * s.params.L * s.params.L;
-    if (!host || n != N) return fail(SPKMC_EINVAL, "host buffer must hold L^3 = %zu int8", N);
+    const size_t sites = (size_t)s.params.L * s.params.L * s.params.L, N = packed ? sites / 8 : sites;
+    if (!host || n != N)
+        return fail(SPKMC_EINVAL, packed ? "host buffer must hold L^3 / 8 = %zu bytes" : "host buffer must hold L^3 = %zu int8", N);
     DeviceGuard g(b->device);
     if ((rc = sync_and_check(b)) != SPKMC_OK) return rc;
-    int8_t *tmp = (int8_t *)b->dev_alloc(N);
+    void *tmp = b->dev_alloc(N);
     if (!tmp) return fail(SPKMC_ENOMEM, "device allocation of %zu bytes failed", N);
     cudaError_t e = cudaMemcpyAsync(tmp, host, N, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) // the R_max history described the old spins
         e = cudaMemsetAsync(b->d_state[slot].rmax, 0, sizeof(b->d_state[slot].rmax), b->stream);
     if (e == cudaSuccess) {
-        rc = launch_pack_rows(s.desc, tmp, b->stream);
+        rc = packed ? launch_pack_bits(s.desc, (const uint8_t *)tmp, b->stream)
+                    : launch_pack_rows(s.desc, (const int8_t *)tmp, b->stream);
         if (!rc) rc = refresh_derived(b, s.desc);
         if (!rc) rc = recompute_MB(b, slot);
         if (rc) e = cudaGetLastError();
@@ -1053,6 +1058,18 @@ int spkmc_set_spins(spkmc_t *h, const int8_t *host_buf, size_t n)
 {
     if (!h) return fail(SPKMC_EINVAL, "handle is NULL");
     return set_spins(h->b, h->slot, host_buf, n);
+}
+
+int spkmc_get_spins_packed(spkmc_t *h, uint8_t *host_bits, size_t nbytes)
+{
+    if (!h) return fail(SPKMC_EINVAL, "handle is NULL");
+    return get_spins(h->b, h->slot, host_bits, nbytes, true);
+}
+
+int spkmc_set_spins_packed(spkmc_t *h, const uint8_t *host_bits, size_t nbytes)
+{
+    if (!h) return fail(SPKMC_EINVAL, "handle is NULL");
+    return set_spins(h->b, h->slot, host_bits, nbytes, true);
 }
 
 int spkmc_get_event_log(spkmc_t *h, spkmc_event *buf, size_t cap, size_t *n_out)

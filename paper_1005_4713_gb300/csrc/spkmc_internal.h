@@ -142,6 +142,9 @@ int launch_cycles(const LaunchParams &p, int grid, void *stream, bool cooperativ
 int launch_init_rows(const LatticeDesc &d, int init, void *stream);
 int launch_pack_rows(const LatticeDesc &d, const int8_t *dev_spins, void *stream);
 int launch_unpack_rows(const LatticeDesc &d, int8_t *dev_spins, void *stream);
+// The same with one bit per site (bit i mod 8 of byte i / 8, 1 for +1).
+int launch_pack_bits(const LatticeDesc &d, const uint8_t *dev_bits, void *stream);
+int launch_unpack_bits(const LatticeDesc &d, uint8_t *dev_bits, void *stream);
 // mode 0: rebuild every domain's ghost faces from its neighbours' rows;
 // mode 1: compare and add the number of stale ghost words to *mismatch.
 int launch_ghosts(const LatticeDesc &d, int mode, unsigned long long *mismatch, void *stream);

@@ -1693,6 +1693,59 @@ __global__ void unpack_rows_kernel(LatticeDesc Ld, int8_t *s8)
     }
 }
 
+// Rows from global spins packed one bit per site (bit i mod 8 of byte i / 8
+// is site i in global order, 1 for +1).
+template <int D>
+__global__ void pack_bits_kernel(LatticeDesc Ld, const uint8_t *bits)
+{
+    const long long nrows = Ld.K * (D * D);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nrows;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long k = i / (D * D);
+        const int r = (int)(i % (D * D));
+        const long long g0 = first_site_of_row<D>(Ld, k, r);
+        uint32_t row = 0;
+        if constexpr (D >= 8) { // L and x0 are multiples of 8: the row is D / 8 whole bytes
+            row = bits[g0 >> 3];
+            if constexpr (D == 16) row |= (uint32_t)bits[(g0 >> 3) + 1] << 8;
+        } else {
+            for (int x = 0; x < D; ++x) row |= (uint32_t)((bits[(g0 + x) >> 3] >> ((g0 + x) & 7)) & 1) << x;
+        }
+        block_of<D>(Ld, k)[r] = (uint16_t)row;
+    }
+}
+
+// Global spins packed one bit per site from the rows: one thread per byte
+// (8 consecutive sites in global order, which may span domains and lines).
+template <int D>
+__global__ void unpack_bits_kernel(LatticeDesc Ld, uint8_t *bits)
+{
+    const long long L = Ld.L, nbytes = L * L * L / 8;
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nbytes;
+         b += (long long)gridDim.x * blockDim.x) {
+        const long long site = 8 * b;
+        int X = (int)(site % L), Y = (int)((site / L) % L), Z = (int)(site / (L * L));
+        if constexpr (D >= 8) { // L is a multiple of 8: the byte is 8 bits of one row
+            const long long k = domain_index(Ld.nd, X / D, Y / D, Z / D);
+            bits[b] = (uint8_t)(block_of<D>(Ld, k)[(Y % D) + D * (Z % D)] >> (X % D));
+            continue;
+        }
+        uint32_t v = 0;
+        for (int j = 0; j < 8; ++j) {
+            const long long k = domain_index(Ld.nd, X / D, Y / D, Z / D);
+            v |= (uint32_t)((block_of<D>(Ld, k)[(Y % D) + D * (Z % D)] >> (X % D)) & 1u) << j;
+            if (++X == Ld.L) { // the next site in global order
+                X = 0;
+                if (++Y == Ld.L) {
+                    Y = 0;
+                    ++Z;
+                }
+            }
+        }
+        bits[b] = (uint8_t)v;
+    }
+}
+
 // The ghost word (face f, index i) of domain k as the neighbours' rows define it.
 template <int D>
 __device__ __forceinline__ uint32_t ghost_word(const LatticeDesc &Ld, long long k, int f, int i)
@@ -1891,6 +1944,21 @@ int launch_unpack_rows(const LatticeDesc &d, int8_t *dev_spins, void *stream)
 {
     const int grid = simple_grid(d.K * d.d * d.d, 256);
     SPKMC_DISPATCH_D(d.d, unpack_rows_kernel, grid, 256, (cudaStream_t)stream, d, dev_spins);
+    return to_status(cudaGetLastError());
+}
+
+int launch_pack_bits(const LatticeDesc &d, const uint8_t *dev_bits, void *stream)
+{
+    const int grid = simple_grid(d.K * d.d * d.d, 256);
+    SPKMC_DISPATCH_D(d.d, pack_bits_kernel, grid, 256, (cudaStream_t)stream, d, dev_bits);
+    return to_status(cudaGetLastError());
+}
+
+int launch_unpack_bits(const LatticeDesc &d, uint8_t *dev_bits, void *stream)
+{
+    const long long L = d.L;
+    const int grid = simple_grid(L * L * L / 8, 256);
+    SPKMC_DISPATCH_D(d.d, unpack_bits_kernel, grid, 256, (cudaStream_t)stream, d, dev_bits);
     return to_status(cudaGetLastError());
 }
 

@@ -314,3 +314,36 @@ def test_graph_arguments_are_checked():
         with pytest.raises(sp.SpkmcError) as e:
             sp.spkmc_graph_create(lat.h, 2, 2, ctypes.addressof(pageable))
         assert e.value.code == sp.SPKMC_EINVAL
+
+
+@pytest.mark.parametrize("spec", [
+    wl.LatticeSpec(L=4, d=2, seed=61),    # L^3 / 8 bytes cross x-lines
+    wl.LatticeSpec(L=12, d=2, seed=62),   # L not a multiple of 8
+    wl.LatticeSpec(L=24, d=4, seed=63),
+    wl.LatticeSpec(L=48, d=8, seed=64),
+    wl.LatticeSpec(L=96, d=16, seed=65),
+])
+def test_packed_spins_round_trip(spec):
+    """One bit per site in global order, little-endian within a byte: the
+    packed read-out equals np.packbits of the int8 one, and writing packed
+    spins has the effect of writing the same spins as int8."""
+    with gpu_lattice(spec) as a, gpu_lattice(spec) as b:
+        a.run(13)
+        s = a.spins()
+        bits = a.spins_packed()
+        assert bits.size == spec.L ** 3 // 8
+        assert np.array_equal(bits, np.packbits(s > 0, bitorder="little"))
+        rng = np.random.default_rng(spec.seed)
+        new = np.where(rng.random(spec.L ** 3) < 0.3, 1, -1).astype(np.int8)
+        a.set_spins_packed(np.packbits(new > 0, bitorder="little"))
+        b.set_spins(new)
+        assert np.array_equal(a.spins(), new)
+        assert a.check_counts() == 0
+        oa, ob = a.observables(), b.observables()
+        assert (oa.M, oa.B) == (ob.M, ob.B)
+        a.set_state(b.state())
+        a.run(9)
+        b.run(9)
+        assert np.array_equal(a.spins(), b.spins())
+        with pytest.raises(sp.SpkmcError):
+            a.set_spins_packed(np.zeros(spec.L ** 3 // 8 + 1, dtype=np.uint8))

@@ -557,11 +557,14 @@ __device__ void phase_a(const LaunchParams &P, CtaShared &S, unsigned char *stag
                                                (uint32_t)n1.x, (uint32_t)n1.y, (uint32_t)n1.z, (uint32_t)n1.w,
                                                (uint32_t)n2.x, (uint32_t)n2.y, (uint32_t)n2.z, (uint32_t)n2.w,
                                                (uint32_t)n3.x, (uint32_t)n3.y};
-                // the products fl(n_c r_c) come from the lattice's table
+                // the products fl(n_c r_c) come from the lattice's table (a
+                // count is at most d^3; the clamp keeps the read in the table
+                // whatever the words hold)
                 const int tstride = Ld.d * Ld.d * Ld.d + 1;
                 double prod[kClasses];
 #pragma unroll
-                for (int c = 0; c < kClasses; ++c) prod[c] = __ldg(Ld.nrate + c * tstride + (cw[c] & 0xFFFFu));
+                for (int c = 0; c < kClasses; ++c)
+                    prod[c] = __ldg(Ld.nrate + c * tstride + min(cw[c] & 0xFFFFu, (uint32_t)(tstride - 1)));
                 double cum[kClasses];
                 double acc = prod[0];
                 cum[0] = acc;

@@ -218,3 +218,17 @@ def test_noalloc_entry_point_with_learned_bound():
     assert (state.cycle, state.n_flip, state.n_null) == (st.cycle, st.n_flip, st.n_null)
     assert math.isclose(state.clock, st.clock, rel_tol=CLOCK_RTOL)
     assert list(state.rmax_hist) == list(st.rmax_hist)
+
+
+@pytest.mark.parametrize("mode", MODES + [sp.SPKMC_RMAX_EXACT])
+@pytest.mark.parametrize("L,d,cycles", [(1024, 16, 2000), (256, 16, 20000), (128, 8, 20000), (64, 4, 20000)])
+def test_long_runs_keep_counts_consistent(mode, L, d, cycles):
+    """Long runs in launches of many cycles (where CTAs drift apart most
+    across the cycles without a grid barrier): the class counts, ghost faces,
+    M and B kept flip by flip still equal a recount from the spins."""
+    spec = wl.LatticeSpec(L=L, d=d, seed=71)
+    with gpu_lattice(spec, mode) as lat:
+        lat.run(cycles)
+        assert lat.check_counts() == 0
+        o = lat.observables()
+        assert o.cycle == cycles and o.n_flip + o.n_null == cycles * lat.K_act

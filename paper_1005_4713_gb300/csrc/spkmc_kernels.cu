@@ -747,6 +747,23 @@ __device__ __forceinline__ void class_bits(const WorkItem &w, const unsigned cha
     }
 }
 
+// Position of the n-th set bit (from 0, in ascending order) of a word that
+// has more than n set bits: a binary search on bit counts of halves.
+__device__ __forceinline__ int nth_set_bit(uint32_t b, int n)
+{
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const int c = __popc(b & ((1u << w) - 1u));
+        if (n >= c) {
+            n -= c;
+            b >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
 // Rank the sites of class w.cls in the half w.half of the domain in
 // ascending local index and return the w.j-th (-1 if the half has fewer),
 // cooperatively in the octet that holds `lane`.  Every lane of the warp
@@ -780,11 +797,7 @@ __device__ __forceinline__ int select_site(const WorkItem &w, const unsigned cha
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int pc = __popc(cb.m[i]);
-            if (jj >= 0 && jj < pc) {
-                uint32_t bits = cb.m[i];
-                for (int r = 0; r < jj; ++r) bits &= bits - 1;
-                site = cb.base + i * cb.stride + (__ffs(bits) - 1) + cb.offset;
-            }
+            if (jj >= 0 && jj < pc) site = cb.base + i * cb.stride + nth_set_bit(cb.m[i], jj) + cb.offset;
             jj -= pc;
         }
     }

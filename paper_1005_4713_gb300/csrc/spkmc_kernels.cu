@@ -1,28 +1,38 @@
 // spkmc_kernels.cu -- sm_103a kernels of the spkMC cycle (arXiv:1005.4713,
 // Sec. 3.1 steps 1-6 with the chessboard sublattice of Sec. 3.2).
 //
-// One persistent cooperative launch runs many cycles.  Per cycle:
-//   phase A (step 1)    one lane per active domain reads the domain's 14 class
-//                       counts, builds the cumulative frequency line in FP64
-//                       (class order, no fused multiply-add), draws its Philox
-//                       block and keeps the line in scratch; partial maxima
-//                       go to shared memory, then one atomicMax per CTA and
-//                       lattice;
-//   grid barrier        (step 2: R_max is known everywhere);
+// One persistent cooperative launch runs many cycles over the active domains
+// of one or many lattices (a flat table of items, split evenly over the
+// CTAs).  Per cycle:
+//   staging             a CTA whose domains fit its staging area requests
+//                       their blocks (bit-packed rows and one-site halo, 704
+//                       bytes at d = 16) at once, one bulk copy each, from the
+//                       upper warps; the copies land during steps 1-2;
+//   recount             (two random colours only) the class counts of every
+//                       active domain, recounted from its staged block;
+//   phase A (step 1)    one lane per active domain reads its 14 class count
+//                       words, looks up the products fl(n_c r_c) and sums the
+//                       cumulative frequency line in FP64 in class order (no
+//                       fused multiply-add); the line stays in registers, or
+//                       goes to scratch for CTAs that stage in rounds; partial
+//                       maxima go to shared memory, then one atomicMax per CTA
+//                       and lattice;
+//   grid barrier        (step 2: R_max is known everywhere) -- only when some
+//                       lattice pads to the exact R_max; the bounds of
+//                       Sec. 3.2 step 4b need none;
 //   phase B (steps 3-6) one lane per domain finds its event on the line
-//                       padded by the null rate R_max - R_k; the blocks of the
-//                       domains that flip (rows and one-site halo, 704 bytes
-//                       at d = 16) are staged into shared memory by bulk
-//                       copies on the TMA engine; one warp per domain ranks
-//                       the sites of the chosen class with a bit-sliced adder,
-//                       popc and a warp scan; one thread per domain flips the
-//                       site, moves the class counts of the site and of its 6
-//                       neighbours and refreshes the neighbours' ghost faces;
+//                       padded by the null rate R - R_k and splits the site's
+//                       rank into a half of the domain and a rank there; one
+//                       octet of lanes per domain classifies the chosen half
+//                       with a bit-sliced adder and picks the site by popc, an
+//                       octet scan and a bit search; one thread per domain
+//                       flips the site, moves the class counts of the site
+//                       and of its 6 neighbours and refreshes the neighbours'
+//                       ghost faces;
 //   grid barrier        (step 6: the flips are visible) -- skipped after an
-//                       odd cycle, whose flips never touch the data that the
-//                       next colour reads.
-// The clock (step 5) is advanced once per cycle by the lane that owns the
-// lattice's first active domain.
+//                       odd cycle t when that is safe (see the loop).
+// The clock (step 5) of a lattice is advanced one cycle behind by the last
+// thread of the CTA that holds the lattice's first active domain.
 #include <cuda_runtime.h>
 
 #include <cstdint>

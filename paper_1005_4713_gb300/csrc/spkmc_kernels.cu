@@ -46,6 +46,7 @@ namespace {
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kDescCached = 4; // lattice descriptors a CTA keeps in shared memory
 
 // ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11), the counter-based
@@ -302,6 +303,7 @@ struct CtaShared {
     double seg_rnow[kMaxSegPerCta];   // R_max of the running cycle
     int seg_tick[kMaxSegPerCta];      // the clock of this lattice moves in this round
     int seg_slot[kMaxSegPerCta];
+    LatticeDesc descc[kDescCached]; // descriptors of the CTA's first lattices
     unsigned long long mbar;
     int nsegc;
     int nwork;
@@ -327,6 +329,17 @@ __device__ __forceinline__ int find_segment(const CtaShared &S, long long q)
         else hi = mid - 1;
     }
     return lo;
+}
+
+static_assert(sizeof(LatticeDesc) % 8 == 0, "the descriptor is copied in 8-byte words");
+
+// Descriptor of local segment ls: a shared-memory copy for the CTA's first
+// kDescCached lattices (the fields are read in every phase, and the L1 copy
+// of the global one does not survive the product-table lookups), else the
+// global one.
+__device__ __forceinline__ const LatticeDesc &seg_desc(const LaunchParams &P, const CtaShared &S, int ls)
+{
+    return ls < kDescCached ? S.descc[ls] : P.desc[S.seg_slot[ls]];
 }
 
 // Grid-wide barrier on a monotone arrival counter.  Waits at most
@@ -549,7 +562,7 @@ __device__ void phase_a(const LaunchParams &P, CtaShared &S, unsigned char *stag
         if (q < hi) {
             ls = find_segment(S, q);
             if (g < S.seg_part[ls]) {
-                const LatticeDesc &Ld = P.desc[S.seg_slot[ls]];
+                const LatticeDesc &Ld = seg_desc(P, S, ls);
                 const long long a = q - S.seg_base[ls];
                 const long long t = S.seg_t0[ls] + g;
                 int dx, dy, dz;
@@ -626,7 +639,7 @@ __device__ void phase_a(const LaunchParams &P, CtaShared &S, unsigned char *stag
 // -ln(xi) of the time step of lattice segment i in grid cycle g (step 5).
 __device__ __forceinline__ double neg_log_xi(const LaunchParams &P, const CtaShared &S, int i, long long g)
 {
-    const LatticeDesc &Ld = P.desc[S.seg_slot[i]];
+    const LatticeDesc &Ld = seg_desc(P, S, i);
     unsigned long long wc[4];
     philox4x64_10((unsigned long long)(S.seg_t0[i] + g), 0ULL, 2ULL, 0ULL, Ld.seed, 0ULL, wc);
     const double xi = __ull2double_rn(2ULL * (wc[0] >> 12) + 1ULL) * 0x1p-53;
@@ -896,7 +909,7 @@ __device__ void phase_r(const LaunchParams &P, CtaShared &S, unsigned char *stag
             int bytes = 0;
             if (q < rend) {
                 const int ls = find_segment(S, q);
-                const LatticeDesc &Ld = P.desc[S.seg_slot[ls]];
+                const LatticeDesc &Ld = seg_desc(P, S, ls);
                 if (Ld.sub2 && g < S.seg_part[ls]) {
                     int dx, dy, dz;
                     active_domain(Ld, q - S.seg_base[ls], cycle_colour(S, Ld, ls, S.seg_t0[ls] + g), dx, dy, dz);
@@ -930,7 +943,7 @@ __device__ void phase_r(const LaunchParams &P, CtaShared &S, unsigned char *stag
             long long k = 0;
             if (q < rend) {
                 const int ls = find_segment(S, q);
-                const LatticeDesc &Ld = P.desc[S.seg_slot[ls]];
+                const LatticeDesc &Ld = seg_desc(P, S, ls);
                 if (Ld.sub2 && g < S.seg_part[ls]) {
                     int dx, dy, dz;
                     active_domain(Ld, q - S.seg_base[ls], cycle_colour(S, Ld, ls, S.seg_t0[ls] + g), dx, dy, dz);
@@ -998,7 +1011,7 @@ template <int D>
 __device__ FlipDelta apply_flip(const LaunchParams &P, CtaShared &S, const WorkItem &w,
                                 const unsigned char *stage, long long g)
 {
-    const LatticeDesc &Ld = P.desc[S.seg_slot[w.ls]];
+    const LatticeDesc &Ld = seg_desc(P, S, w.ls);
     const uint16_t *st = reinterpret_cast<const uint16_t *>(stage + w.off);
     int32_t *cnt = Ld.counts;
     // the domain's own count words (staged with the block); no other thread
@@ -1206,7 +1219,7 @@ __device__ __forceinline__ void phase_b_round(const LaunchParams &P, CtaShared &
             ls = find_segment(S, q);
             if (g < S.seg_part[ls]) {
                 const int slot = S.seg_slot[ls];
-                const LatticeDesc &Ld = P.desc[slot];
+                const LatticeDesc &Ld = seg_desc(P, S, ls);
                 a = q - S.seg_base[ls];
                 const long long t = S.seg_t0[ls] + g;
                 // the rate R the lines are padded to (Sec. 3.1 step 2 or the
@@ -1371,7 +1384,7 @@ __device__ __forceinline__ void phase_b_round(const LaunchParams &P, CtaShared &
             __syncthreads();
             if (threadIdx.x < nwork) {
                 const WorkItem &w = S.work[threadIdx.x];
-                const LatticeDesc &Ld = P.desc[S.seg_slot[w.ls]];
+                const LatticeDesc &Ld = seg_desc(P, S, w.ls);
                 asm volatile("fence.proxy.async.global;" ::: "memory");
                 bulk_copy_g2s(stage + w.off, Ld.cells + w.k * block_words(w.d), staged_bytes(w.d), &S.mbar);
             }
@@ -1481,6 +1494,13 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
     }
     __syncthreads();
     if (!S.ok) return; // the host sizes the grid so that this cannot happen
+    {
+        constexpr int kWords = (int)(sizeof(LatticeDesc) / 8);
+        const int ncached = S.nsegc < kDescCached ? S.nsegc : kDescCached;
+        for (int i = threadIdx.x; i < ncached * kWords; i += blockDim.x)
+            reinterpret_cast<unsigned long long *>(&S.descc[i / kWords])[i % kWords] =
+                reinterpret_cast<const unsigned long long *>(&P.desc[S.seg_slot[i / kWords]])[i % kWords];
+    }
     for (int i = threadIdx.x; i < S.nsegc; i += blockDim.x) {
         const LatticeState &st = P.state[S.seg_slot[i]];
         const long long budget = st.budget;
@@ -1510,7 +1530,7 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
         for (int i = threadIdx.x; i < S.nsegc; i += blockDim.x) {
             // the bound of Sec. 3.2 step 4b for lattices that use one (read
             // by the prepass, after step 1's barrier)
-            const LatticeDesc &Ld = P.desc[S.seg_slot[i]];
+            const LatticeDesc &Ld = seg_desc(P, S, i);
             if (Ld.rmode != SPKMC_RMAX_EXACT && g < S.seg_part[i]) {
                 double R = Ld.rbound;
                 if (Ld.rmode == SPKMC_RMAX_LEARNED) {
@@ -1530,7 +1550,7 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
         if (P.sub2_any) {
             // Sec. 3.2 step 4a, two colours: the colour of this cycle
             for (int i = threadIdx.x; i < S.nsegc; i += blockDim.x) {
-                const LatticeDesc &Ld = P.desc[S.seg_slot[i]];
+                const LatticeDesc &Ld = seg_desc(P, S, i);
                 if (Ld.sub2 && g < S.seg_part[i]) {
                     unsigned long long w[4];
                     philox4x64_10((unsigned long long)(S.seg_t0[i] + g), 0ULL, 5ULL, 0ULL, Ld.seed, 0ULL, w);
@@ -1546,7 +1566,7 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
                     if (g >= S.seg_part[i]) continue;
                     const long long a0 = S.seg_base[i] > lo ? S.seg_base[i] : lo;
                     const long long a1 = S.seg_base[i + 1] < hi ? S.seg_base[i + 1] : hi;
-                    total += (unsigned)(a1 - a0) * (unsigned)staged_bytes(P.desc[S.seg_slot[i]].d);
+                    total += (unsigned)(a1 - a0) * (unsigned)staged_bytes(seg_desc(P, S, i).d);
                 }
                 S.early_bytes = (int)total;
                 if (total) mbar_expect_tx(&S.mbar, total);
@@ -1558,7 +1578,7 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
             if (q < hi) {
                 const int ls = find_segment(S, q);
                 if (g < S.seg_part[ls]) {
-                    const LatticeDesc &Ld = P.desc[S.seg_slot[ls]];
+                    const LatticeDesc &Ld = seg_desc(P, S, ls);
                     const long long t = S.seg_t0[ls] + g;
                     int dx, dy, dz;
                     active_domain(Ld, q - S.seg_base[ls], cycle_colour(S, Ld, ls, t), dx, dy, dz);

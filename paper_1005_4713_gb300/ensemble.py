@@ -1,19 +1,20 @@
 """Batched ensembles of independent lattices (finite-size-scaling replicas).
 
 ``run_batched`` advances every lattice of the ensemble in one persistent
-launch per chunk of cycles (one flat table of all active domains, a separate
-R_max, clock and random streams per lattice); ``run_one_at_a_time`` runs the
-same lattices one after the other with the single-lattice entry points.
-Both sample m^2 and m^4 every ``sample_every`` cycles after ``burn_in``
-cycles, for the Binder ratio U_4 = <m^4>/<m^2>^2 of Eq. 7 (and the cumulant
-U = 1 - U_4/3), and return bit-comparable final observables.
+launch (one flat table of all active domains, a separate R_max, clock and
+random streams per lattice); ``run_one_at_a_time`` runs the same lattices
+one after the other with the single-lattice entry points.  Both sample m^2
+and m^4 every ``sample_every`` cycles after ``burn_in`` cycles, recorded on
+the device inside the launch, for the Binder ratio U_4 = <m^4>/<m^2>^2 of
+Eq. 7 (and the cumulant U = 1 - U_4/3), and return bit-comparable final
+observables.
 """
 from __future__ import annotations
 
 import time
 from dataclasses import dataclass, field
 
-from . import Batch, Lattice, make_config
+from . import Batch, Lattice, make_config, obs_buffer
 
 
 @dataclass
@@ -52,10 +53,23 @@ def run_batched(specs, cycles: int, sample_every: int = 50, burn_in: int = 0, co
         b.synchronize()
         t0 = time.perf_counter()
         done = 0
-        while done < cycles:
-            step = min(sample_every, cycles - done)
-            b.run(step)
-            done += step
+        # the samples are recorded on the device, many per launch
+        per_launch = max(1, (1 << 18) // sample_every)
+        rec = obs_buffer(n * min(per_launch, max(1, cycles // sample_every)))
+        while cycles - done >= sample_every:
+            nrec = min(per_launch, (cycles - done) // sample_every)
+            b.run_recorded(sample_every, nrec, rec)
+            b.synchronize()
+            for r in range(nrec):
+                done += sample_every
+                if done > burn_in:
+                    for i, sl in enumerate(slots):
+                        o = rec[sl * nrec + r]
+                        m2[i].append(o.m2)
+                        m4[i].append(o.m4)
+        if done < cycles:  # a last, shorter sample
+            b.run(cycles - done)
+            done = cycles
             if done > burn_in:
                 obs = b.observables_all()
                 for i, sl in enumerate(slots):
@@ -80,10 +94,20 @@ def run_one_at_a_time(specs, cycles: int, sample_every: int = 50, burn_in: int =
             lat.synchronize()
             t0 = time.perf_counter()
             done = 0
-            while done < cycles:
-                step = min(sample_every, cycles - done)
-                lat.run(step)
-                done += step
+            per_launch = max(1, (1 << 18) // sample_every)
+            rec = obs_buffer(min(per_launch, max(1, cycles // sample_every)))
+            while cycles - done >= sample_every:
+                nrec = min(per_launch, (cycles - done) // sample_every)
+                lat.run_recorded(sample_every, nrec, rec)
+                lat.synchronize()
+                for r in range(nrec):
+                    done += sample_every
+                    if done > burn_in:
+                        m2.append(rec[r].m2)
+                        m4.append(rec[r].m4)
+            if done < cycles:
+                lat.run(cycles - done)
+                done = cycles
                 if done > burn_in:
                     o = lat.observables()
                     m2.append(o.m2)

@@ -74,3 +74,21 @@ def test_batched_ensemble_equals_one_at_a_time():
     for x, y in zip(a.binder, b.binder):
         assert x["samples"] == y["samples"] == 2
         assert x["U4"] == y["U4"]
+
+
+def test_ensemble_samples_equal_plain_read_outs():
+    """The recorded samples (and a last, shorter sample) equal m^2 and m^4
+    read synchronously after plain runs to the same cycles."""
+    specs = wl.ensemble_specs(5, seed=13)
+    a = ensemble.run_batched(specs, cycles=130, sample_every=40, burn_in=50)
+    for s, got in zip(specs, a.binder):
+        with sp.Lattice(s.L, s.d, s.J, s.H, s.T, s.seed, cold=s.cold) as lat:
+            m2, m4 = [], []
+            for c in (40, 40, 40, 10):  # samples after cycles 80, 120, 130
+                lat.run(c)
+                if lat.observables().cycle > 50:
+                    o = lat.observables()
+                    m2.append(o.m2)
+                    m4.append(o.m4)
+        assert got["samples"] == 3
+        assert got["m2"] == sum(m2) / 3 and got["m4"] == sum(m4) / 3

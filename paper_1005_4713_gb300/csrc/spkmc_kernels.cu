@@ -1527,9 +1527,11 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
     const bool early = hi - lo <= P.round_items;
     for (long long g = 0; g < P.ncycles; ++g) {
         Line line; // this cycle's frequency line of the thread's item (one-round CTAs)
-        for (int i = threadIdx.x; i < S.nsegc; i += blockDim.x) {
+        for (int i = kThreads - 1 - (int)threadIdx.x; i < S.nsegc; i += kThreads) {
             // the bound of Sec. 3.2 step 4b for lattices that use one (read
-            // by the prepass, after step 1's barrier)
+            // by the prepass, after step 1), from the last threads: the
+            // learned bound waits for a memory round trip, and the first
+            // warps hold the items of step 1
             const LatticeDesc &Ld = seg_desc(P, S, i);
             if (Ld.rmode != SPKMC_RMAX_EXACT && g < S.seg_part[i]) {
                 double R = Ld.rbound;

@@ -105,13 +105,23 @@ def test_config_128_against_oracle(spec):
 
 def test_config_1024_first_eight_cycles():
     """1024^3 with 16^3-site domains (32768 events per cycle) in the launch
-    configuration the benchmark times: one visit of every colour, compared
-    in full with the oracle."""
+    configuration the benchmark times (one recorded launch, records every few
+    cycles): one visit of every colour, the records and the final state
+    compared in full with the oracle."""
     spec = wl.CONFIG_1024
     st = oracle_state(spec)
+    rec = sp.obs_buffer(2)
     with gpu_lattice(spec) as lat:
-        lat.run(8)
-        st.run(8, threads=THREADS)
+        lat.run_recorded(4, 2, rec)
+        lat.synchronize()
+        for r in range(2):
+            st.run(4, threads=THREADS)
+            o = rec[r]
+            assert o.cycle == st.cycle
+            assert (o.n_flip, o.n_null) == (st.n_flip, st.n_null)
+            assert (o.M, o.B) == st.observables()
+            assert int(o.sum_null_rate_fx[0]) | (int(o.sum_null_rate_fx[1]) << 64) == st.null_fx
+            assert o.clock == pytest.approx(st.clock, rel=CLOCK_RTOL, abs=0.0)
         assert_same(lat, st)
         o = lat.observables()
         assert o.n_flip + o.n_null == 8 * st.k_act

@@ -241,6 +241,52 @@ def cpu_baseline(rank: int, world: int, cycles: int = 8):
                       f"(one visit of each colour), OpenMP over active domains, {dt:.2f} s"}
 
 
+def cpu_baseline_extras(cycles_128: int = 40):
+    """The oracle single-threaded on one cycle of the 1024^3 lattice, and on
+    all cores on the 128^3 lattice with 8^3-site domains."""
+    import oracle
+    cores = os.cpu_count() or 1
+    st = oracle.State(L_BENCH, D_BENCH, 1.0, 0.0, 4.5115, SEED_BENCH)
+    t0 = time.perf_counter()
+    st.run(1, threads=1)
+    dt1 = time.perf_counter() - t0
+    st2 = oracle.State(128, 8, 1.0, 0.0, 4.5115, 2)
+    t0 = time.perf_counter()
+    st2.run(cycles_128, threads=cores)
+    dt2 = time.perf_counter() - t0
+    return {"single_thread": {"value": st.k_act / dt1, "unit": "events/s", "cores": 1,
+                              "sample": f"cycle 0 of {L_BENCH}^3, d={D_BENCH}, {dt1:.2f} s"},
+            "config_128_d8": {"value": cycles_128 * st2.k_act / dt2, "unit": "events/s", "cores": cores,
+                              "sample": f"{cycles_128} cycles of 128^3, d=8, hot start seed 2, {dt2:.2f} s"}}
+
+
+def small_configs(cfg, stream, every=100, nrec=20):
+    """Cycles of the two small lattices that live in L2 and shared memory
+    (16^3 with 4^3-site domains, 128^3 with 8^3-site domains), bound by the
+    per-cycle latency: microseconds per cycle and events/s of one recorded
+    launch of every * nrec cycles, CUDA events on the launch stream."""
+    import torch
+
+    import paper_1005_4713_gb300 as sp
+
+    out = {}
+    for name, (L, d, seed) in (("config_16_d4", (16, 4, 1)), ("config_128_d8", (128, 8, 2))):
+        with sp.Lattice(L, d, 1.0, 0.0, 4.5115, seed, config=cfg) as lat:
+            rec = sp.obs_buffer(nrec)
+            lat.run_recorded(every, nrec, rec)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lat.run_recorded(every, nrec, rec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            cycles = every * nrec
+            out[name] = {"us_per_cycle": ms * 1e3 / cycles, "events_per_s": cycles * lat.K_act / (ms / 1e3),
+                         "events_per_cycle": lat.K_act, "cycles": cycles}
+    return out
+
+
 def batched_summary(n_lattices=256, cycles=5000, solo_sample=16):
     """Ensemble of uneven lattices in one persistent launch per chunk vs the
     same lattices one at a time (a sample of them, scaled to all)."""
@@ -494,6 +540,8 @@ def run_gpu(args, world, rank, local, pg):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(rank, world)
+        cpu.update(cpu_baseline_extras())
+    small = small_configs(cfg, stream) if rank == 0 and world == 1 else None
     batched = served = variants = None
     if rank == 0 and world == 1 and not args.no_ensembles:
         batched = batched_summary()
@@ -535,6 +583,7 @@ def run_gpu(args, world, rank, local, pg):
             "per_step_launches": per_step,
             "graph": graph,
             "variants": variants,
+            "small_configs": small,
             "batched": batched,
             "served": served,
         }
@@ -556,9 +605,20 @@ def main(argv=None):
     ap.add_argument("--no-graph", action="store_true", help="skip the per-step launches and their CUDA-graph replay")
     ap.add_argument("--no-variants", "--no-bounds", dest="no_variants", action="store_true",
                     help="skip the R_max-bound and two-colour summaries")
+    ap.add_argument("--only-small", action="store_true",
+                    help="time only the 16^3 and 128^3 lattices (no contract line; for profiling)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.only_small:
+        import torch
+
+        import paper_1005_4713_gb300 as sp
+        torch.cuda.set_device(0)
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
+        print(json.dumps({"small_configs": small_configs(sp.torch_config(), stream)}))
+        return 0
     world, rank, local, pg = dist_setup(args.gpus)
     try:
         if args.impl == "reference":

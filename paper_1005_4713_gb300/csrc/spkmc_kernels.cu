@@ -1017,8 +1017,6 @@ __device__ FlipDelta apply_flip(const LaunchParams &P, CtaShared &S, const WorkI
     // the domain's own count words (staged with the block); no other thread
     // touches them this cycle
     int4 *own = reinterpret_cast<int4 *>(cnt + w.k * kCountStride);
-    const int4 *tw = reinterpret_cast<const int4 *>(slot_counts(const_cast<unsigned char *>(stage), w.off, P.item_bytes));
-    const int4 o0 = tw[0], o1 = tw[1], o2 = tw[2], o3 = tw[3];
     const int l = w.site;
     const int s3[3] = {l % D, (l / D) % D, l / (D * D)};
     const int sig = w.cls >= 7, us = w.cls - 7 * sig;
@@ -1133,35 +1131,38 @@ __device__ FlipDelta apply_flip(const LaunchParams &P, CtaShared &S, const WorkI
     }
     bool ok = true;
     if (!Ld.sub2) { // two-colour lattices recount at each visit instead
-    // a class move of a site adds 1 to the total and, in the lower half of
-    // its domain (z < D/2), 1 to bits 16-31 of the class word
-    int v[kClasses] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w, o2.x, o2.y, o2.z, o2.w, o3.x, o3.y};
-    const int snew = 7 * (1 - sig) + us;
-    const int inc_s = 1 + ((s3[2] < D / 2) << 16);
+        // a class move of a site adds 1 to the total and, in the lower half
+        // of its domain (z < D/2), 1 to bits 16-31 of the class word; the
+        // moves of the domain's own words go to its staged copy (only this
+        // thread touches the slot now), which is then written out
+        int *tail = reinterpret_cast<int *>(slot_counts(const_cast<unsigned char *>(stage), w.off, P.item_bytes));
+        const int inc_s = 1 + ((s3[2] < D / 2) << 16);
+        tail[w.cls] -= inc_s;
+        tail[7 * (1 - sig) + us] += inc_s;
 #pragma unroll
-    for (int c = 0; c < kClasses; ++c) v[c] += ((c == snew) - (c == w.cls)) * inc_s;
-#pragma unroll
-    for (int dir = 0; dir < 6; ++dir) {
-        const int cn = cold[dir] + delta;
-        int j3z = s3[2] + (dir == 4 ? -1 : (dir == 5 ? 1 : 0));
-        j3z = j3z < 0 ? D - 1 : (j3z >= D ? 0 : j3z); // z of the neighbour in its own domain
-        const int inc = 1 + ((j3z < D / 2) << 16);
-        if (cold[dir] >= 0 && cold[dir] < kClasses && cn >= 0 && cn < kClasses) {
-            if (outv[dir]) {
-                atomicAdd(cnt + kj[dir] * kCountStride + cold[dir], -inc);
-                atomicAdd(cnt + kj[dir] * kCountStride + cn, inc);
+        for (int dir = 0; dir < 6; ++dir) {
+            const int cn = cold[dir] + delta;
+            int j3z = s3[2] + (dir == 4 ? -1 : (dir == 5 ? 1 : 0));
+            j3z = j3z < 0 ? D - 1 : (j3z >= D ? 0 : j3z); // z of the neighbour in its own domain
+            const int inc = 1 + ((j3z < D / 2) << 16);
+            if (cold[dir] >= 0 && cold[dir] < kClasses && cn >= 0 && cn < kClasses) {
+                if (outv[dir]) {
+                    atomicAdd(cnt + kj[dir] * kCountStride + cold[dir], -inc);
+                    atomicAdd(cnt + kj[dir] * kCountStride + cn, inc);
+                } else {
+                    tail[cold[dir]] -= inc;
+                    tail[cn] += inc;
+                }
             } else {
-#pragma unroll
-                for (int c = 0; c < kClasses; ++c) v[c] += ((c == cn) - (c == cold[dir])) * inc;
+                ok = false;
             }
-        } else {
-            ok = false;
         }
-    }
-    __stcg(own, make_int4(v[0], v[1], v[2], v[3]));
-    __stcg(own + 1, make_int4(v[4], v[5], v[6], v[7]));
-    __stcg(own + 2, make_int4(v[8], v[9], v[10], v[11]));
-    __stcg(own + 3, make_int4(v[12], v[13], 0, 0));
+        const int4 *t4 = reinterpret_cast<const int4 *>(tail);
+        const int4 v0 = t4[0], v1 = t4[1], v2 = t4[2], v3 = t4[3];
+        __stcg(own, v0);
+        __stcg(own + 1, v1);
+        __stcg(own + 2, v2);
+        __stcg(own + 3, make_int4(v3.x, v3.y, 0, 0));
     }
     if (!ok) raise_error(P.err, SPKMC_EINTERNAL);
     const int x = s3[0], y = s3[1], z = s3[2];

@@ -414,10 +414,15 @@ int upload_slot(spkmc_batch *b, int slot)
     return SPKMC_OK;
 }
 
-int refresh_derived(spkmc_batch *b, const LatticeDesc &d)
+// Ghost faces, class counts and the exact M and B of a slot from its rows
+// (the last two in one pass).
+int refresh_derived(spkmc_batch *b, int slot)
 {
+    const LatticeDesc &d = b->slots[slot].desc;
+    LatticeState *st = b->d_state + slot;
     if (launch_ghosts(d, 0, nullptr, b->stream) != SPKMC_OK) return cuda_fail(cudaGetLastError(), "ghost faces");
-    if (launch_count_classes(d, 0, nullptr, b->stream) != SPKMC_OK)
+    CUDA_TRY(cudaMemsetAsync(&st->M, 0, 2 * sizeof(long long), b->stream), "clear M, B");
+    if (launch_count_classes(d, 0, nullptr, &st->M, b->stream) != SPKMC_OK)
         return cuda_fail(cudaGetLastError(), "class counts");
     return SPKMC_OK;
 }
@@ -497,8 +502,7 @@ int admit(spkmc_batch *b, const spkmc_params *p, long long cycles, int slot_hint
     s.budget = cycles;
     rc = upload_slot(b, slot);
     if (!rc) rc = launch_init_rows(D, p->init, b->stream);
-    if (!rc) rc = refresh_derived(b, D);
-    if (!rc) rc = recompute_MB(b, slot);
+    if (!rc) rc = refresh_derived(b, slot);
     if (rc) {
         free_slot_memory(b, s);
         s.live = false;
@@ -695,6 +699,25 @@ int observables(spkmc_batch *b, int slot, spkmc_obs *out)
 }
 
 // Spins to the host: one int8 per site, or (packed) one bit per site.
+// Device address of n bytes of page-locked host memory mapped into the
+// current device's address space (cudaHostAlloc, or cudaHostRegister with
+// mapping), or nullptr for any other memory: packed spins move between such
+// a buffer and the rows in the transposing kernel itself, without a staging
+// copy.  Both ends of the range must be mapped, at the same offset.
+void *mapped_host(const void *host, size_t n)
+{
+    cudaPointerAttributes a{}, z{};
+    if (cudaPointerGetAttributes(&a, host) != cudaSuccess ||
+        cudaPointerGetAttributes(&z, (const char *)host + (n - 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || z.type != cudaMemoryTypeHost || !a.devicePointer || !z.devicePointer ||
+        (char *)z.devicePointer != (char *)a.devicePointer + (n - 1))
+        return nullptr;
+    return a.devicePointer;
+}
+
 int get_spins(spkmc_batch *b, int slot, void *host, size_t n, bool packed = false)
 {
     int rc = slot_check(b, slot);
@@ -705,6 +728,12 @@ int get_spins(spkmc_batch *b, int slot, void *host, size_t n, bool packed = fals
         return fail(SPKMC_EINVAL, packed ? "host buffer must hold L^3 / 8 = %zu bytes" : "host buffer must hold L^3 = %zu int8", N);
     DeviceGuard g(b->device);
     if ((rc = sync_and_check(b)) != SPKMC_OK) return rc;
+    if (void *direct = packed ? mapped_host(host, N) : nullptr) {
+        if ((rc = launch_unpack_bits(s.desc, (uint8_t *)direct, b->stream)) != SPKMC_OK)
+            return cuda_fail(cudaGetLastError(), "read spins");
+        CUDA_TRY(cudaStreamSynchronize(b->stream), "read spins");
+        return SPKMC_OK;
+    }
     void *tmp = b->dev_alloc(N);
     if (!tmp) return fail(SPKMC_ENOMEM, "device allocation of %zu bytes failed", N);
     rc = packed ? launch_unpack_bits(s.desc, (uint8_t *)tmp, b->stream)
@@ -728,20 +757,20 @@ int set_spins(spkmc_batch *b, int slot, const void *host, size_t n, bool packed 
         return fail(SPKMC_EINVAL, packed ? "host buffer must hold L^3 / 8 = %zu bytes" : "host buffer must hold L^3 = %zu int8", N);
     DeviceGuard g(b->device);
     if ((rc = sync_and_check(b)) != SPKMC_OK) return rc;
-    void *tmp = b->dev_alloc(N);
-    if (!tmp) return fail(SPKMC_ENOMEM, "device allocation of %zu bytes failed", N);
-    cudaError_t e = cudaMemcpyAsync(tmp, host, N, cudaMemcpyHostToDevice, b->stream);
+    void *direct = packed ? mapped_host(host, N) : nullptr;
+    void *tmp = direct ? nullptr : b->dev_alloc(N);
+    if (!direct && !tmp) return fail(SPKMC_ENOMEM, "device allocation of %zu bytes failed", N);
+    cudaError_t e = direct ? cudaSuccess : cudaMemcpyAsync(tmp, host, N, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) // the R_max history described the old spins
         e = cudaMemsetAsync(b->d_state[slot].rmax, 0, sizeof(b->d_state[slot].rmax), b->stream);
     if (e == cudaSuccess) {
-        rc = packed ? launch_pack_bits(s.desc, (const uint8_t *)tmp, b->stream)
+        rc = packed ? launch_pack_bits(s.desc, (const uint8_t *)(direct ? direct : tmp), b->stream)
                     : launch_pack_rows(s.desc, (const int8_t *)tmp, b->stream);
-        if (!rc) rc = refresh_derived(b, s.desc);
-        if (!rc) rc = recompute_MB(b, slot);
+        if (!rc) rc = refresh_derived(b, slot);
         if (rc) e = cudaGetLastError();
     }
     cudaError_t e2 = cudaStreamSynchronize(b->stream);
-    b->dev_free(tmp, N);
+    if (tmp) b->dev_free(tmp, N);
     if (e != cudaSuccess) return cuda_fail(e, "write spins");
     if (rc) return rc;
     if (e2 != cudaSuccess) return cuda_fail(e2, "write spins");
@@ -1148,7 +1177,7 @@ int spkmc_class_counts(spkmc_t *h, int32_t *host_counts, size_t n)
     int rc = sync_and_check(b);
     if (rc) return rc;
     // two-colour lattices keep no class counts between visits: count now
-    if (s.desc.sub2 && launch_count_classes(s.desc, 0, nullptr, b->stream) != SPKMC_OK)
+    if (s.desc.sub2 && launch_count_classes(s.desc, 0, nullptr, nullptr, b->stream) != SPKMC_OK)
         return cuda_fail(cudaGetLastError(), "recount");
     std::vector<int32_t> tmp((size_t)(s.desc.K * kCountStride));
     CUDA_TRY(cudaMemcpyAsync(tmp.data(), s.desc.counts, tmp.size() * 4, cudaMemcpyDeviceToHost, b->stream),
@@ -1172,7 +1201,7 @@ int spkmc_check_counts(spkmc_t *h, int64_t *mismatched)
     const LatticeDesc &D = b->slots[h->slot].desc;
     // two-colour lattices keep no class counts between visits: refresh them
     // (the ghost faces and M, B are still checked)
-    if ((rc = launch_count_classes(D, D.sub2 ? 0 : 1, b->d_mismatch, b->stream)) != SPKMC_OK)
+    if ((rc = launch_count_classes(D, D.sub2 ? 0 : 1, b->d_mismatch, nullptr, b->stream)) != SPKMC_OK)
         return cuda_fail(cudaGetLastError(), "recount");
     if ((rc = launch_ghosts(D, 1, b->d_mismatch, b->stream)) != SPKMC_OK)
         return cuda_fail(cudaGetLastError(), "ghost check");
@@ -1461,7 +1490,7 @@ extern "C" int spkmc_run_cycles_noalloc(const spkmc_params *p, int8_t *dev_spins
     CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), s), "clear error flag");
     if ((rc = launch_pack_rows(D, dev_spins, s)) != SPKMC_OK) return cuda_fail(cudaGetLastError(), "pack spins");
     if ((rc = launch_ghosts(D, 0, nullptr, s)) != SPKMC_OK) return cuda_fail(cudaGetLastError(), "ghost faces");
-    if ((rc = launch_count_classes(D, 0, nullptr, s)) != SPKMC_OK) return cuda_fail(cudaGetLastError(), "class counts");
+    if ((rc = launch_count_classes(D, 0, nullptr, nullptr, s)) != SPKMC_OK) return cuda_fail(cudaGetLastError(), "class counts");
 
     // the cycles, in launches of at most 2^18 cycles, as spkmc_run_cycles
     const long long per_sm = g_noalloc_blocks_per_sm[dev];

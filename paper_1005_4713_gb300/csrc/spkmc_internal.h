@@ -150,7 +150,9 @@ int launch_unpack_bits(const LatticeDesc &d, uint8_t *dev_bits, void *stream);
 int launch_ghosts(const LatticeDesc &d, int mode, unsigned long long *mismatch, void *stream);
 // mode 0: write counts; mode 1: compare with the stored counts and add the
 // number of mismatching domains to *mismatch (device int64).
-int launch_count_classes(const LatticeDesc &d, int mode, unsigned long long *mismatch,
+// With MB (mode 0), also M and B (device int64 pair, accumulated) in the same
+// pass; the ghost faces must be current.
+int launch_count_classes(const LatticeDesc &d, int mode, unsigned long long *mismatch, long long *MB,
                          void *stream);
 // M and B (device int64 pair, accumulated).
 int launch_obs_record(const LatticeState *st, int L, int d, double J, double H, spkmc_obs *out, void *stream);

@@ -182,9 +182,11 @@ __device__ __forceinline__ long long domain_index(int nd, int dx, int dy, int dz
 
 __device__ __forceinline__ void domain_coords(const LatticeDesc &Ld, long long k, int &dx, int &dy, int &dz)
 {
-    dx = (int)(k % Ld.nd);
-    dy = (int)((k / Ld.nd) % Ld.nd);
-    dz = (int)(k / ((long long)Ld.nd * Ld.nd));
+    // K = nd^3 < 2^32 for any lattice that fits a GPU: 32-bit divisions
+    const unsigned kk = (unsigned)k, nd = (unsigned)Ld.nd, q = kk / nd;
+    dx = (int)(kk - q * nd);
+    dy = (int)(q % nd);
+    dz = (int)(q / nd);
 }
 
 __device__ __forceinline__ int wrap_coord(int a, int n)
@@ -1742,8 +1744,129 @@ __global__ void unpack_rows_kernel(LatticeDesc Ld, int8_t *s8)
     }
 }
 
-// Rows from global spins packed one bit per site (bit i mod 8 of byte i / 8
-// is site i in global order, 1 for +1).
+// Transposition between domain rows and spins packed one bit per site in
+// global order (bit i mod 8 of byte i / 8 is site i, 1 for +1), by tiles of
+// up to 32 domains along x at one (dy, dz).  Their D*D rows r = y + D z cover
+// D*D global line segments of 4 D bytes or fewer, which start on a byte
+// when L % 8 == 0 (and on a word when L % 32 == 0); the segments sit in
+// shared memory, one per row, at a stride of an odd number of words so that
+// a warp on consecutive rows meets distinct banks.
+constexpr int kTileDomains = 32;
+template <int D>
+__host__ __device__ constexpr int tile_line_stride() { return ((kTileDomains * D / 32) | 1) * 4; }
+
+struct BitTile {
+    int dx0, dy, dz, G, nb; // first domain, extent along x, segment bytes
+    long long seg0;         // byte of row 0's segment
+};
+
+template <int D>
+__device__ __forceinline__ BitTile bit_tile(const LatticeDesc &Ld, long long tile)
+{
+    const int nd = Ld.nd, ngx = (nd + kTileDomains - 1) / kTileDomains;
+    BitTile T;
+    const long long q = tile / ngx;
+    T.dx0 = (int)(tile - q * ngx) * kTileDomains;
+    T.dy = (int)(q % nd);
+    T.dz = (int)(q / nd);
+    T.G = min(kTileDomains, nd - T.dx0);
+    T.nb = T.G * D / 8;
+    const long long L = Ld.L;
+    T.seg0 = (((long long)T.dz * D * L + (long long)T.dy * D) * L + (long long)T.dx0 * D) / 8;
+    return T;
+}
+
+// byte offset of row r's segment from the tile's first
+template <int D>
+__device__ __forceinline__ long long seg_offset(long long L, int r)
+{
+    return ((long long)(r / D) * L + (r % D)) * (L / 8);
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) pack_bits_tiled_kernel(LatticeDesc Ld, const uint8_t *bits)
+{
+    constexpr int S = tile_line_stride<D>();
+    __shared__ __align__(16) uint8_t seg[D * D * S];
+    const long long L = Ld.L, ntiles = (long long)Ld.nd * Ld.nd * ((Ld.nd + kTileDomains - 1) / kTileDomains);
+    const bool wide = L % 32 == 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const BitTile T = bit_tile<D>(Ld, tile);
+        if (wide) {
+            const int nw = T.nb / 4;
+            for (int i = threadIdx.x; i < D * D * nw; i += blockDim.x) {
+                const int r = i / nw, w = i - r * nw;
+                *reinterpret_cast<uint32_t *>(seg + r * S + 4 * w) =
+                    __ldcs(reinterpret_cast<const uint32_t *>(bits + T.seg0 + seg_offset<D>(L, r)) + w);
+            }
+        } else {
+            for (int i = threadIdx.x; i < D * D * T.nb; i += blockDim.x) {
+                const int r = i / T.nb, b = i - r * T.nb;
+                seg[r * S + b] = bits[T.seg0 + seg_offset<D>(L, r) + b];
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < T.G * D * D; i += blockDim.x) {
+            const int j = i / (D * D), r = i % (D * D);
+            const uint8_t *ln = seg + r * S;
+            uint32_t row;
+            if constexpr (D == 16) row = ln[2 * j] | ((uint32_t)ln[2 * j + 1] << 8);
+            else if constexpr (D == 8) row = ln[j];
+            else row = (ln[(j * D) >> 3] >> ((j * D) & 7)) & ((1u << D) - 1u);
+            block_of<D>(Ld, domain_index(Ld.nd, T.dx0 + j, T.dy, T.dz))[r] = (uint16_t)row;
+        }
+        __syncthreads();
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) unpack_bits_tiled_kernel(LatticeDesc Ld, uint8_t *bits)
+{
+    constexpr int S = tile_line_stride<D>();
+    __shared__ __align__(16) uint8_t seg[D * D * S];
+    const long long L = Ld.L, ntiles = (long long)Ld.nd * Ld.nd * ((Ld.nd + kTileDomains - 1) / kTileDomains);
+    const bool wide = L % 32 == 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const BitTile T = bit_tile<D>(Ld, tile);
+        if constexpr (D >= 8) { // a row is whole bytes of its segment
+            for (int i = threadIdx.x; i < T.G * D * D; i += blockDim.x) {
+                const int j = i / (D * D), r = i % (D * D);
+                const uint32_t row = block_of<D>(Ld, domain_index(Ld.nd, T.dx0 + j, T.dy, T.dz))[r];
+                uint8_t *ln = seg + r * S;
+                ln[(D / 8) * j] = (uint8_t)row;
+                if constexpr (D == 16) ln[2 * j + 1] = (uint8_t)(row >> 8);
+            }
+        } else { // 8 / D rows of consecutive domains share a byte
+            for (int i = threadIdx.x; i < D * D * T.nb; i += blockDim.x) {
+                const int r = i / T.nb, b = i - r * T.nb;
+                uint32_t v = 0;
+#pragma unroll
+                for (int m = 0; m < 8 / D; ++m)
+                    v |= (uint32_t)block_of<D>(Ld, domain_index(Ld.nd, T.dx0 + b * (8 / D) + m, T.dy, T.dz))[r]
+                         << (m * D);
+                seg[r * S + b] = (uint8_t)v;
+            }
+        }
+        __syncthreads();
+        if (wide) {
+            const int nw = T.nb / 4;
+            for (int i = threadIdx.x; i < D * D * nw; i += blockDim.x) {
+                const int r = i / nw, w = i - r * nw;
+                __stcs(reinterpret_cast<uint32_t *>(bits + T.seg0 + seg_offset<D>(L, r)) + w,
+                       *reinterpret_cast<const uint32_t *>(seg + r * S + 4 * w));
+            }
+        } else {
+            for (int i = threadIdx.x; i < D * D * T.nb; i += blockDim.x) {
+                const int r = i / T.nb, b = i - r * T.nb;
+                bits[T.seg0 + seg_offset<D>(L, r) + b] = seg[r * S + b];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// The same one thread per row or byte, for L % 8 != 0 (lines that do not
+// start on a byte, possible for D < 8).
 template <int D>
 __global__ void pack_bits_kernel(LatticeDesc Ld, const uint8_t *bits)
 {
@@ -1773,7 +1896,17 @@ __global__ void unpack_bits_kernel(LatticeDesc Ld, uint8_t *bits)
     for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nbytes;
          b += (long long)gridDim.x * blockDim.x) {
         const long long site = 8 * b;
-        int X = (int)(site % L), Y = (int)((site / L) % L), Z = (int)(site / (L * L));
+        int X, Y, Z;
+        if (L * L * L <= 0xFFFFFFFFLL) { // 32-bit divisions when the sites fit
+            const unsigned sv = (unsigned)site, ul = (unsigned)L, q = sv / ul;
+            X = (int)(sv - q * ul);
+            Y = (int)(q % ul);
+            Z = (int)(q / ul);
+        } else {
+            X = (int)(site % L);
+            Y = (int)((site / L) % L);
+            Z = (int)(site / (L * L));
+        }
         if constexpr (D >= 8) { // L is a multiple of 8: the byte is 8 bits of one row
             const long long k = domain_index(Ld.nd, X / D, Y / D, Z / D);
             bits[b] = (uint8_t)(block_of<D>(Ld, k)[(Y % D) + D * (Z % D)] >> (X % D));
@@ -1835,20 +1968,36 @@ __global__ void ghosts_kernel(LatticeDesc Ld, int mode, unsigned long long *mism
     if (mode == 1 && bad) atomicAdd(mismatch, bad);
 }
 
+// With MB (mode 0), M and B of Eq. 1 / Eq. 4 in the same pass: +x bonds
+// inside each row and against the +x ghost, +y and +z bonds against the next
+// row or the ghost faces (which must be current).
 template <int D>
 __global__ void __launch_bounds__(256) count_classes_kernel(LatticeDesc Ld, int mode,
-                                                            unsigned long long *mismatch)
+                                                            unsigned long long *mismatch, long long *MB)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr uint32_t V = ((1u << D) - 1u) << 1;
     unsigned long long bad = 0;
+    long long M = 0, B = 0;
     for (long long k = blockIdx.x * 8LL + warp; k < Ld.K; k += gridDim.x * 8LL) {
         const uint16_t *blk = block_of<D>(Ld, k);
+        const uint16_t *gh = blk + D * D;
         int cnt[kClasses];
 #pragma unroll
         for (int c = 0; c < kClasses; ++c) cnt[c] = 0;
+        int m = 0, b = 0;
         for (int r = lane; r < D * D; r += 32) {
             const RowPlanes p = classify_row<D>(blk, r % D, r / D);
+            if (MB) {
+                const int y = r % D, z = r / D;
+                const uint32_t s = p.s; // bit x + 1 is spin x, x in [-1, D]
+                const uint32_t yp = (uint32_t)(y < D - 1 ? blk[r + 1] : gh[3 * D + z]) << 1;
+                const uint32_t zp = (uint32_t)(z < D - 1 ? blk[r + D] : gh[5 * D + y]) << 1;
+                m += 2 * __popc(s & V) - D;
+                b += 2 * __popc(~(s ^ (s >> 1)) & V) - D;
+                b += 2 * __popc(~(s ^ yp) & V) - D;
+                b += 2 * __popc(~(s ^ zp) & V) - D;
+            }
             const int inc_low = (r < D * D / 2) ? (1 << 16) : 0; // lower half: z < D/2
 #pragma unroll
             for (int u = 0; u < 7; ++u) {
@@ -1871,8 +2020,16 @@ __global__ void __launch_bounds__(256) count_classes_kernel(LatticeDesc Ld, int 
         }
         if (mode == 0 && lane >= kClasses && lane < kCountStride) Ld.counts[k * kCountStride + lane] = 0;
         if (__any_sync(kFull, differs) && lane == 0) ++bad;
+        if (MB) {
+            M += __reduce_add_sync(kFull, m);
+            B += __reduce_add_sync(kFull, b);
+        }
     }
     if (mode == 1 && lane == 0 && bad) atomicAdd(mismatch, bad);
+    if (MB && lane == 0 && (M || B)) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(MB), (unsigned long long)M);
+        atomicAdd(reinterpret_cast<unsigned long long *>(MB + 1), (unsigned long long)B);
+    }
 }
 
 // M and B of Eq. 1 / Eq. 4, one warp per domain: +x bonds inside each row
@@ -1998,6 +2155,12 @@ int launch_unpack_rows(const LatticeDesc &d, int8_t *dev_spins, void *stream)
 
 int launch_pack_bits(const LatticeDesc &d, const uint8_t *dev_bits, void *stream)
 {
+    if (d.L % 8 == 0) {
+        const long long tiles = (long long)d.nd * d.nd * ((d.nd + kTileDomains - 1) / kTileDomains);
+        SPKMC_DISPATCH_D(d.d, pack_bits_tiled_kernel, (int)(tiles < 2048 ? tiles : 2048), 256, (cudaStream_t)stream, d,
+                         dev_bits);
+        return to_status(cudaGetLastError());
+    }
     const int grid = simple_grid(d.K * d.d * d.d, 256);
     SPKMC_DISPATCH_D(d.d, pack_bits_kernel, grid, 256, (cudaStream_t)stream, d, dev_bits);
     return to_status(cudaGetLastError());
@@ -2005,6 +2168,12 @@ int launch_pack_bits(const LatticeDesc &d, const uint8_t *dev_bits, void *stream
 
 int launch_unpack_bits(const LatticeDesc &d, uint8_t *dev_bits, void *stream)
 {
+    if (d.L % 8 == 0) {
+        const long long tiles = (long long)d.nd * d.nd * ((d.nd + kTileDomains - 1) / kTileDomains);
+        SPKMC_DISPATCH_D(d.d, unpack_bits_tiled_kernel, (int)(tiles < 2048 ? tiles : 2048), 256, (cudaStream_t)stream, d,
+                         dev_bits);
+        return to_status(cudaGetLastError());
+    }
     const long long L = d.L;
     const int grid = simple_grid(L * L * L / 8, 256);
     SPKMC_DISPATCH_D(d.d, unpack_bits_kernel, grid, 256, (cudaStream_t)stream, d, dev_bits);
@@ -2018,10 +2187,10 @@ int launch_ghosts(const LatticeDesc &d, int mode, unsigned long long *mismatch, 
     return to_status(cudaGetLastError());
 }
 
-int launch_count_classes(const LatticeDesc &d, int mode, unsigned long long *mismatch, void *stream)
+int launch_count_classes(const LatticeDesc &d, int mode, unsigned long long *mismatch, long long *MB, void *stream)
 {
     const int grid = simple_grid(d.K, 8);
-    SPKMC_DISPATCH_D(d.d, count_classes_kernel, grid, 256, (cudaStream_t)stream, d, mode, mismatch);
+    SPKMC_DISPATCH_D(d.d, count_classes_kernel, grid, 256, (cudaStream_t)stream, d, mode, mismatch, MB);
     return to_status(cudaGetLastError());
 }
 

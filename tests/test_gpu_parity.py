@@ -326,6 +326,41 @@ def test_graph_arguments_are_checked():
         assert e.value.code == sp.SPKMC_EINVAL
 
 
+@pytest.mark.parametrize("L,d", [
+    (80, 2),    # nd = 40: a full and a partial tile of domains along x, byte lines
+    (160, 4),   # word lines (L % 32 == 0)
+    (288, 8),
+    (544, 16),  # nd = 34: the second tile two domains wide
+    (64, 2),    # nd = 32: one full tile
+])
+@pytest.mark.parametrize("pinned", [False, True])
+def test_packed_spins_tiles(L, d, pinned):
+    """Packed spins written and read back through tiles of up to 32 domains
+    along x, from pageable buffers (staged through device memory) and from
+    page-locked ones (read and written by the kernels in place): random bytes
+    come back unchanged, the int8 read-out is their little-endian bits, and
+    M and B of Eq. 1 / Eq. 4, refreshed on writing, equal the sums over the
+    lattice."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(L + d)
+    bits = rng.integers(0, 256, size=L ** 3 // 8, dtype=np.uint8)
+    src, out = bits, np.empty_like(bits)
+    if pinned:
+        src = torch.empty(bits.size, dtype=torch.uint8, pin_memory=True).numpy()
+        src[:] = bits
+        out = torch.empty(bits.size, dtype=torch.uint8, pin_memory=True).numpy()
+    with gpu_lattice(wl.LatticeSpec(L=L, d=d, seed=66)) as a:
+        a.set_spins_packed(src)
+        assert np.array_equal(a.spins_packed(out), bits)
+        s = np.unpackbits(bits, bitorder="little").astype(np.int8) * 2 - 1
+        assert np.array_equal(a.spins(), s)
+        s = s.reshape(L, L, L)  # [Z, Y, X]
+        B = sum(int(np.sum(s * np.roll(s, -1, axis=ax), dtype=np.int64)) for ax in range(3))
+        o = a.observables()
+        assert (o.M, o.B) == (int(np.sum(s, dtype=np.int64)), B)
+        assert a.check_counts() == 0
+
+
 @pytest.mark.parametrize("spec", [
     wl.LatticeSpec(L=4, d=2, seed=61),    # L^3 / 8 bytes cross x-lines
     wl.LatticeSpec(L=12, d=2, seed=62),   # L not a multiple of 8

@@ -274,11 +274,11 @@ int spkmc_set_spins(spkmc_t *h, const int8_t *host_buf, size_t n);
 /* The same spins packed one bit per site: bit (i mod 8) of byte i / 8 is site
  * i = x + L (y + L z) of the global order above, 1 for +1 and 0 for -1;
  * nbytes = L^3 / 8 (an eighth of the int8 transfer), else EINVAL.  set has
- * the effects of spkmc_set_spins.  A page-locked buffer mapped into the
- * device's address space (cudaHostAlloc, cudaHostRegister with mapping) is
- * read or written in place by the transposing kernel, with no device
- * staging buffer; any other host memory goes through one.  Both calls return
- * once the buffer is no longer used. */
+ * the effects of spkmc_set_spins.  For these and spkmc_get/set_spins, a
+ * page-locked buffer mapped into the device's address space (cudaHostAlloc,
+ * cudaHostRegister with mapping) is read or written in place by the
+ * transposing kernel, with no device staging buffer; any other host memory
+ * goes through one.  All four return once the buffer is no longer used. */
 int spkmc_get_spins_packed(spkmc_t *h, uint8_t *host_bits, size_t nbytes);
 int spkmc_set_spins_packed(spkmc_t *h, const uint8_t *host_bits, size_t nbytes);
 /* Copy up to cap logged events (cycle-major, ascending k within a cycle);

@@ -701,8 +701,8 @@ int observables(spkmc_batch *b, int slot, spkmc_obs *out)
 // Spins to the host: one int8 per site, or (packed) one bit per site.
 // Device address of n bytes of page-locked host memory mapped into the
 // current device's address space (cudaHostAlloc, or cudaHostRegister with
-// mapping), or nullptr for any other memory: packed spins move between such
-// a buffer and the rows in the transposing kernel itself, without a staging
+// mapping), or nullptr for any other memory: spins move between such a
+// buffer and the rows in the transposing kernel itself, without a staging
 // copy.  Both ends of the range must be mapped, at the same offset.
 void *mapped_host(const void *host, size_t n)
 {
@@ -728,9 +728,10 @@ int get_spins(spkmc_batch *b, int slot, void *host, size_t n, bool packed = fals
         return fail(SPKMC_EINVAL, packed ? "host buffer must hold L^3 / 8 = %zu bytes" : "host buffer must hold L^3 = %zu int8", N);
     DeviceGuard g(b->device);
     if ((rc = sync_and_check(b)) != SPKMC_OK) return rc;
-    if (void *direct = packed ? mapped_host(host, N) : nullptr) {
-        if ((rc = launch_unpack_bits(s.desc, (uint8_t *)direct, b->stream)) != SPKMC_OK)
-            return cuda_fail(cudaGetLastError(), "read spins");
+    if (void *direct = mapped_host(host, N)) {
+        rc = packed ? launch_unpack_bits(s.desc, (uint8_t *)direct, b->stream)
+                    : launch_unpack_rows(s.desc, (int8_t *)direct, b->stream);
+        if (rc) return cuda_fail(cudaGetLastError(), "read spins");
         CUDA_TRY(cudaStreamSynchronize(b->stream), "read spins");
         return SPKMC_OK;
     }
@@ -757,7 +758,7 @@ int set_spins(spkmc_batch *b, int slot, const void *host, size_t n, bool packed 
         return fail(SPKMC_EINVAL, packed ? "host buffer must hold L^3 / 8 = %zu bytes" : "host buffer must hold L^3 = %zu int8", N);
     DeviceGuard g(b->device);
     if ((rc = sync_and_check(b)) != SPKMC_OK) return rc;
-    void *direct = packed ? mapped_host(host, N) : nullptr;
+    void *direct = mapped_host(host, N);
     void *tmp = direct ? nullptr : b->dev_alloc(N);
     if (!direct && !tmp) return fail(SPKMC_ENOMEM, "device allocation of %zu bytes failed", N);
     cudaError_t e = direct ? cudaSuccess : cudaMemcpyAsync(tmp, host, N, cudaMemcpyHostToDevice, b->stream);
@@ -765,7 +766,7 @@ int set_spins(spkmc_batch *b, int slot, const void *host, size_t n, bool packed 
         e = cudaMemsetAsync(b->d_state[slot].rmax, 0, sizeof(b->d_state[slot].rmax), b->stream);
     if (e == cudaSuccess) {
         rc = packed ? launch_pack_bits(s.desc, (const uint8_t *)(direct ? direct : tmp), b->stream)
-                    : launch_pack_rows(s.desc, (const int8_t *)tmp, b->stream);
+                    : launch_pack_rows(s.desc, (const int8_t *)(direct ? direct : tmp), b->stream);
         if (!rc) rc = refresh_derived(b, slot);
         if (rc) e = cudaGetLastError();
     }

@@ -1865,6 +1865,95 @@ __global__ void __launch_bounds__(256) unpack_bits_tiled_kernel(LatticeDesc Ld, 
     }
 }
 
+// The same tiles for one int8 per site (+1 or -1; a site is +1 where its
+// byte is > 0).  A domain's row is D consecutive bytes of its global line, so
+// the rows are formed or expanded in registers and shared memory holds the
+// tile's rows, [domain][row] at a stride of an odd number of words.
+template <int D>
+__device__ __forceinline__ long long tile_site0(const LatticeDesc &Ld, const BitTile &T)
+{
+    const long long L = Ld.L;
+    return ((long long)T.dz * D * L + (long long)T.dy * D) * L + (long long)T.dx0 * D;
+}
+
+template <int D>
+__device__ __forceinline__ long long line_offset(long long L, int r)
+{
+    return ((long long)(r / D) * L + (r % D)) * L;
+}
+
+// 4 bits to 4 bytes of +1 (bit set) or -1
+__device__ __forceinline__ uint32_t spins4(uint32_t b)
+{
+    const uint32_t w = ((b & 0xFu) * 0x00204081u) & 0x01010101u; // bit i to byte i
+    return w | ((w ^ 0x01010101u) * 0xFFu);
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) pack_rows_tiled_kernel(LatticeDesc Ld, const int8_t *s8)
+{
+    constexpr int S = D * D + 2;
+    __shared__ __align__(16) uint16_t rows[kTileDomains * S];
+    const long long L = Ld.L, ntiles = (long long)Ld.nd * Ld.nd * ((Ld.nd + kTileDomains - 1) / kTileDomains);
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const BitTile T = bit_tile<D>(Ld, tile);
+        const long long site0 = tile_site0<D>(Ld, T);
+        for (int i = threadIdx.x; i < D * D * T.G; i += blockDim.x) {
+            const int r = i / T.G, j = i - r * T.G;
+            const int8_t *src = s8 + site0 + line_offset<D>(L, r) + (long long)j * D;
+            uint32_t row = 0;
+            if constexpr (D == 16) { // 16-byte aligned: L, x0 and the buffer
+                const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(src));
+                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int x = 0; x < 4; ++x) row |= (uint32_t)((int8_t)(w[q] >> (8 * x)) > 0) << (4 * q + x);
+            } else {
+#pragma unroll
+                for (int x = 0; x < D; ++x) row |= (uint32_t)(src[x] > 0) << x;
+            }
+            rows[j * S + r] = (uint16_t)row;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < T.G * D * D; i += blockDim.x) {
+            const int j = i / (D * D), r = i % (D * D);
+            block_of<D>(Ld, domain_index(Ld.nd, T.dx0 + j, T.dy, T.dz))[r] = rows[j * S + r];
+        }
+        __syncthreads();
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) unpack_rows_tiled_kernel(LatticeDesc Ld, int8_t *s8)
+{
+    constexpr int S = D * D + 2;
+    __shared__ __align__(16) uint16_t rows[kTileDomains * S];
+    const long long L = Ld.L, ntiles = (long long)Ld.nd * Ld.nd * ((Ld.nd + kTileDomains - 1) / kTileDomains);
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const BitTile T = bit_tile<D>(Ld, tile);
+        const long long site0 = tile_site0<D>(Ld, T);
+        for (int i = threadIdx.x; i < T.G * D * D; i += blockDim.x) {
+            const int j = i / (D * D), r = i % (D * D);
+            rows[j * S + r] = block_of<D>(Ld, domain_index(Ld.nd, T.dx0 + j, T.dy, T.dz))[r];
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < D * D * T.G; i += blockDim.x) {
+            const int r = i / T.G, j = i - r * T.G;
+            int8_t *dst = s8 + site0 + line_offset<D>(L, r) + (long long)j * D;
+            const uint32_t row = rows[j * S + r];
+            if constexpr (D == 16) {
+                __stcs(reinterpret_cast<uint4 *>(dst),
+                       make_uint4(spins4(row), spins4(row >> 4), spins4(row >> 8), spins4(row >> 12)));
+            } else {
+#pragma unroll
+                for (int x = 0; x < D; ++x) dst[x] = ((row >> x) & 1u) ? int8_t(1) : int8_t(-1);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // The same one thread per row or byte, for L % 8 != 0 (lines that do not
 // start on a byte, possible for D < 8).
 template <int D>
@@ -2141,6 +2230,12 @@ int launch_init_rows(const LatticeDesc &d, int init, void *stream)
 
 int launch_pack_rows(const LatticeDesc &d, const int8_t *dev_spins, void *stream)
 {
+    if (d.d != 16 || ((uintptr_t)dev_spins & 15) == 0) { // vector accesses at d = 16
+        const long long tiles = (long long)d.nd * d.nd * ((d.nd + kTileDomains - 1) / kTileDomains);
+        SPKMC_DISPATCH_D(d.d, pack_rows_tiled_kernel, (int)(tiles < 2048 ? tiles : 2048), 256, (cudaStream_t)stream, d,
+                         dev_spins);
+        return to_status(cudaGetLastError());
+    }
     const int grid = simple_grid(d.K * d.d * d.d, 256);
     SPKMC_DISPATCH_D(d.d, pack_rows_kernel, grid, 256, (cudaStream_t)stream, d, dev_spins);
     return to_status(cudaGetLastError());
@@ -2148,6 +2243,12 @@ int launch_pack_rows(const LatticeDesc &d, const int8_t *dev_spins, void *stream
 
 int launch_unpack_rows(const LatticeDesc &d, int8_t *dev_spins, void *stream)
 {
+    if (d.d != 16 || ((uintptr_t)dev_spins & 15) == 0) { // vector accesses at d = 16
+        const long long tiles = (long long)d.nd * d.nd * ((d.nd + kTileDomains - 1) / kTileDomains);
+        SPKMC_DISPATCH_D(d.d, unpack_rows_tiled_kernel, (int)(tiles < 2048 ? tiles : 2048), 256, (cudaStream_t)stream, d,
+                         dev_spins);
+        return to_status(cudaGetLastError());
+    }
     const int grid = simple_grid(d.K * d.d * d.d, 256);
     SPKMC_DISPATCH_D(d.d, unpack_rows_kernel, grid, 256, (cudaStream_t)stream, d, dev_spins);
     return to_status(cudaGetLastError());

@@ -361,6 +361,36 @@ def test_packed_spins_tiles(L, d, pinned):
         assert a.check_counts() == 0
 
 
+@pytest.mark.parametrize("L,d", [(80, 2), (12, 2), (160, 4), (288, 8), (544, 16), (96, 16)])
+@pytest.mark.parametrize("buf", ["pageable", "pinned", "pinned_unaligned"])
+def test_int8_spins_tiles(L, d, buf):
+    """int8 spins written and read back through the same tiles: any byte
+    value > 0 is +1 and any other -1; the read-out is +1 / -1.  Page-locked
+    buffers are used in place (at d = 16, one that is not 16-byte aligned
+    takes the per-row kernels)."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(L * d)
+    raw = rng.integers(-128, 128, size=L ** 3, dtype=np.int16).astype(np.int8)
+    want = np.where(raw > 0, 1, -1).astype(np.int8)
+    if buf == "pageable":
+        src, out = raw, np.empty_like(raw)
+    else:
+        off = 1 if buf == "pinned_unaligned" else 0
+        src = torch.empty(L ** 3 + off, dtype=torch.int8, pin_memory=True).numpy()[off:]
+        out = torch.empty(L ** 3 + off, dtype=torch.int8, pin_memory=True).numpy()[off:]
+        src[:] = raw
+    with gpu_lattice(wl.LatticeSpec(L=L, d=d, seed=67)) as a:
+        a.set_spins(src)
+        sp.spkmc_get_spins(a.h, out)
+        assert np.array_equal(out, want)
+        assert np.array_equal(a.spins_packed(), np.packbits(want > 0, bitorder="little"))
+        s = want.reshape(L, L, L)
+        B = sum(int(np.sum(s * np.roll(s, -1, axis=ax), dtype=np.int64)) for ax in range(3))
+        o = a.observables()
+        assert (o.M, o.B) == (int(np.sum(s, dtype=np.int64)), B)
+        assert a.check_counts() == 0
+
+
 @pytest.mark.parametrize("spec", [
     wl.LatticeSpec(L=4, d=2, seed=61),    # L^3 / 8 bytes cross x-lines
     wl.LatticeSpec(L=12, d=2, seed=62),   # L not a multiple of 8

@@ -532,7 +532,8 @@ def run_gpu(args, world, rank, local, pg):
         e2e = {"value": events / s_bits, "unit": "events/s",
                "h2d_bytes_per_step": n // 8 // args.steps,
                "d2h_bytes_per_step": n // 8 // args.steps + obs_bytes,
-               "spins": "one bit per site (spkmc_set_spins_packed / spkmc_get_spins_packed)",
+               "spins": "one bit per site (spkmc_set_spins_packed / spkmc_get_spins_packed), page-locked host "
+                        "buffers read and written in place by the transposing kernels",
                "int8_spins": {"value": events / s_int8, "h2d_bytes_per_step": n // args.steps,
                               "d2h_bytes_per_step": n // args.steps + obs_bytes}}
         lat2.close()

@@ -414,16 +414,15 @@ int upload_slot(spkmc_batch *b, int slot)
     return SPKMC_OK;
 }
 
-// Ghost faces, class counts and the exact M and B of a slot from its rows
-// (the last two in one pass).
+// Ghost faces, class counts and the exact M and B of a slot from its rows,
+// in one pass.
 int refresh_derived(spkmc_batch *b, int slot)
 {
     const LatticeDesc &d = b->slots[slot].desc;
     LatticeState *st = b->d_state + slot;
-    if (launch_ghosts(d, 0, nullptr, b->stream) != SPKMC_OK) return cuda_fail(cudaGetLastError(), "ghost faces");
     CUDA_TRY(cudaMemsetAsync(&st->M, 0, 2 * sizeof(long long), b->stream), "clear M, B");
-    if (launch_count_classes(d, 0, nullptr, &st->M, b->stream) != SPKMC_OK)
-        return cuda_fail(cudaGetLastError(), "class counts");
+    if (launch_refresh(d, &st->M, b->stream) != SPKMC_OK)
+        return cuda_fail(cudaGetLastError(), "ghost faces and class counts");
     return SPKMC_OK;
 }
 
@@ -1490,8 +1489,8 @@ extern "C" int spkmc_run_cycles_noalloc(const spkmc_params *p, int8_t *dev_spins
              "upload rate products");
     CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), s), "clear error flag");
     if ((rc = launch_pack_rows(D, dev_spins, s)) != SPKMC_OK) return cuda_fail(cudaGetLastError(), "pack spins");
-    if ((rc = launch_ghosts(D, 0, nullptr, s)) != SPKMC_OK) return cuda_fail(cudaGetLastError(), "ghost faces");
-    if ((rc = launch_count_classes(D, 0, nullptr, nullptr, s)) != SPKMC_OK) return cuda_fail(cudaGetLastError(), "class counts");
+    if ((rc = launch_refresh(D, nullptr, s)) != SPKMC_OK)
+        return cuda_fail(cudaGetLastError(), "ghost faces and class counts");
 
     // the cycles, in launches of at most 2^18 cycles, as spkmc_run_cycles
     const long long per_sm = g_noalloc_blocks_per_sm[dev];

@@ -154,6 +154,9 @@ int launch_ghosts(const LatticeDesc &d, int mode, unsigned long long *mismatch, 
 // pass; the ghost faces must be current.
 int launch_count_classes(const LatticeDesc &d, int mode, unsigned long long *mismatch, long long *MB,
                          void *stream);
+// Ghost faces from the rows, then class counts (and, with MB, M and B) in one
+// pass: one warp per domain.
+int launch_refresh(const LatticeDesc &d, long long *MB, void *stream);
 // M and B (device int64 pair, accumulated).
 int launch_obs_record(const LatticeState *st, int L, int d, double J, double H, spkmc_obs *out, void *stream);
 int launch_observables(const LatticeDesc &d, long long *MB, void *stream);

@@ -2059,17 +2059,33 @@ __global__ void ghosts_kernel(LatticeDesc Ld, int mode, unsigned long long *mism
 
 // With MB (mode 0), M and B of Eq. 1 / Eq. 4 in the same pass: +x bonds
 // inside each row and against the +x ghost, +y and +z bonds against the next
-// row or the ghost faces (which must be current).
+// row or the ghost faces.  With ghosts (mode 0), the warp first forms the
+// domain's ghost faces from the neighbours' rows and writes them out, and
+// classifies from a copy of the block in shared memory; otherwise the ghost
+// faces must be current.
 template <int D>
 __global__ void __launch_bounds__(256) count_classes_kernel(LatticeDesc Ld, int mode,
-                                                            unsigned long long *mismatch, long long *MB)
+                                                            unsigned long long *mismatch, long long *MB, int ghosts)
 {
+    __shared__ __align__(16) uint16_t staged[8][block_words(D)];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr uint32_t V = ((1u << D) - 1u) << 1;
     unsigned long long bad = 0;
     long long M = 0, B = 0;
     for (long long k = blockIdx.x * 8LL + warp; k < Ld.K; k += gridDim.x * 8LL) {
         const uint16_t *blk = block_of<D>(Ld, k);
+        if (ghosts) {
+            uint16_t *own = block_of<D>(Ld, k), *sb = staged[warp];
+            for (int i = lane; i < D * D / 2; i += 32)
+                reinterpret_cast<uint32_t *>(sb)[i] = reinterpret_cast<const uint32_t *>(own)[i];
+            for (int i = lane; i < 6 * D; i += 32) {
+                const uint16_t w = (uint16_t)ghost_word<D>(Ld, k, i / D, i % D);
+                own[D * D + i] = w;
+                sb[D * D + i] = w;
+            }
+            __syncwarp();
+            blk = sb;
+        }
         const uint16_t *gh = blk + D * D;
         int cnt[kClasses];
 #pragma unroll
@@ -2113,6 +2129,7 @@ __global__ void __launch_bounds__(256) count_classes_kernel(LatticeDesc Ld, int 
             M += __reduce_add_sync(kFull, m);
             B += __reduce_add_sync(kFull, b);
         }
+        __syncwarp(); // the staged block is read before the next is written
     }
     if (mode == 1 && lane == 0 && bad) atomicAdd(mismatch, bad);
     if (MB && lane == 0 && (M || B)) {
@@ -2291,7 +2308,14 @@ int launch_ghosts(const LatticeDesc &d, int mode, unsigned long long *mismatch, 
 int launch_count_classes(const LatticeDesc &d, int mode, unsigned long long *mismatch, long long *MB, void *stream)
 {
     const int grid = simple_grid(d.K, 8);
-    SPKMC_DISPATCH_D(d.d, count_classes_kernel, grid, 256, (cudaStream_t)stream, d, mode, mismatch, MB);
+    SPKMC_DISPATCH_D(d.d, count_classes_kernel, grid, 256, (cudaStream_t)stream, d, mode, mismatch, MB, 0);
+    return to_status(cudaGetLastError());
+}
+
+int launch_refresh(const LatticeDesc &d, long long *MB, void *stream)
+{
+    const int grid = simple_grid(d.K, 8);
+    SPKMC_DISPATCH_D(d.d, count_classes_kernel, grid, 256, (cudaStream_t)stream, d, 0, nullptr, MB, 1);
     return to_status(cudaGetLastError());
 }
 

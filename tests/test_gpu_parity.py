@@ -361,6 +361,38 @@ def test_packed_spins_tiles(L, d, pinned):
         assert a.check_counts() == 0
 
 
+def test_transfers_at_the_benchmark_size():
+    """1024^3, d = 16, through page-locked buffers read and written in place:
+    random packed spins come back unchanged, packed and as int8; the refresh
+    that follows the write leaves counts, ghost faces and M, B as the
+    device's independent recount finds them, and M is 2 (ones) - L^3."""
+    torch = pytest.importorskip("torch")
+    L = 1024
+    n = L ** 3
+    rng = np.random.default_rng(1024)
+    bits = torch.empty(n // 8, dtype=torch.uint8, pin_memory=True).numpy()
+    bits[:] = rng.integers(0, 256, size=n // 8, dtype=np.uint8)
+    out = torch.empty(n // 8, dtype=torch.uint8, pin_memory=True).numpy()
+    s8 = torch.empty(n, dtype=torch.int8, pin_memory=True).numpy()
+    with gpu_lattice(wl.LatticeSpec(L=L, d=16, seed=68, cold=True)) as a:
+        a.set_spins_packed(bits)
+        assert a.check_counts() == 0
+        ones = int(np.unpackbits(bits).sum(dtype=np.int64))
+        assert a.observables().M == 2 * ones - n
+        a.spins_packed(out)
+        assert np.array_equal(out, bits)
+        sp.spkmc_get_spins(a.h, s8)
+        assert np.array_equal(np.packbits(s8 > 0, bitorder="little"), bits)
+        a.run(20)
+        a.spins_packed(out)
+        sp.spkmc_get_spins(a.h, s8)
+        assert np.array_equal(np.packbits(s8 > 0, bitorder="little"), out)
+        a.set_spins(s8)  # int8 in place: the same lattice again
+        assert a.check_counts() == 0
+        a.spins_packed(bits)
+        assert np.array_equal(bits, out)
+
+
 @pytest.mark.parametrize("L,d", [(80, 2), (12, 2), (160, 4), (288, 8), (544, 16), (96, 16)])
 @pytest.mark.parametrize("buf", ["pageable", "pinned", "pinned_unaligned"])
 def test_int8_spins_tiles(L, d, buf):

@@ -1,0 +1,54 @@
+"""Host logic of bench.py's roofline (no GPU): the algorithmic bytes per
+event, and the DRAM traffic taken from a committed ncu capture only while the
+kernel sources are the ones it was taken on, scaled to the launch's cycles."""
+import json
+import os
+
+import bench
+
+
+def test_bytes_per_event():
+    # 14 int32 class counts plus the bit-packed block with its one-site halo
+    assert bench.bytes_per_event(16) == 14 * 4 + (16 ** 3 + 6 * 16 ** 2) // 8 == 760
+    assert bench.bytes_per_event(8) == 56 + (512 + 384) // 8
+    # the int8 layout that the bit-packed one is compared with
+    assert bench.int8_bytes_per_event(16) == 5632
+
+
+def _write_traffic(root, entry):
+    os.makedirs(os.path.join(root, "profiles"))
+    with open(os.path.join(root, "profiles", "traffic.json"), "w") as f:
+        json.dump({"spkmc-1024^3-d16": entry}, f)
+
+
+def test_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
+    h = bench.kernel_source_hash()
+    assert len(h) == 16
+    root = str(tmp_path)
+    _write_traffic(root, {"kernel_source_hash": h, "dram_bytes_per_launch": 1000, "cycles_per_launch": 500})
+    monkeypatch.setattr(bench, "ROOT", root)
+    # the hash is still taken from the package sources, the capture from root
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: h)
+    assert bench.ncu_traffic("spkmc-1024^3-d16", 500) == 1000
+    assert bench.ncu_traffic("spkmc-1024^3-d16", 250) == 500  # scaled by the cycles
+    assert bench.ncu_traffic("spkmc-1024^3-d16", 1000) == 2000
+    assert bench.ncu_traffic("another-workload", 500) is None
+    # a capture of other kernel sources is not reported
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
+    assert bench.ncu_traffic("spkmc-1024^3-d16", 500) is None
+
+
+def test_traffic_without_a_capture(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.ncu_traffic("spkmc-1024^3-d16", 500) is None
+
+
+def test_kernel_source_hash_changes_with_the_sources(tmp_path, monkeypatch):
+    csrc = tmp_path / "paper_1005_4713_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "spkmc_kernels.cu").write_text("a")
+    (csrc / "spkmc_internal.h").write_text("b")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h1 = bench.kernel_source_hash()
+    (csrc / "spkmc_kernels.cu").write_text("a ")
+    assert bench.kernel_source_hash() != h1

@@ -194,8 +194,10 @@ def barrier(pg, device=None):
 
 
 def kernel_source_hash() -> str:
+    """Hash of the sources the cycle kernel is compiled from (its translation
+    unit and the headers it includes)."""
     h = hashlib.sha256()
-    for f in ("spkmc_kernels.cu", "spkmc_internal.h"):
+    for f in ("spkmc_kernels.cu", "spkmc_device.cuh", "spkmc_internal.h"):
         with open(os.path.join(ROOT, "paper_1005_4713_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

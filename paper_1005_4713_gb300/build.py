@@ -1,7 +1,8 @@
 """In-tree build of libspkmc.so for sm_103a (GB300) with nvcc.
 
-Two translation units (kernels and host runtime) are compiled in parallel and
-linked into ``paper_1005_4713_gb300/libspkmc.so``.  Device FP64 arithmetic is
+Three translation units (the cycle kernel, the set-up and read-out kernels,
+and the host runtime) are compiled in parallel and linked into
+``paper_1005_4713_gb300/libspkmc.so``.  Device FP64 arithmetic is
 compiled without fused multiply-add (``-fmad=false``) and host code with
 ``-ffp-contract=off``, so that the frequency lines are summed exactly as
 written.
@@ -17,8 +18,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libspkmc.so")
-SOURCES = ["spkmc_kernels.cu", "spkmc_api.cu"]
-HEADERS = ["spkmc_internal.h", os.path.join("..", "..", "include", "spkmc.h")]
+SOURCES = ["spkmc_kernels.cu", "spkmc_setup_kernels.cu", "spkmc_api.cu"]
+HEADERS = ["spkmc_internal.h", "spkmc_device.cuh", os.path.join("..", "..", "include", "spkmc.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC,-ffp-contract=off",
               "-I", os.path.join(ROOT, "include")]

@@ -47,8 +47,17 @@ def test_kernel_source_hash_changes_with_the_sources(tmp_path, monkeypatch):
     csrc = tmp_path / "paper_1005_4713_gb300" / "csrc"
     csrc.mkdir(parents=True)
     (csrc / "spkmc_kernels.cu").write_text("a")
+    (csrc / "spkmc_device.cuh").write_text("c")
     (csrc / "spkmc_internal.h").write_text("b")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     h1 = bench.kernel_source_hash()
     (csrc / "spkmc_kernels.cu").write_text("a ")
-    assert bench.kernel_source_hash() != h1
+    h2 = bench.kernel_source_hash()
+    assert h2 != h1
+    (csrc / "spkmc_device.cuh").write_text("c ")  # a header the cycle kernel includes
+    assert bench.kernel_source_hash() not in (h1, h2)
+    # the set-up kernels are another translation unit: not part of the hash
+    (csrc / "spkmc_setup_kernels.cu").write_text("d")
+    h3 = bench.kernel_source_hash()
+    (csrc / "spkmc_setup_kernels.cu").write_text("d ")
+    assert bench.kernel_source_hash() == h3

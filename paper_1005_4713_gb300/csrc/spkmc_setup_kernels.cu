@@ -387,6 +387,15 @@ __global__ void ghosts_kernel(LatticeDesc Ld, int mode, unsigned long long *mism
     if (mode == 1 && bad) atomicAdd(mismatch, bad);
 }
 
+// Sites 0..D-1 of two row words in the classify_row layout (site x at bit
+// x + 1), side by side: the first row at bits 0..D-1, the second at 16..16+D-1.
+template <int D>
+__device__ __forceinline__ uint32_t pair_bits(uint32_t a, uint32_t b)
+{
+    constexpr uint32_t M = (1u << D) - 1u;
+    return ((a >> 1) & M) | (((b >> 1) & M) << 16);
+}
+
 // With MB (mode 0), M and B of Eq. 1 / Eq. 4 in the same pass: +x bonds
 // inside each row and against the +x ghost, +y and +z bonds against the next
 // row or the ghost faces.  With ghosts (mode 0), the warp first forms the
@@ -421,27 +430,33 @@ __global__ void __launch_bounds__(256) count_classes_kernel(LatticeDesc Ld, int 
 #pragma unroll
         for (int c = 0; c < kClasses; ++c) cnt[c] = 0;
         int m = 0, b = 0;
-        for (int r = lane; r < D * D; r += 32) {
-            const RowPlanes p = classify_row<D>(blk, r % D, r / D);
-            if (MB) {
-                const int y = r % D, z = r / D;
-                const uint32_t s = p.s; // bit x + 1 is spin x, x in [-1, D]
-                const uint32_t yp = (uint32_t)(y < D - 1 ? blk[r + 1] : gh[3 * D + z]) << 1;
-                const uint32_t zp = (uint32_t)(z < D - 1 ? blk[r + D] : gh[5 * D + y]) << 1;
-                m += 2 * __popc(s & V) - D;
-                b += 2 * __popc(~(s ^ (s >> 1)) & V) - D;
-                b += 2 * __popc(~(s ^ yp) & V) - D;
-                b += 2 * __popc(~(s ^ zp) & V) - D;
+        // rows (y, z) and (y + 1, z), y even, side by side in one word (sites
+        // at bits 0..D-1 and 16..16+D-1), so that each mask is counted once
+        // for both
+        for (int q = lane; q < D * D / 2; q += 32) {
+            const int r = 2 * q, y = r % D, z = r / D;
+            const RowPlanes p0 = classify_row<D>(blk, y, z), p1 = classify_row<D>(blk, y + 1, z);
+            const uint32_t s = pair_bits<D>(p0.s, p1.s);
+            if (MB) { // bit x + 1 of p.s is spin x, x in [-1, D]
+                const uint32_t yp1 = (uint32_t)(y + 1 < D - 1 ? blk[r + 2] : gh[3 * D + z]) << 1;
+                const uint32_t zp0 = (uint32_t)(z < D - 1 ? blk[r + D] : gh[5 * D + y]) << 1;
+                const uint32_t zp1 = (uint32_t)(z < D - 1 ? blk[r + 1 + D] : gh[5 * D + y + 1]) << 1;
+                m += 2 * __popc(s) - 2 * D;
+                b += 2 * __popc(pair_bits<D>(~(p0.s ^ (p0.s >> 1)), ~(p1.s ^ (p1.s >> 1)))) - 2 * D; // +x
+                b += 2 * __popc(pair_bits<D>(~(p0.s ^ p1.s), ~(p1.s ^ yp1))) - 2 * D;                 // +y
+                b += 2 * __popc(pair_bits<D>(~(p0.s ^ zp0), ~(p1.s ^ zp1))) - 2 * D;                // +z
             }
-            const int inc_low = (r < D * D / 2) ? (1 << 16) : 0; // lower half: z < D/2
+            const uint32_t u0 = pair_bits<D>(p0.u0, p1.u0), u1 = pair_bits<D>(p0.u1, p1.u1),
+                           u2 = pair_bits<D>(p0.u2, p1.u2);
+            const int inc = 1 + ((r < D * D / 2) ? (1 << 16) : 0); // lower half: z < D/2
 #pragma unroll
             for (int u = 0; u < 7; ++u) {
-                uint32_t e = V;
-                e &= (u & 1) ? p.u0 : ~p.u0;
-                e &= (u & 2) ? p.u1 : ~p.u1;
-                e &= (u & 4) ? p.u2 : ~p.u2;
-                cnt[7 + u] += __popc(e & p.s) * (1 + inc_low);
-                cnt[u] += __popc(e & ~p.s) * (1 + inc_low);
+                uint32_t e = (u & 1) ? u0 : ~u0;
+                e &= (u & 2) ? u1 : ~u1;
+                e &= (u & 4) ? u2 : ~u2;
+                const int up = __popc(e & s), all = __popc(e & pair_bits<D>(~0u, ~0u));
+                cnt[7 + u] += up * inc;
+                cnt[u] += (all - up) * inc;
             }
         }
         int differs = 0;

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libspkmc.so")
 SOURCES = ["spkmc_kernels.cu", "spkmc_setup_kernels.cu", "spkmc_api.cu"]
-HEADERS = ["spkmc_internal.h", "spkmc_device.cuh", os.path.join("..", "..", "include", "spkmc.h")]
+HEADERS = ["spkmc_internal.h", "spkmc_device.cuh", "spkmc_setup.h", os.path.join("..", "..", "include", "spkmc.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC,-ffp-contract=off",
               "-I", os.path.join(ROOT, "include")]

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "spkmc_internal.h"
+#include "spkmc_setup.h"
 
 using namespace spkmc;
 
@@ -249,6 +250,11 @@ struct spkmc_batch {
     bool phase_unknown = false; // launches being captured for replays at other t % 4
     std::vector<Segment> uploaded_seg; // segment table currently on the device
     long long live_bytes = 0;
+    // second stream and events of the layer-pipelined spin write (made on
+    // first use)
+    static constexpr int kWriteSlabs = 16;
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev[kWriteSlabs + 1] = {};
 
     void *dev_alloc(size_t bytes)
     {
@@ -314,6 +320,12 @@ void release_batch(spkmc_batch *b)
     cudaFreeHost(b->h_err);
     cudaFreeHost(b->h_MB);
     if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->aux) {
+        cudaStreamSynchronize(b->aux);
+        cudaStreamDestroy(b->aux);
+    }
+    for (cudaEvent_t e : b->ev)
+        if (e) cudaEventDestroy(e);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -747,6 +759,53 @@ int get_spins(spkmc_batch *b, int slot, void *host, size_t n, bool packed = fals
     return SPKMC_OK;
 }
 
+// Rows from host-order spins at src (device-accessible) and the refresh of
+// ghost faces, class counts and M, B.  Where the tiled pack applies and the
+// lattice has at least 8 domain layers, the layers go in S = 8 or 16 slabs,
+// packed on the batch stream in the order 0, S-1, 1, 2, ..., S-2, while a
+// second stream refreshes each slab as soon as it and its two z neighbours
+// (periodic) are in place: slab 0 after the third pack, slab j after the pack
+// of slab j + 1, and slabs S-2 and S-1 after the last.  The transfer of the
+// spins (a host-link-bound read when src is mapped host memory) thus
+// overlaps most of the refresh (bound by integer arithmetic).
+int write_rows(spkmc_batch *b, int slot, const void *src, bool packed)
+{
+    const LatticeDesc &d = b->slots[slot].desc;
+    LatticeState *st = b->d_state + slot;
+    const int S = d.nd >= spkmc_batch::kWriteSlabs ? spkmc_batch::kWriteSlabs : 8;
+    if (d.nd < 8 || !pack_is_tiled(d, src, packed)) {
+        const int rc = packed ? launch_pack_bits(d, (const uint8_t *)src, b->stream)
+                              : launch_pack_rows(d, (const int8_t *)src, b->stream);
+        if (rc) return cuda_fail(cudaGetLastError(), "write rows");
+        return refresh_derived(b, slot);
+    }
+    if (!b->aux) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking), "create stream");
+        for (cudaEvent_t &e : b->ev) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "create event");
+    }
+    auto z = [&](int i) { return (int)((long long)d.nd * i / S); };
+    CUDA_TRY(cudaMemsetAsync(&st->M, 0, 2 * sizeof(long long), b->stream), "clear M, B");
+    for (int q = 0; q < S; ++q) {
+        const int i = q == 0 ? 0 : (q == 1 ? S - 1 : q - 1); // the slab packed q-th
+        // a few CTAs per SM: the refresh of earlier slabs shares the GPU
+        if (launch_pack_layers(d, src, packed, z(i), z(i + 1), 4 * (b->sm_count > 0 ? b->sm_count : 152), b->stream))
+            return cuda_fail(cudaGetLastError(), "write rows");
+        CUDA_TRY(cudaEventRecord(b->ev[q], b->stream), "record event");
+        if (q >= 2) { // slab 0 (q = 2), else slab q - 2: its neighbours are packed
+            CUDA_TRY(cudaStreamWaitEvent(b->aux, b->ev[q], 0), "wait event");
+            const int j = q == 2 ? 0 : q - 2;
+            if (launch_refresh_layers(d, &st->M, z(j), z(j + 1), b->aux))
+                return cuda_fail(cudaGetLastError(), "ghost faces and class counts");
+        }
+    }
+    // slabs S-2 and S-1 (the aux stream has waited for the last pack)
+    if (launch_refresh_layers(d, &st->M, z(S - 2), z(S), b->aux))
+        return cuda_fail(cudaGetLastError(), "ghost faces and class counts");
+    CUDA_TRY(cudaEventRecord(b->ev[spkmc_batch::kWriteSlabs], b->aux), "record event");
+    CUDA_TRY(cudaStreamWaitEvent(b->stream, b->ev[spkmc_batch::kWriteSlabs], 0), "wait event");
+    return SPKMC_OK;
+}
+
 int set_spins(spkmc_batch *b, int slot, const void *host, size_t n, bool packed = false)
 {
     int rc = slot_check(b, slot);
@@ -764,9 +823,7 @@ int set_spins(spkmc_batch *b, int slot, const void *host, size_t n, bool packed 
     if (e == cudaSuccess) // the R_max history described the old spins
         e = cudaMemsetAsync(b->d_state[slot].rmax, 0, sizeof(b->d_state[slot].rmax), b->stream);
     if (e == cudaSuccess) {
-        rc = packed ? launch_pack_bits(s.desc, (const uint8_t *)(direct ? direct : tmp), b->stream)
-                    : launch_pack_rows(s.desc, (const int8_t *)(direct ? direct : tmp), b->stream);
-        if (!rc) rc = refresh_derived(b, slot);
+        rc = write_rows(b, slot, direct ? direct : tmp, packed);
         if (rc) e = cudaGetLastError();
     }
     cudaError_t e2 = cudaStreamSynchronize(b->stream);

@@ -4,6 +4,7 @@
 // rows, the ghost faces, the 14 class counts of Sec. 3.1 step 1 and the
 // exact M and B (Eq. 1, Eq. 4), built or checked.
 #include "spkmc_device.cuh"
+#include "spkmc_setup.h"
 
 namespace spkmc {
 
@@ -114,13 +115,14 @@ __device__ __forceinline__ long long seg_offset(long long L, int r)
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) pack_bits_tiled_kernel(LatticeDesc Ld, const uint8_t *bits)
+__global__ void __launch_bounds__(256) pack_bits_tiled_kernel(LatticeDesc Ld, const uint8_t *bits, long long t0,
+                                                              long long t1)
 {
     constexpr int S = tile_line_stride<D>();
     __shared__ __align__(16) uint8_t seg[D * D * S];
-    const long long L = Ld.L, ntiles = (long long)Ld.nd * Ld.nd * ((Ld.nd + kTileDomains - 1) / kTileDomains);
+    const long long L = Ld.L;
     const bool wide = L % 32 == 0;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (long long tile = t0 + blockIdx.x; tile < t1; tile += gridDim.x) {
         const BitTile T = bit_tile<D>(Ld, tile);
         if (wide) {
             const int nw = T.nb / 4;
@@ -220,12 +222,13 @@ __device__ __forceinline__ uint32_t spins4(uint32_t b)
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) pack_rows_tiled_kernel(LatticeDesc Ld, const int8_t *s8)
+__global__ void __launch_bounds__(256) pack_rows_tiled_kernel(LatticeDesc Ld, const int8_t *s8, long long t0,
+                                                              long long t1)
 {
     constexpr int S = D * D + 2;
     __shared__ __align__(16) uint16_t rows[kTileDomains * S];
-    const long long L = Ld.L, ntiles = (long long)Ld.nd * Ld.nd * ((Ld.nd + kTileDomains - 1) / kTileDomains);
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long L = Ld.L;
+    for (long long tile = t0 + blockIdx.x; tile < t1; tile += gridDim.x) {
         const BitTile T = bit_tile<D>(Ld, tile);
         const long long site0 = tile_site0<D>(Ld, T);
         for (int i = threadIdx.x; i < D * D * T.G; i += blockDim.x) {
@@ -404,14 +407,15 @@ __device__ __forceinline__ uint32_t pair_bits(uint32_t a, uint32_t b)
 // faces must be current.
 template <int D>
 __global__ void __launch_bounds__(256) count_classes_kernel(LatticeDesc Ld, int mode,
-                                                            unsigned long long *mismatch, long long *MB, int ghosts)
+                                                            unsigned long long *mismatch, long long *MB, int ghosts,
+                                                            long long k0, long long k1)
 {
     __shared__ __align__(16) uint16_t staged[8][block_words(D)];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr uint32_t V = ((1u << D) - 1u) << 1;
     unsigned long long bad = 0;
     long long M = 0, B = 0;
-    for (long long k = blockIdx.x * 8LL + warp; k < Ld.K; k += gridDim.x * 8LL) {
+    for (long long k = k0 + blockIdx.x * 8LL + warp; k < k1; k += gridDim.x * 8LL) {
         const uint16_t *blk = block_of<D>(Ld, k);
         if (ghosts) {
             uint16_t *own = block_of<D>(Ld, k), *sb = staged[warp];
@@ -535,14 +539,43 @@ int launch_init_rows(const LatticeDesc &d, int init, void *stream)
     return to_status(cudaGetLastError());
 }
 
+// Tiles of domain layers [z0, z1) (tiles run with dz slowest), and the grid
+// for them: at most `cap` CTAs.
+inline void layer_tiles(const LatticeDesc &d, int z0, int z1, long long &t0, long long &t1)
+{
+    const long long per_layer = (long long)d.nd * ((d.nd + kTileDomains - 1) / kTileDomains);
+    t0 = z0 * per_layer;
+    t1 = z1 * per_layer;
+}
+
+inline int tile_grid(long long tiles, int cap)
+{
+    return (int)(tiles < cap ? (tiles > 0 ? tiles : 1) : cap);
+}
+
+bool pack_is_tiled(const LatticeDesc &d, const void *src, bool packed)
+{
+    return packed ? d.L % 8 == 0 : (d.d != 16 || ((uintptr_t)src & 15) == 0);
+}
+
+int launch_pack_layers(const LatticeDesc &d, const void *src, bool packed, int z0, int z1, int cap, void *stream)
+{
+    if (!pack_is_tiled(d, src, packed) || z0 < 0 || z1 > d.nd || z0 >= z1) return SPKMC_EINVAL;
+    long long t0, t1;
+    layer_tiles(d, z0, z1, t0, t1);
+    const int grid = tile_grid(t1 - t0, cap);
+    if (packed)
+        SPKMC_DISPATCH_D(d.d, pack_bits_tiled_kernel, grid, 256, (cudaStream_t)stream, d, (const uint8_t *)src, t0,
+                         t1);
+    else
+        SPKMC_DISPATCH_D(d.d, pack_rows_tiled_kernel, grid, 256, (cudaStream_t)stream, d, (const int8_t *)src, t0, t1);
+    return to_status(cudaGetLastError());
+}
+
 int launch_pack_rows(const LatticeDesc &d, const int8_t *dev_spins, void *stream)
 {
-    if (d.d != 16 || ((uintptr_t)dev_spins & 15) == 0) { // vector accesses at d = 16
-        const long long tiles = (long long)d.nd * d.nd * ((d.nd + kTileDomains - 1) / kTileDomains);
-        SPKMC_DISPATCH_D(d.d, pack_rows_tiled_kernel, (int)(tiles < 2048 ? tiles : 2048), 256, (cudaStream_t)stream, d,
-                         dev_spins);
-        return to_status(cudaGetLastError());
-    }
+    if (pack_is_tiled(d, dev_spins, false)) // vector accesses at d = 16 need 16-byte alignment
+        return launch_pack_layers(d, dev_spins, false, 0, d.nd, 2048, stream);
     const int grid = simple_grid(d.K * d.d * d.d, 256);
     SPKMC_DISPATCH_D(d.d, pack_rows_kernel, grid, 256, (cudaStream_t)stream, d, dev_spins);
     return to_status(cudaGetLastError());
@@ -563,12 +596,7 @@ int launch_unpack_rows(const LatticeDesc &d, int8_t *dev_spins, void *stream)
 
 int launch_pack_bits(const LatticeDesc &d, const uint8_t *dev_bits, void *stream)
 {
-    if (d.L % 8 == 0) {
-        const long long tiles = (long long)d.nd * d.nd * ((d.nd + kTileDomains - 1) / kTileDomains);
-        SPKMC_DISPATCH_D(d.d, pack_bits_tiled_kernel, (int)(tiles < 2048 ? tiles : 2048), 256, (cudaStream_t)stream, d,
-                         dev_bits);
-        return to_status(cudaGetLastError());
-    }
+    if (pack_is_tiled(d, dev_bits, true)) return launch_pack_layers(d, dev_bits, true, 0, d.nd, 2048, stream);
     const int grid = simple_grid(d.K * d.d * d.d, 256);
     SPKMC_DISPATCH_D(d.d, pack_bits_kernel, grid, 256, (cudaStream_t)stream, d, dev_bits);
     return to_status(cudaGetLastError());
@@ -598,14 +626,21 @@ int launch_ghosts(const LatticeDesc &d, int mode, unsigned long long *mismatch, 
 int launch_count_classes(const LatticeDesc &d, int mode, unsigned long long *mismatch, long long *MB, void *stream)
 {
     const int grid = simple_grid(d.K, 8);
-    SPKMC_DISPATCH_D(d.d, count_classes_kernel, grid, 256, (cudaStream_t)stream, d, mode, mismatch, MB, 0);
+    SPKMC_DISPATCH_D(d.d, count_classes_kernel, grid, 256, (cudaStream_t)stream, d, mode, mismatch, MB, 0, 0LL, d.K);
     return to_status(cudaGetLastError());
 }
 
 int launch_refresh(const LatticeDesc &d, long long *MB, void *stream)
 {
-    const int grid = simple_grid(d.K, 8);
-    SPKMC_DISPATCH_D(d.d, count_classes_kernel, grid, 256, (cudaStream_t)stream, d, 0, nullptr, MB, 1);
+    return launch_refresh_layers(d, MB, 0, d.nd, stream);
+}
+
+int launch_refresh_layers(const LatticeDesc &d, long long *MB, int z0, int z1, void *stream)
+{
+    if (z0 < 0 || z1 > d.nd || z0 >= z1) return SPKMC_EINVAL;
+    const long long layer = (long long)d.nd * d.nd, k0 = z0 * layer, k1 = z1 * layer;
+    const int grid = simple_grid(k1 - k0, 8);
+    SPKMC_DISPATCH_D(d.d, count_classes_kernel, grid, 256, (cudaStream_t)stream, d, 0, nullptr, MB, 1, k0, k1);
     return to_status(cudaGetLastError());
 }
 

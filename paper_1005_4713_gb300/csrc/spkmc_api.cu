@@ -779,9 +779,20 @@ int write_rows(spkmc_batch *b, int slot, const void *src, bool packed)
         if (rc) return cuda_fail(cudaGetLastError(), "write rows");
         return refresh_derived(b, slot);
     }
-    if (!b->aux) {
-        CUDA_TRY(cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking), "create stream");
-        for (cudaEvent_t &e : b->ev) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "create event");
+    if (!b->aux) { // all or nothing
+        cudaStream_t aux = nullptr;
+        cudaEvent_t ev[spkmc_batch::kWriteSlabs + 1] = {};
+        cudaError_t e = cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking);
+        for (int i = 0; e == cudaSuccess && i <= spkmc_batch::kWriteSlabs; ++i)
+            e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            for (cudaEvent_t x : ev)
+                if (x) cudaEventDestroy(x);
+            if (aux) cudaStreamDestroy(aux);
+            return cuda_fail(e, "create stream and events");
+        }
+        b->aux = aux;
+        for (int i = 0; i <= spkmc_batch::kWriteSlabs; ++i) b->ev[i] = ev[i];
     }
     auto z = [&](int i) { return (int)((long long)d.nd * i / S); };
     CUDA_TRY(cudaMemsetAsync(&st->M, 0, 2 * sizeof(long long), b->stream), "clear M, B");

@@ -332,6 +332,9 @@ def test_graph_arguments_are_checked():
     (288, 8),
     (544, 16),  # nd = 34: the second tile two domains wide
     (64, 2),    # nd = 32: one full tile
+    (640, 16),  # 16-byte lines (L % 128 == 0), the second tile 8 domains wide
+    (384, 4),   # 16-byte lines, three full tiles
+    (256, 2),   # L % 128 == 0 but 8-byte segments: word lines
 ])
 @pytest.mark.parametrize("pinned", [False, True])
 def test_packed_spins_tiles(L, d, pinned):

@@ -114,14 +114,6 @@ __device__ __forceinline__ long long seg_offset(long long L, int r)
     return ((long long)(r / D) * L + (r % D)) * (L / 8);
 }
 
-// Whether a tile's segments move as 16-byte vectors: every line starts on 16
-// bytes (L % 128 == 0) in a 16-byte-aligned buffer, and so do the tile's
-// first segment and its length.
-__device__ __forceinline__ bool vec16(const LatticeDesc &Ld, const BitTile &T, const void *bits)
-{
-    return Ld.L % 128 == 0 && ((uintptr_t)bits & 15) == 0 && (T.seg0 & 15) == 0 && (T.nb & 15) == 0;
-}
-
 template <int D>
 __global__ void __launch_bounds__(256) pack_bits_tiled_kernel(LatticeDesc Ld, const uint8_t *bits, long long t0,
                                                               long long t1)
@@ -132,18 +124,7 @@ __global__ void __launch_bounds__(256) pack_bits_tiled_kernel(LatticeDesc Ld, co
     const bool wide = L % 32 == 0;
     for (long long tile = t0 + blockIdx.x; tile < t1; tile += gridDim.x) {
         const BitTile T = bit_tile<D>(Ld, tile);
-        if (vec16(Ld, T, bits)) {
-            const int nq = T.nb / 16;
-            for (int i = threadIdx.x; i < D * D * nq; i += blockDim.x) {
-                const int r = i / nq, w = i - r * nq;
-                const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(bits + T.seg0 + seg_offset<D>(L, r)) + w);
-                uint32_t *dst = reinterpret_cast<uint32_t *>(seg + r * S + 16 * w);
-                dst[0] = v.x;
-                dst[1] = v.y;
-                dst[2] = v.z;
-                dst[3] = v.w;
-            }
-        } else if (wide) {
+        if (wide) {
             const int nw = T.nb / 4;
             for (int i = threadIdx.x; i < D * D * nw; i += blockDim.x) {
                 const int r = i / nw, w = i - r * nw;
@@ -199,15 +180,7 @@ __global__ void __launch_bounds__(256) unpack_bits_tiled_kernel(LatticeDesc Ld, 
             }
         }
         __syncthreads();
-        if (vec16(Ld, T, bits)) {
-            const int nq = T.nb / 16;
-            for (int i = threadIdx.x; i < D * D * nq; i += blockDim.x) {
-                const int r = i / nq, w = i - r * nq;
-                const uint32_t *src = reinterpret_cast<const uint32_t *>(seg + r * S + 16 * w);
-                __stcs(reinterpret_cast<uint4 *>(bits + T.seg0 + seg_offset<D>(L, r)) + w,
-                       make_uint4(src[0], src[1], src[2], src[3]));
-            }
-        } else if (wide) {
+        if (wide) {
             const int nw = T.nb / 4;
             for (int i = threadIdx.x; i < D * D * nw; i += blockDim.x) {
                 const int r = i / nw, w = i - r * nw;

@@ -406,7 +406,7 @@ __device__ __forceinline__ uint32_t pair_bits(uint32_t a, uint32_t b)
 // classifies from a copy of the block in shared memory; otherwise the ghost
 // faces must be current.
 template <int D>
-__global__ void __launch_bounds__(256) count_classes_kernel(LatticeDesc Ld, int mode,
+__global__ void __launch_bounds__(256, 5) count_classes_kernel(LatticeDesc Ld, int mode,
                                                             unsigned long long *mismatch, long long *MB, int ghosts,
                                                             long long k0, long long k1)
 {

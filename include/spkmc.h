@@ -346,7 +346,8 @@ int spkmc_batch_usage(spkmc_batch_t *b, int32_t *live_slots, int64_t *device_byt
  *   p          physics of the lattice (L, domain_edge, J, H, T, seed); init
  *              is ignored and event_log_capacity must be 0;
  *   dev_spins  device buffer of L^3 int8 +1/-1 in global order (input), which
- *              receives the spins after the cycles (output);
+ *              receives the spins after the cycles (output); on any error
+ *              return it still holds its input, and state is unchanged;
  *   state      host struct: cycle, clock and counters before the call (input)
  *              and after it (output); start from all zeros;
  *   ncycles    cycles to run (>= 0);
@@ -356,9 +357,11 @@ int spkmc_batch_usage(spkmc_batch_t *b, int32_t *live_slots, int64_t *device_byt
  * the array: EINVAL (with the size in the message) for larger lattices, e.g.
  * 256^3 with d = 16 fits and 512^3 does not.  The call returns after the
  * work has finished.  No cudaMalloc, cudaFree or other allocating routine is
- * called.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the one array and it keeps
+ * called.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress) with the caller's current device, so the address
+ * is right again after the device's primary context was reset; the first
+ * call on a device also reads its SM count and the kernel's occupancy.  Make
+ * that first call before any stream capture.  Every call shares the one array and it keeps
  * the last call's contents (the call clears what must start at zero): calls
  * that overlap on the GPU, from any thread or stream, race with each other
  * and must be serialised by the caller. */

@@ -11,7 +11,9 @@ arrays.  Parity pins for every function are in ``tests/test_oracle_pins.py``.
 from __future__ import annotations
 
 import ctypes
+import hashlib
 import os
+import platform
 import subprocess
 import threading
 
@@ -31,17 +33,38 @@ _dbl = ctypes.c_double
 _ptr = ctypes.c_void_p
 
 
+_FLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared", "-std=c11"]
+
+
+def _digest() -> str:
+    """Hash of the oracle's source, its gcc flags and the host architecture."""
+    h = hashlib.sha256()
+    with open(_SRC, "rb") as f:
+        h.update(f.read())
+    h.update(" ".join(_FLAGS).encode())
+    h.update(platform.machine().encode())
+    return h.hexdigest()
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle shared library (gcc, -O2 -ffp-contract=off -fopenmp)."""
+    """Compile the oracle shared library (gcc, -O2 -ffp-contract=off -fopenmp),
+    unless the one in place was built from the current source and flags."""
     os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-        return _LIB
+    stamp = _LIB + ".sha256"
+    digest = _digest()
+    if not force and os.path.exists(_LIB) and os.path.exists(stamp):
+        with open(stamp) as f:
+            if f.read().strip() == digest:
+                return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-           "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"]
+    cmd = ["gcc", *_FLAGS, "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
+    if os.path.exists(stamp):
+        os.remove(stamp)
     os.replace(tmp, _LIB)
+    with open(stamp + f".tmp{os.getpid()}", "w") as f:
+        f.write(digest + "\n")
+    os.replace(stamp + f".tmp{os.getpid()}", stamp)
     return _LIB
 
 

@@ -9,7 +9,9 @@ written.
 """
 from __future__ import annotations
 
+import hashlib
 import os
+import platform
 import subprocess
 import sys
 import tempfile
@@ -18,6 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libspkmc.so")
+STAMP = LIB + ".sha256"  # hash of the sources, headers and flags the library was built from
 SOURCES = ["spkmc_kernels.cu", "spkmc_setup_kernels.cu", "spkmc_api.cu"]
 HEADERS = ["spkmc_internal.h", "spkmc_device.cuh", "spkmc_setup.h", os.path.join("..", "..", "include", "spkmc.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -32,18 +35,42 @@ def nvcc() -> str:
     return "nvcc"
 
 
+def source_hash() -> str:
+    """SHA-256 of everything the library is built from: the translation
+    units, the headers, the nvcc flags, the compiler path and the host
+    architecture (a library built on another machine type never matches)."""
+    h = hashlib.sha256()
+    for name in SOURCES + HEADERS:
+        path = os.path.normpath(os.path.join(CSRC, name))
+        h.update(name.encode() + b"\0")
+        with open(path, "rb") as f:
+            h.update(f.read())
+        h.update(b"\0")
+    h.update(" ".join(ARCH + NVCC_FLAGS).replace(ROOT, "<root>").encode())
+    h.update(nvcc().encode())
+    h.update(platform.machine().encode())
+    return h.hexdigest()
+
+
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    """A library is reused only when its stamp holds the hash of the current
+    sources and flags (a library copied from elsewhere, or built from other
+    sources, has none or another)."""
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
         return True
-    t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, h) for h in HEADERS]
-    return any(os.path.getmtime(p) > t for p in deps if os.path.exists(p))
+    try:
+        with open(STAMP) as f:
+            return f.read().strip() != source_hash()
+    except OSError:
+        return True
 
 
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile libspkmc.so if it is missing or older than its sources."""
+    """Compile libspkmc.so unless the one in place was built from exactly
+    the current sources and flags."""
     if not force and not _stale():
         return LIB
+    digest = source_hash()
     with tempfile.TemporaryDirectory(prefix="spkmc_build_") as tmp:
         procs = []
         objs = []
@@ -68,7 +95,14 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         tmp_lib = LIB + f".tmp{os.getpid()}"
         cmd = [nvcc(), *ARCH, "-shared", "-o", tmp_lib, *objs]
         subprocess.run(cmd, check=True)
+        # the stamp goes first: a library in place without a matching stamp is rebuilt
+        if os.path.exists(STAMP):
+            os.remove(STAMP)
         os.replace(tmp_lib, LIB)
+        tmp_stamp = STAMP + f".tmp{os.getpid()}"
+        with open(tmp_stamp, "w") as f:
+            f.write(digest + "\n")
+        os.replace(tmp_stamp, STAMP)
     return LIB
 
 

@@ -43,6 +43,14 @@ int cuda_fail(cudaError_t e, const char *what)
     return fail(SPKMC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// A launch helper's status as the calling entry point's: a CUDA error with its
+// message, or the helper's own code (EINVAL for a layout it refuses).
+int helper_fail(int rc, const char *what)
+{
+    return rc == SPKMC_ECUDA ? cuda_fail(cudaGetLastError(), what) : fail(rc, "%s refused the lattice", what);
+}
+
+
 #define CUDA_TRY(expr, what)                                                                       \
     do {                                                                                           \
         cudaError_t e_ = (expr);                                                                   \
@@ -776,7 +784,7 @@ int write_rows(spkmc_batch *b, int slot, const void *src, bool packed)
     if (d.nd < 8 || !pack_is_tiled(d, src, packed)) {
         const int rc = packed ? launch_pack_bits(d, (const uint8_t *)src, b->stream)
                               : launch_pack_rows(d, (const int8_t *)src, b->stream);
-        if (rc) return cuda_fail(cudaGetLastError(), "write rows");
+        if (rc) return helper_fail(rc, "write rows");
         return refresh_derived(b, slot);
     }
     if (!b->aux) { // all or nothing
@@ -799,19 +807,20 @@ int write_rows(spkmc_batch *b, int slot, const void *src, bool packed)
     for (int q = 0; q < S; ++q) {
         const int i = q == 0 ? 0 : (q == 1 ? S - 1 : q - 1); // the slab packed q-th
         // a few CTAs per SM: the refresh of earlier slabs shares the GPU
-        if (launch_pack_layers(d, src, packed, z(i), z(i + 1), 4 * (b->sm_count > 0 ? b->sm_count : 152), b->stream))
-            return cuda_fail(cudaGetLastError(), "write rows");
+        int rc = launch_pack_layers(d, src, packed, z(i), z(i + 1), 4 * (b->sm_count > 0 ? b->sm_count : 152),
+                                    b->stream);
+        if (rc) return helper_fail(rc, "write rows");
         CUDA_TRY(cudaEventRecord(b->ev[q], b->stream), "record event");
         if (q >= 2) { // slab 0 (q = 2), else slab q - 2: its neighbours are packed
             CUDA_TRY(cudaStreamWaitEvent(b->aux, b->ev[q], 0), "wait event");
             const int j = q == 2 ? 0 : q - 2;
-            if (launch_refresh_layers(d, &st->M, z(j), z(j + 1), b->aux))
-                return cuda_fail(cudaGetLastError(), "ghost faces and class counts");
+            if ((rc = launch_refresh_layers(d, &st->M, z(j), z(j + 1), b->aux)) != SPKMC_OK)
+                return helper_fail(rc, "ghost faces and class counts");
         }
     }
     // slabs S-2 and S-1 (the aux stream has waited for the last pack)
-    if (launch_refresh_layers(d, &st->M, z(S - 2), z(S), b->aux))
-        return cuda_fail(cudaGetLastError(), "ghost faces and class counts");
+    const int rc = launch_refresh_layers(d, &st->M, z(S - 2), z(S), b->aux);
+    if (rc) return helper_fail(rc, "ghost faces and class counts");
     CUDA_TRY(cudaEventRecord(b->ev[spkmc_batch::kWriteSlabs], b->aux), "record event");
     CUDA_TRY(cudaStreamWaitEvent(b->stream, b->ev[spkmc_batch::kWriteSlabs], 0), "wait event");
     return SPKMC_OK;
@@ -1452,30 +1461,31 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[SPKMC_NOALLOC_S
 
 constexpr int kNoallocMaxDevices = 64;
 std::mutex g_noalloc_mutex;
-unsigned char *g_noalloc_ptr[kNoallocMaxDevices] = {};
 int g_noalloc_blocks_per_sm[kNoallocMaxDevices] = {};
 int g_noalloc_sms[kNoallocMaxDevices] = {};
 
-// Device address of the array on the current device, looked up once per
-// device (a host-side use of the symbol itself is not a device address).
+// Device address of the array on the current device (a host-side use of
+// the symbol itself is not a device address).  It is looked up on every
+// call, so a device whose primary context was reset and created again gets
+// the address in its new context; the device's SM count and the cycle
+// kernel's occupancy are kept from the first call.
 int noalloc_base(int dev, unsigned char **out)
 {
     if (dev < 0 || dev >= kNoallocMaxDevices) return fail(SPKMC_EINVAL, "device ordinal %d out of range", dev);
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
-        void *ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess || !ptr) return cuda_fail(e, "cudaGetSymbolAddress of the no-allocation scratch");
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) return cuda_fail(e, "cudaGetSymbolAddress of the no-allocation scratch");
+    if (!g_noalloc_sms[dev]) {
         int sms = 0;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
             return cuda_fail(e, "device attributes");
         const int per = cycle_kernel_max_blocks_per_sm(dev);
         if (per < 1) return fail(SPKMC_ECUDA, "cycle kernel cannot be resident");
-        g_noalloc_ptr[dev] = static_cast<unsigned char *>(ptr);
-        g_noalloc_sms[dev] = sms;
         g_noalloc_blocks_per_sm[dev] = per;
+        g_noalloc_sms[dev] = sms;
     }
-    *out = g_noalloc_ptr[dev];
+    *out = static_cast<unsigned char *>(ptr);
     return SPKMC_OK;
 }
 
@@ -1556,9 +1566,8 @@ extern "C" int spkmc_run_cycles_noalloc(const spkmc_params *p, int8_t *dev_spins
     CUDA_TRY(cudaMemcpyAsync(const_cast<double *>(D.nrate), nrate.data(), nrate.size() * 8, cudaMemcpyHostToDevice, s),
              "upload rate products");
     CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), s), "clear error flag");
-    if ((rc = launch_pack_rows(D, dev_spins, s)) != SPKMC_OK) return cuda_fail(cudaGetLastError(), "pack spins");
-    if ((rc = launch_refresh(D, nullptr, s)) != SPKMC_OK)
-        return cuda_fail(cudaGetLastError(), "ghost faces and class counts");
+    if ((rc = launch_pack_rows(D, dev_spins, s)) != SPKMC_OK) return helper_fail(rc, "pack spins");
+    if ((rc = launch_refresh(D, nullptr, s)) != SPKMC_OK) return helper_fail(rc, "ghost faces and class counts");
 
     // the cycles, in launches of at most 2^18 cycles, as spkmc_run_cycles
     const long long per_sm = g_noalloc_blocks_per_sm[dev];
@@ -1586,12 +1595,13 @@ extern "C" int spkmc_run_cycles_noalloc(const spkmc_params *p, int8_t *dev_spins
         P.exact_any = p->rmax_mode == SPKMC_RMAX_EXACT;
         P.sub2_any = D.sub2;
         if (D.sub2) P.parity0 = -1;
-        if (launch_cycles(P, (int)grid, s, grid > 1) != SPKMC_OK)
-            return cuda_fail(cudaGetLastError(), "persistent cycle launch");
+        if ((rc = launch_cycles(P, (int)grid, s, grid > 1)) != SPKMC_OK) return helper_fail(rc, "persistent cycle launch");
         left -= n;
         t += n;
     }
-    if ((rc = launch_unpack_rows(D, dev_spins, s)) != SPKMC_OK) return cuda_fail(cudaGetLastError(), "unpack spins");
+    // the unpack reads the error flag on the device and writes nothing after
+    // a failed launch, so dev_spins keeps its input on every error return
+    if ((rc = launch_unpack_rows(D, dev_spins, s, d_err)) != SPKMC_OK) return helper_fail(rc, "unpack spins");
     int err = 0;
     CUDA_TRY(cudaMemcpyAsync(&st, d_state, sizeof(st), cudaMemcpyDeviceToHost, s), "read state");
     CUDA_TRY(cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s), "read error flag");

@@ -141,7 +141,9 @@ int cycle_kernel_max_blocks_per_sm(int device);
 int launch_cycles(const LaunchParams &p, int grid, void *stream, bool cooperative);
 int launch_init_rows(const LatticeDesc &d, int init, void *stream);
 int launch_pack_rows(const LatticeDesc &d, const int8_t *dev_spins, void *stream);
-int launch_unpack_rows(const LatticeDesc &d, int8_t *dev_spins, void *stream);
+// With `gate` (a device int), the unpack writes nothing when *gate != 0 at
+// the time it runs (an error raised by the launches before it).
+int launch_unpack_rows(const LatticeDesc &d, int8_t *dev_spins, void *stream, const int *gate = nullptr);
 // The same with one bit per site (bit i mod 8 of byte i / 8, 1 for +1).
 int launch_pack_bits(const LatticeDesc &d, const uint8_t *dev_bits, void *stream);
 int launch_unpack_bits(const LatticeDesc &d, uint8_t *dev_bits, void *stream);

@@ -62,8 +62,9 @@ __global__ void pack_rows_kernel(LatticeDesc Ld, const int8_t *s8)
 }
 
 template <int D>
-__global__ void unpack_rows_kernel(LatticeDesc Ld, int8_t *s8)
+__global__ void unpack_rows_kernel(LatticeDesc Ld, int8_t *s8, const int *gate)
 {
+    if (gate && ld_volatile_int(gate) != 0) return; // a failed run leaves the caller's spins as they were
     const long long nrows = Ld.K * (D * D);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nrows;
          i += (long long)gridDim.x * blockDim.x) {
@@ -258,8 +259,9 @@ __global__ void __launch_bounds__(256) pack_rows_tiled_kernel(LatticeDesc Ld, co
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) unpack_rows_tiled_kernel(LatticeDesc Ld, int8_t *s8)
+__global__ void __launch_bounds__(256) unpack_rows_tiled_kernel(LatticeDesc Ld, int8_t *s8, const int *gate)
 {
+    if (gate && ld_volatile_int(gate) != 0) return; // a failed run leaves the caller's spins as they were
     constexpr int S = D * D + 2;
     __shared__ __align__(16) uint16_t rows[kTileDomains * S];
     const long long L = Ld.L, ntiles = (long long)Ld.nd * Ld.nd * ((Ld.nd + kTileDomains - 1) / kTileDomains);
@@ -581,16 +583,16 @@ int launch_pack_rows(const LatticeDesc &d, const int8_t *dev_spins, void *stream
     return to_status(cudaGetLastError());
 }
 
-int launch_unpack_rows(const LatticeDesc &d, int8_t *dev_spins, void *stream)
+int launch_unpack_rows(const LatticeDesc &d, int8_t *dev_spins, void *stream, const int *gate)
 {
     if (d.d != 16 || ((uintptr_t)dev_spins & 15) == 0) { // vector accesses at d = 16
         const long long tiles = (long long)d.nd * d.nd * ((d.nd + kTileDomains - 1) / kTileDomains);
         SPKMC_DISPATCH_D(d.d, unpack_rows_tiled_kernel, (int)(tiles < 2048 ? tiles : 2048), 256, (cudaStream_t)stream, d,
-                         dev_spins);
+                         dev_spins, gate);
         return to_status(cudaGetLastError());
     }
     const int grid = simple_grid(d.K * d.d * d.d, 256);
-    SPKMC_DISPATCH_D(d.d, unpack_rows_kernel, grid, 256, (cudaStream_t)stream, d, dev_spins);
+    SPKMC_DISPATCH_D(d.d, unpack_rows_kernel, grid, 256, (cudaStream_t)stream, d, dev_spins, gate);
     return to_status(cudaGetLastError());
 }
 

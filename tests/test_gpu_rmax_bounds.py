@@ -220,6 +220,35 @@ def test_noalloc_entry_point_with_learned_bound():
     assert list(state.rmax_hist) == list(st.rmax_hist)
 
 
+def test_noalloc_error_leaves_the_spins_and_the_state_as_they_were():
+    """A history too small for the lattice makes the device's tolerance check
+    stop the no-allocation run with EBOUND: the caller's spin buffer still
+    holds its input and the state its old values, and a call with a valid
+    state then runs as the oracle."""
+    torch = pytest.importorskip("torch")
+    spec = wl.LatticeSpec(L=32, d=4, seed=65)
+    mode = sp.SPKMC_RMAX_LEARNED
+    st = oracle_state(spec, mode)
+    spins0 = st.spins.copy()
+    dev = torch.from_numpy(spins0.copy()).cuda()
+    p = sp.make_params(spec.L, spec.d, spec.J, spec.H, spec.T, spec.seed, rmax_mode=mode)
+    bad = sp.spkmc_state()
+    for i in range(8):
+        bad.rmax_hist[i] = 1.0
+    with pytest.raises(sp.SpkmcError) as e:
+        sp.spkmc_run_cycles_noalloc(p, dev.data_ptr(), bad, 20)
+    assert e.value.code == sp.SPKMC_EBOUND
+    torch.cuda.synchronize()
+    assert np.array_equal(dev.cpu().numpy(), spins0)
+    assert (bad.cycle, bad.n_flip, bad.n_null, bad.clock) == (0, 0, 0, 0.0)
+    assert list(bad.rmax_hist) == [1.0] * 8
+    good = sp.spkmc_state()
+    sp.spkmc_run_cycles_noalloc(p, dev.data_ptr(), good, 20)
+    st.run(20)
+    assert np.array_equal(dev.cpu().numpy(), st.spins)
+    assert (good.cycle, good.n_flip, good.n_null) == (st.cycle, st.n_flip, st.n_null)
+
+
 @pytest.mark.parametrize("mode", MODES + [sp.SPKMC_RMAX_EXACT])
 @pytest.mark.parametrize("L,d,cycles", [(1024, 16, 2000), (256, 16, 20000), (128, 8, 20000), (64, 4, 20000)])
 def test_long_runs_keep_counts_consistent(mode, L, d, cycles):

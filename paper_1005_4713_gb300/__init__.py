@@ -24,7 +24,7 @@ from ._abi import (SPKMC_EBOUND, SPKMC_EBUSY, SPKMC_ECUDA, SPKMC_EINTERNAL, SPKM
                    spkmc_event, spkmc_info, spkmc_obs, spkmc_params, spkmc_state)
 
 __all__ = [n for n in _abi.PROTOTYPES] + ["Lattice", "Batch", "Graph", "SpkmcError", "torch_config", "obs_buffer",
-                                            "make_params", "make_config", "EVENT_DTYPE"]
+                                            "make_params", "make_config", "EVENT_DTYPE", "tuned_config", "with_launch"]
 
 _lock = threading.Lock()
 _lib = None
@@ -413,15 +413,38 @@ def spkmc_last_error() -> str:
 # ---------------------------------------------------------------------------
 # Convenience wrappers
 # ---------------------------------------------------------------------------
+def with_launch(config: spkmc_config | None, items_per_cta: int, ctas_per_sm: int) -> spkmc_config:
+    """A copy of ``config`` (or of the defaults) with the given launch geometry."""
+    c = make_config() if config is None else spkmc_config.from_buffer_copy(config)
+    c.items_per_cta, c.ctas_per_sm = int(items_per_cta), int(ctas_per_sm)
+    return c
+
+
+def tuned_config(L: int, domain_edge: int, config: spkmc_config | None = None):
+    """``config`` with the autotuner's cached launch geometry for (L, d) filled
+    in, when the caller set neither knob and the geometry was tuned on this
+    device; otherwise ``config`` itself.  Geometry never changes results."""
+    if config is not None and (config.items_per_cta or config.ctas_per_sm):
+        return config
+    from . import autotune
+    d = int(domain_edge) or spkmc_resolve_domain_edge(int(L))
+    hit = autotune.cached_launch(int(L), d)
+    return config if hit is None else with_launch(config, *hit)
+
+
 class Lattice:
-    """One lattice on the GPU (owns a spkmc_t handle)."""
+    """One lattice on the GPU (owns a spkmc_t handle).  With ``tuned`` (the
+    default) the autotuner's cached launch geometry is used when ``config``
+    sets none."""
 
     def __init__(self, L, domain_edge=0, J=1.0, H=0.0, T=4.5115, seed=1, cold=False,
                  event_log_capacity=0, config: spkmc_config | None = None, rmax_mode=SPKMC_RMAX_EXACT,
-                 sublattice=SPKMC_SUBLATTICE_8_ROTATING):
+                 sublattice=SPKMC_SUBLATTICE_8_ROTATING, tuned: bool = True):
         self.params = make_params(L, domain_edge, J, H, T, seed,
                                   SPKMC_INIT_COLD if cold else SPKMC_INIT_HOT, event_log_capacity, rmax_mode,
                                   sublattice)
+        if tuned:
+            config = tuned_config(L, domain_edge, config)
         self.config = config
         self.h = spkmc_create_ex(self.params, config)
         info = spkmc_info_get(self.h)

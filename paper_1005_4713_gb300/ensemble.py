@@ -28,6 +28,14 @@ class EnsembleResult:
     def events_per_s(self):
         return self.events / self.seconds if self.seconds > 0 else 0.0
 
+    @property
+    def flips(self):
+        return sum(f[4] for f in self.final)
+
+    @property
+    def flips_per_s(self):
+        return self.flips / self.seconds if self.seconds > 0 else 0.0
+
 
 def _obs_key(o):
     return (o.cycle, o.clock, o.M, o.B, o.n_flip, o.n_null, int(o.sum_null_rate_fx[0]), int(o.sum_null_rate_fx[1]))
@@ -43,8 +51,21 @@ def _binder(L, m2s, m4s):
     return {"L": L, "samples": n, "m2": a2, "m4": a4, "U4": u4, "U": 1.0 - u4 / 3.0}
 
 
-def run_batched(specs, cycles: int, sample_every: int = 50, burn_in: int = 0, config=None) -> EnsembleResult:
+def batch_config(specs, config=None):
+    """``config`` with the autotuner's cached launch geometry for this mix of
+    lattices, when the caller set none and the mix was tuned on this device."""
+    if config is not None and (config.items_per_cta or config.ctas_per_sm):
+        return config
+    from . import autotune, with_launch
+    hit = autotune.cached_batch(specs)
+    return config if hit is None else with_launch(config, *hit)
+
+
+def run_batched(specs, cycles: int, sample_every: int = 50, burn_in: int = 0, config=None,
+                tuned: bool = True) -> EnsembleResult:
     n = len(specs)
+    if tuned:
+        config = batch_config(specs, config)
     sample_every = max(1, min(sample_every, cycles)) if cycles > 0 else 1
     with Batch(n, config) as b:
         slots = [b.admit(s.L, s.d, s.J, s.H, s.T, s.seed, cold=s.cold, cycles=cycles) for s in specs]

@@ -266,43 +266,12 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *m, unsigned pa
     return done != 0;
 }
 
-// L2 eviction priorities: the domain blocks stream through L2 (a block is
-// staged once per visit of its colour, eight cycles apart, and the lattice's
-// blocks are larger than L2), so their copies are marked evict-first; the
-// class-count lines are read by step 1 and moved by the flips of the
-// neighbouring colours in between, so their loads are marked evict-last and
-// they stay in L2 from one visit to the next.
-__device__ __forceinline__ unsigned long long l2_evict_first_policy()
-{
-    unsigned long long pol;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-
-__device__ __forceinline__ unsigned long long l2_evict_last_policy()
-{
-    unsigned long long pol;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-
 __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes,
                                               unsigned long long *m)
 {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
-                 "[%0], [%1], %2, [%3], %4;"
-                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(m)), "l"(l2_evict_first_policy())
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(m))
                  : "memory");
-}
-
-// 16 bytes of global memory through L2 (no L1), marked evict-last.
-__device__ __forceinline__ int4 ldcg_evict_last(const int4 *p, unsigned long long pol)
-{
-    int4 v;
-    asm volatile("ld.global.cg.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "l"(p), "l"(pol));
-    return v;
 }
 
 // Wait for the bulk copies of one round.  The first limit raises an error
@@ -368,10 +337,8 @@ __device__ void phase_a(const LaunchParams &P, CtaShared &S, unsigned char *stag
                 active_domain(Ld, a, cycle_colour(S, Ld, ls, t), dx, dy, dz);
                 const long long k = domain_index(Ld.nd, dx, dy, dz);
                 const int4 *cp = reinterpret_cast<const int4 *>(Ld.counts + k * kCountStride);
-                const unsigned long long keep = l2_evict_last_policy();
-                const int4 n0 = ldcg_evict_last(cp, keep), n1 = ldcg_evict_last(cp + 1, keep),
-                           n2 = ldcg_evict_last(cp + 2, keep),
-                           n3 = ldcg_evict_last(cp + 3, keep); // total | lower-half count << 16
+                const int4 n0 = __ldcg(cp), n1 = __ldcg(cp + 1), n2 = __ldcg(cp + 2),
+                           n3 = __ldcg(cp + 3); // total | lower-half count << 16
                 // the draw does not depend on the counts: compute it while they load
                 unsigned long long w[4];
                 philox4x64_10((unsigned long long)t, (unsigned long long)k, 1ULL, 0ULL, Ld.seed, 0ULL,

@@ -1,5 +1,7 @@
 """Batched ensembles: many lattices of uneven L, T and H in one persistent
 launch; each one's trajectory must equal its solo run and the oracle."""
+import os
+
 import numpy as np
 import pytest
 
@@ -111,4 +113,21 @@ def test_mixed_edges_share_warps(kw):
             st.run(n)
             o = b.observables(slot)
             assert (o.n_flip, o.n_null) == (st.n_flip, st.n_null)
+            assert np.array_equal(b.spins(slot), st.spins)
+
+
+def test_batch_of_multi_round_ctas():
+    """One CTA per SM, so each CTA holds more domains than one staging round
+    (a dozen uneven lattices with 2^3-site domains): every lattice equals its
+    oracle run."""
+    specs = [wl.LatticeSpec(L=s.L, d=2, T=s.T, H=s.H, seed=s.seed) for s in wl.ensemble_specs(12)]
+    n = 40
+    with sp.Batch(len(specs), sp.make_config(items_per_cta=64, ctas_per_sm=1)) as b:
+        slots = [b.admit(s.L, s.d, s.J, s.H, s.T, s.seed) for s in specs]
+        b.run(n)
+        for s, slot in zip(specs, slots):
+            st = oracle.State(s.L, s.d, s.J, s.H, s.T, s.seed)
+            st.run(n, threads=min(16, os.cpu_count() or 1))
+            o = b.observables(slot)
+            assert (o.n_flip, o.n_null) == (st.n_flip, st.n_null), s
             assert np.array_equal(b.spins(slot), st.spins)

@@ -206,6 +206,21 @@ def test_launch_geometry_does_not_change_the_trajectory(kw):
         assert_same(lat, st)
 
 
+@pytest.mark.parametrize("kw", [dict(items_per_cta=1000), dict(items_per_cta=300), dict(max_ctas=2)])
+def test_multi_round_ctas_in_a_grid(kw):
+    """More active domains per CTA than one staging round holds, in a grid of
+    several CTAs (each CTA stages, ranks and flips its domains in rounds,
+    between grid barriers): 64^3 with 2^3-site domains, 4096 per cycle."""
+    spec = wl.LatticeSpec(L=64, d=2, seed=31)
+    st = oracle_state(spec)
+    st.run(40, threads=THREADS)
+    with gpu_lattice(spec, config=sp.make_config(**kw)) as lat:
+        lat.run(40)
+        assert lat.info().grid_ctas > 1
+        assert_same(lat, st)
+        assert lat.check_counts() == 0
+
+
 def test_checkpoint_resume_is_bit_exact():
     spec = wl.LatticeSpec(L=64, d=8, seed=23)
     with gpu_lattice(spec) as a:

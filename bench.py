@@ -289,44 +289,95 @@ def small_configs(cfg, stream, every=100, nrec=20):
     return out
 
 
-def batched_summary(n_lattices=256, cycles=5000, solo_sample=16):
-    """Ensemble of uneven lattices in one persistent launch per chunk vs the
-    same lattices one at a time (a sample of them, scaled to all)."""
+def binder_table(binder, t_edges=(4.40, 4.45, 4.50, 4.55, 4.60)):
+    """Binder cumulant U = 1 - <m^4>/(3 <m^2>^2) (Eq. 7 and the cumulant form)
+    per lattice edge and temperature bin: the mean over the lattices in the
+    bin and its standard error."""
+    import numpy as np
+    rows = []
+    for L in sorted({b["L"] for b in binder}):
+        for lo, hi in zip(t_edges[:-1], t_edges[1:]):
+            us = [b["U"] for b in binder if b["L"] == L and lo <= b["T"] < hi + (1e-12 if hi == t_edges[-1] else 0)
+                  and b["U"] is not None]
+            if us:
+                rows.append({"L": L, "T_lo": lo, "T_hi": hi, "n": len(us), "U": float(np.mean(us)),
+                             "err": float(np.std(us, ddof=1) / np.sqrt(len(us))) if len(us) > 1 else None})
+    return rows
+
+
+def batched_summary(n_lattices=256, cycles=5000):
+    """Ensemble of uneven lattices in one persistent launch per chunk against
+    the same lattices run one at a time with the single-lattice path: all of
+    them, each bit-equal.  The domain edge of each L is the autotuner's (most
+    flips per second), the batch's launch geometry too (least time per
+    cycle); both are measured on this GPU first."""
     import paper_1005_4713_gb300 as sp  # noqa: F401
     from paper_1005_4713_gb300 import autotune, ensemble
     from paper_1005_4713_gb300 import workloads as wl
     Ls = [s.L for s in wl.ensemble_specs(n_lattices)]
     edges = autotune.edge_map(Ls)
     specs = wl.ensemble_specs(n_lattices, domain_edge=lambda L: edges[L])
+    launch = autotune.tune_batch(specs)
     bat = ensemble.run_batched(specs, cycles, sample_every=50, burn_in=cycles // 5)
-    sample = specs[:solo_sample]
-    solo = ensemble.run_one_at_a_time(sample, cycles, sample_every=50, burn_in=cycles // 5)
-    assert solo.final == bat.final[:solo_sample], "batched results differ from the solo runs"
-    frac = sum((s.L // s.d // 2) ** 3 for s in sample) / sum((s.L // s.d // 2) ** 3 for s in specs)
-    solo_all = solo.seconds * len(specs) / len(sample)
-    u = [x["U"] for x in bat.binder if x["U"] is not None]
+    solo = ensemble.run_one_at_a_time(specs, cycles, sample_every=50, burn_in=cycles // 5)
+    same = [a == b for a, b in zip(solo.final, bat.final)]
+    if not all(same):
+        raise RuntimeError(f"batched results differ from the solo runs for {same.count(False)} lattices")
     return {"workload": f"{n_lattices} lattices, L in {{16..128}}, T~U[4.40,4.60], H in {{0,0.01}}, {cycles} cycles",
             "edges": {str(k): v for k, v in edges.items()},
+            "edge_objective": "flips_per_s (null events excluded), measured per L on this GPU",
+            "edge_trials": autotune.edge_report(Ls),
+            "launch": {"items_per_cta": launch["items_per_cta"], "ctas_per_sm": launch["ctas_per_sm"],
+                       "objective": launch["objective"]},
             "batched_s": bat.seconds, "batched_events_per_s": bat.events_per_s,
-            "solo_sample": solo_sample, "solo_sample_s": solo.seconds, "solo_sample_event_fraction": frac,
-            "solo_all_s_est": solo_all, "speedup_vs_solo": solo_all / bat.seconds,
-            "bit_exact_vs_solo_sample": True,
-            "binder_U_mean": sum(u) / len(u) if u else None}
+            "batched_flips_per_s": bat.flips_per_s,
+            "solo_all_s": solo.seconds, "solo_events_per_s": solo.events_per_s, "solo_flips_per_s": solo.flips_per_s,
+            "speedup_vs_solo": solo.seconds / bat.seconds,
+            "bit_exact_vs_solo": f"{len(same)} of {len(same)} lattices",
+            "binder_U_by_L_T": binder_table(bat.binder),
+            "binder_note": "U per lattice from samples every 50 cycles after 1000 cycles; at 5000 cycles the "
+                           "larger lattices have not relaxed, so this is a throughput workload, not an "
+                           "estimate of the critical point (the crossing is measured on L = 8, 12, 16)"}
 
 
-def served_summary(n_requests=400, rate=200.0, budget=120 << 30, step_cycles=100):
-    """Poisson stream of simulation requests served with continuous batching."""
+def served_summary(n_requests=2000, rate=200.0, budget=120 << 30, step_cycles=100, sweep=(25, 100, 400),
+                   sweep_requests=400):
+    """Poisson stream of simulation requests served with continuous batching,
+    against the same requests served one at a time with the plain
+    single-lattice path on the same arrival times; every result bit-equal.
+    A short sweep of the cycles per batch step on the first requests."""
     from paper_1005_4713_gb300 import serve
     from paper_1005_4713_gb300 import workloads as wl
     reqs = wl.request_stream(n=n_requests, rate=rate)
     srv = serve.Server(budget_bytes=budget, capacity=512, step_cycles=step_cycles)
     st = srv.serve(reqs, realtime=True)
+    one = serve.serve_one_at_a_time(reqs, realtime=True)
+    mine = {c.rid: c.obs for c in st.completions}
+    same = sum(1 for c in one.completions if mine.get(c.rid) == c.obs)
+    if same != len(one.completions):
+        raise RuntimeError(f"served results differ from the one-at-a-time runs for {len(one.completions) - same}")
+
+    def arm(x):
+        return {"completed": len(x.completions), "p50_latency_s": x.latency_percentile(50),
+                "p99_latency_s": x.latency_percentile(99), "events_per_s": x.events_per_s, "wall_s": x.wall,
+                "p50_breakdown": x.breakdown(50), "p99_breakdown": x.breakdown(99), "by_L": x.by_size()}
+
+    sw = []
+    for sc in sweep:
+        x = serve.Server(budget_bytes=budget, capacity=512, step_cycles=sc).serve(reqs[:sweep_requests], realtime=True)
+        sw.append({"step_cycles": sc, "p50_latency_s": x.latency_percentile(50),
+                   "p99_latency_s": x.latency_percentile(99), "events_per_s": x.events_per_s, "steps": x.steps})
+    cb = arm(st)
+    cb.update(rejected=len(st.rejected), peak_live=st.peak_live, steps=st.steps, step_cycles=step_cycles)
+    oa = arm(one)
     return {"workload": f"{n_requests} requests, Poisson {rate:g}/s, L in {{32,64,128,256}}, T~U[4.3,4.7], "
                         f"cycles log-uniform 1e2..1e4, budget {budget >> 30} GiB",
-            "completed": len(st.completions), "rejected": len(st.rejected),
-            "p50_latency_s": st.latency_percentile(50), "p99_latency_s": st.latency_percentile(99),
-            "events_per_s": st.events_per_s, "wall_s": st.wall, "peak_live": st.peak_live,
-            "steps": st.steps, "step_cycles": step_cycles}
+            "continuous_batching": cb, "one_at_a_time": oa,
+            "speedup": {"events_per_s": st.events_per_s / one.events_per_s,
+                        "p50_latency": oa["p50_latency_s"] / cb["p50_latency_s"],
+                        "p99_latency": oa["p99_latency_s"] / cb["p99_latency_s"]},
+            "bit_exact_vs_one_at_a_time": f"{same} of {len(one.completions)} requests",
+            "step_cycles_sweep": {"requests": sweep_requests, "runs": sw}}
 
 
 # ---------------------------------------------------------------------------

@@ -22,7 +22,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import Batch, make_params, spkmc_bytes_required, SPKMC_INIT_COLD, SPKMC_INIT_HOT
+from . import Batch, Lattice, make_params, spkmc_bytes_required, SPKMC_INIT_COLD, SPKMC_INIT_HOT
 
 
 @dataclass
@@ -36,6 +36,7 @@ class Completion:
     obs: tuple
     spins: np.ndarray | None = None
     cancelled: bool = False
+    L: int = 0
 
     @property
     def latency(self):
@@ -62,6 +63,24 @@ class ServeStats:
     def latency_percentile(self, q):
         lat = [c.latency for c in self.completions if not c.cancelled]
         return float(np.percentile(lat, q)) if lat else None
+
+    def breakdown(self, q):
+        """Percentile q of the time spent waiting for admission (queue) and
+        of the time from admission to completion (run)."""
+        done = [c for c in self.completions if not c.cancelled]
+        if not done:
+            return None
+        return {"queue_s": float(np.percentile([c.admitted - c.arrival for c in done], q)),
+                "run_s": float(np.percentile([c.finished - c.admitted for c in done], q))}
+
+    def by_size(self):
+        """Latency percentiles per lattice edge."""
+        out = {}
+        for c in self.completions:
+            if not c.cancelled:
+                out.setdefault(c.L, []).append(c.latency)
+        return {str(L): {"n": len(v), "p50_s": float(np.percentile(v, 50)), "p99_s": float(np.percentile(v, 99))}
+                for L, v in sorted(out.items())}
 
 
 def _obs_key(o):
@@ -140,8 +159,34 @@ class Server:
                         stats.completions.append(Completion(
                             rid=r.rid, arrival=r.arrival if realtime else 0.0, admitted=t_adm, finished=t,
                             cycles=o.cycle, events=o.cycle * (s.L // s.d // 2) ** 3, obs=_obs_key(o), spins=spins,
-                            cancelled=r.rid in self._cancel))
+                            cancelled=r.rid in self._cancel, L=s.L))
                         b.retire(slot)
                         live_bytes -= need
         stats.wall = time.perf_counter() - t0
         return stats
+
+
+def serve_one_at_a_time(requests, realtime: bool = True, config=None) -> ServeStats:
+    """The same requests served one at a time with the plain single-lattice
+    path (spkmc_create_ex, spkmc_run_cycles, spkmc_observables), first come
+    first served on the same arrival times: the baseline of continuous
+    batching.  Each result is bit-comparable with the batched one."""
+    stats = ServeStats()
+    t0 = time.perf_counter()
+    for r in sorted(requests, key=lambda r: r.arrival):
+        now = time.perf_counter() - t0
+        if realtime and r.arrival > now:
+            time.sleep(r.arrival - now)
+        t_start = time.perf_counter() - t0
+        s = r.spec
+        with Lattice(s.L, s.d, s.J, s.H, s.T, s.seed, cold=s.cold, config=config) as lat:
+            lat.run(r.cycles)
+            o = lat.observables()
+        t_end = time.perf_counter() - t0
+        stats.completions.append(Completion(
+            rid=r.rid, arrival=r.arrival if realtime else 0.0, admitted=t_start, finished=t_end, cycles=o.cycle,
+            events=o.cycle * (s.L // s.d // 2) ** 3, obs=_obs_key(o), L=s.L))
+        stats.peak_live = 1
+        stats.steps += 1
+    stats.wall = time.perf_counter() - t0
+    return stats

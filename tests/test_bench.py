@@ -61,3 +61,16 @@ def test_kernel_source_hash_changes_with_the_sources(tmp_path, monkeypatch):
     h3 = bench.kernel_source_hash()
     (csrc / "spkmc_setup_kernels.cu").write_text("d ")
     assert bench.kernel_source_hash() == h3
+
+
+def test_binder_table_bins_by_edge_and_temperature():
+    binder = [{"L": 16, "T": 4.41, "U": 0.50}, {"L": 16, "T": 4.44, "U": 0.54},
+              {"L": 16, "T": 4.60, "U": 0.20}, {"L": 32, "T": 4.52, "U": 0.40},
+              {"L": 32, "T": 4.53, "U": None}]
+    rows = bench.binder_table(binder)
+    by = {(r["L"], r["T_lo"]): r for r in rows}
+    assert by[(16, 4.40)]["n"] == 2 and abs(by[(16, 4.40)]["U"] - 0.52) < 1e-12
+    assert abs(by[(16, 4.40)]["err"] - 0.02) < 1e-12     # std 0.0283 / sqrt(2)
+    assert by[(16, 4.55)]["n"] == 1 and by[(16, 4.55)]["err"] is None  # T = 4.60 falls in the last bin
+    assert by[(32, 4.50)]["n"] == 1                        # lattices without samples are left out
+    assert (16, 4.45) not in by

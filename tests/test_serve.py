@@ -92,3 +92,20 @@ def test_ensemble_samples_equal_plain_read_outs():
                     m4.append(o.m4)
         assert got["samples"] == 3
         assert got["m2"] == sum(m2) / 3 and got["m4"] == sum(m4) / 3
+
+
+def test_one_at_a_time_baseline_equals_the_served_results():
+    """The baseline of continuous batching (each request alone with the plain
+    single-lattice path, first come first served) gives the same result for
+    every request, and reports its own queue and run times."""
+    reqs = small_stream(n=10, seed=4)
+    batched = serve.Server(budget_bytes=1 << 30, capacity=8, step_cycles=25).serve(reqs, realtime=False)
+    alone = serve.serve_one_at_a_time(reqs, realtime=False)
+    assert sorted(c.rid for c in alone.completions) == sorted(r.rid for r in reqs)
+    got = {c.rid: c.obs for c in batched.completions}
+    for c in alone.completions:
+        assert c.obs == got[c.rid]
+        assert c.finished >= c.admitted >= c.arrival
+    b = alone.breakdown(50)
+    assert b["queue_s"] >= 0.0 and b["run_s"] > 0.0
+    assert set(alone.by_size()) <= {"16", "32", "48"}

@@ -584,13 +584,19 @@ __device__ __forceinline__ int select_site(const WorkItem &w, const unsigned cha
     const unsigned who = __ballot_sync(kFull, mine) & grp;
     int site = 0;
     if (mine) {
-        int jj = w.j - excl;
+        // the word that holds the site, then one search in it
+        int jj = w.j - excl, at = 0, wi = 0;
+        uint32_t word = 0;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int pc = __popc(cb.m[i]);
-            if (jj >= 0 && jj < pc) site = cb.base + i * cb.stride + nth_set_bit(cb.m[i], jj) + cb.offset;
+            const bool here = jj >= 0 && jj < pc;
+            word = here ? cb.m[i] : word;
+            wi = here ? i : wi;
+            at = here ? jj : at;
             jj -= pc;
         }
+        site = cb.base + wi * cb.stride + nth_set_bit(word, at) + cb.offset;
     }
     site = __shfl_sync(kFull, site, who ? __ffs(who) - 1 : lane);
     return who ? site : -1;

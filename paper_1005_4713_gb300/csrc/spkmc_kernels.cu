@@ -772,6 +772,37 @@ struct FlipDelta {
     int dM, dB; // change of M and B
 };
 
+// Spin bit of local site (x, y, z) of a staged block when only coordinate
+// A (and, if B >= 0, coordinate B) may lie outside [0, D), by one step;
+// with both outside the result is not used.  The other coordinates are in
+// the domain, so only the possible ghost faces are selected.
+template <int D, int A, int B>
+__device__ __forceinline__ uint32_t staged_bit(const uint16_t *blk, int x, int y, int z)
+{
+    const int c3[3] = {x, y, z};
+    const bool ao = c3[A] < 0 || c3[A] >= D;
+    const bool bo = B >= 0 && (c3[B < 0 ? 0 : B] < 0 || c3[B < 0 ? 0 : B] >= D);
+    int idx = (y & (D - 1)) + D * (z & (D - 1));
+    int bit = x & (D - 1);
+    // ghost face of axis q (side by the sign of the coordinate): index by the
+    // remaining coordinates as in the block layout
+    auto ghost = [&](int q, bool below, int &gi, int &gb) {
+        const int face = 2 * q + (below ? 0 : 1);
+        gi = D * D + face * D + (q == 2 ? (y & (D - 1)) : (z & (D - 1)));
+        gb = (q == 0 ? y : x) & (D - 1);
+    };
+    int gi, gb;
+    ghost(A, c3[A] < 0, gi, gb);
+    idx = ao ? gi : idx;
+    bit = ao ? gb : bit;
+    if (B >= 0) {
+        ghost(B < 0 ? 0 : B, c3[B < 0 ? 0 : B] < 0, gi, gb);
+        idx = bo ? gi : idx;
+        bit = bo ? gb : bit;
+    }
+    return ((uint32_t)blk[idx] >> bit) & 1u;
+}
+
 // Flip the chosen site (step 6), move the class counts of the site and of its
 // 6 neighbours (read from the pre-flip state) and refresh the ghost faces of
 // the neighbour domains that see the site; one thread per domain.  The
@@ -792,7 +823,7 @@ __device__ FlipDelta apply_flip(const LaunchParams &P, CtaShared &S, const WorkI
     // touches them this cycle
     int4 *own = reinterpret_cast<int4 *>(cnt + w.k * kCountStride);
     const int l = w.site;
-    const int s3[3] = {l % D, (l / D) % D, l / (D * D)};
+    const int s3[3] = {l % D, (l / D) % D, (l / (D * D)) % D};
     const int sig = w.cls >= 7, us = w.cls - 7 * sig;
     const int delta = sig ? -1 : 1; // change of the neighbours' up count
     const int nd = Ld.nd;
@@ -870,38 +901,74 @@ __device__ FlipDelta apply_flip(const LaunchParams &P, CtaShared &S, const WorkI
         }
     }
     }
-    int cold[6];
-    bool outv[6];
-    const int sbit = block_bit<D>(st, s3[0], s3[1], s3[2]); // the flipped site, before its flip
+    // The spins of the sites within two steps of the flipped site s, before
+    // its flip, one bit each: bit 0 s, bit 1 + dir its neighbour across
+    // direction dir, bit 7 + dir the site two steps out that way, bits 13 +
+    // 4 pr + sg the diagonal sites s + sa e_a + sb e_b (pr: the axis pair
+    // (a, b) = (0,1), (0,2), (1,2); sg: bit 0 sa > 0, bit 1 sb > 0).  A site
+    // with one coordinate one step outside the domain is in a staged ghost
+    // face; two steps out along one axis, or outside along two, it was
+    // loaded from the neighbouring blocks above.  Each neighbour's up count
+    // is then a popc of the ball under a fixed mask.
+    uint32_t ball = ((uint32_t)st[s3[1] + D * s3[2]] >> s3[0]) & 1u;
 #pragma unroll
     for (int dir = 0; dir < 6; ++dir) {
         const int ax = dir >> 1, step = (dir & 1) ? 1 : -1;
-        int j3[3] = {s3[0], s3[1], s3[2]};
-        j3[ax] += step;
-        const bool out = j3[ax] < 0 || j3[ax] >= D;
-        // up count of j if it lies inside the domain: all six from the block
-        int u_in = 0;
+        int n3[3] = {s3[0], s3[1], s3[2]};
+        n3[ax] += step;
+        const uint32_t b1 = ax == 0 ? staged_bit<D, 0, -1>(st, n3[0], n3[1], n3[2])
+                            : ax == 1 ? staged_bit<D, 1, -1>(st, n3[0], n3[1], n3[2])
+                                      : staged_bit<D, 2, -1>(st, n3[0], n3[1], n3[2]);
+        ball |= b1 << (1 + dir);
+        n3[ax] += step;
+        const bool two_out = n3[ax] < -1 || n3[ax] > D;
+        const uint32_t s2 = ax == 0 ? staged_bit<D, 0, -1>(st, n3[0], n3[1], n3[2])
+                            : ax == 1 ? staged_bit<D, 1, -1>(st, n3[0], n3[1], n3[2])
+                                      : staged_bit<D, 2, -1>(st, n3[0], n3[1], n3[2]);
+        const uint32_t b2 = two_out ? ((gv[dir][0] >> gbit[dir][0]) & 1u) : s2;
+        ball |= b2 << (7 + dir);
+    }
 #pragma unroll
-        for (int n = 0; n < 6; ++n) {
-            int n3[3] = {j3[0], j3[1], j3[2]};
-            n3[n >> 1] += (n & 1) ? 1 : -1;
-            u_in += block_bit<D>(st, n3[0], n3[1], n3[2]);
-        }
-        // if it lies outside: the flipped site, the site two steps out, and
-        // the four lateral neighbours (halo face, else the diagonal domain)
-        int u_out = sbit + (int)((gv[dir][0] >> gbit[dir][0]) & 1u);
+    for (int pr = 0; pr < 3; ++pr) {
+        const int a = pr == 2 ? 1 : 0, b = pr == 0 ? 1 : 2;
+        const int bi = (b - a + 2) % 3; // (a + 1 + bi) % 3 == b: the lateral index of b for direction a
 #pragma unroll
-        for (int n = 0; n < 4; ++n) {
-            const int bi = n >> 1, b = (ax + 1 + bi) % 3;
-            int n3[3] = {j3[0], j3[1], j3[2]};
-            n3[b] += (n & 1) ? 1 : -1;
-            const bool far = n3[b] < 0 || n3[b] >= D;
-            const int gbv = (int)((gv[dir][1 + bi] >> gbit[dir][1 + bi]) & 1u);
-            const int sbv = block_bit<D>(st, n3[0], n3[1], n3[2]);
-            u_out += far ? gbv : sbv;
+        for (int sg = 0; sg < 4; ++sg) {
+            const int sa = (sg & 1) ? 1 : -1, sb = (sg & 2) ? 1 : -1;
+            int n3[3] = {s3[0], s3[1], s3[2]};
+            n3[a] += sa;
+            n3[b] += sb;
+            const bool ao = n3[a] < 0 || n3[a] >= D, bo = n3[b] < 0 || n3[b] >= D;
+            const int da = 2 * a + (sa > 0 ? 1 : 0);
+            const uint32_t sv = pr == 0 ? staged_bit<D, 0, 1>(st, n3[0], n3[1], n3[2])
+                                : pr == 1 ? staged_bit<D, 0, 2>(st, n3[0], n3[1], n3[2])
+                                          : staged_bit<D, 1, 2>(st, n3[0], n3[1], n3[2]);
+            const uint32_t v = (ao && bo) ? ((gv[da][1 + bi] >> gbit[da][1 + bi]) & 1u) : sv;
+            ball |= v << (13 + 4 * pr + sg);
         }
-        cold[dir] = 7 * block_bit<D>(st, j3[0], j3[1], j3[2]) + (out ? u_out : u_in);
-        outv[dir] = out;
+    }
+    int cold[6];
+    bool outv[6];
+#pragma unroll
+    for (int dir = 0; dir < 6; ++dir) {
+        const int ax = dir >> 1, sp = dir & 1, step = sp ? 1 : -1;
+        // the neighbours of j = s + step e_ax: s, the site two steps out, and
+        // the four diagonal sites s + step e_ax +- e_b
+        uint32_t m = 1u | (1u << (7 + dir));
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            if (b == ax) continue;
+            const int a0 = ax < b ? ax : b, b0 = ax < b ? b : ax;
+            const int pr = (a0 == 0 && b0 == 1) ? 0 : (a0 == 0 ? 1 : 2);
+#pragma unroll
+            for (int sb = 0; sb < 2; ++sb) {
+                const int sa_bit = ax < b ? sp : sb, sb_bit = ax < b ? sb : sp;
+                m |= 1u << (13 + 4 * pr + sa_bit + 2 * sb_bit);
+            }
+        }
+        cold[dir] = 7 * (int)((ball >> (1 + dir)) & 1u) + __popc(ball & m);
+        const int jc = s3[ax] + step;
+        outv[dir] = jc < 0 || jc >= D;
     }
     bool ok = true;
     if (!Ld.sub2) { // two-colour lattices recount at each visit instead

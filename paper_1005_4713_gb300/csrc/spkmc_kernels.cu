@@ -1236,6 +1236,25 @@ __device__ __forceinline__ void phase_b_round(const LaunchParams &P, CtaShared &
             __syncthreads();
             if (!*reinterpret_cast<volatile int *>(&S.ok)) return;
         }
+        // The class counts of this CTA's domains of the next cycle into L2,
+        // for lattices whose blocks exceed 64 MB (smaller ones stay in L2
+        // anyway): step 1 of that cycle then finds them there, not behind
+        // the block copies that start it.  The flips of this cycle move some
+        // of those counts later, in L2.
+        if (early) {
+            const long long qn = lo + threadIdx.x;
+            if (qn < hi) {
+                const int lsn = find_segment(S, qn);
+                const LatticeDesc &Ldn = seg_desc(P, S, lsn);
+                if (!Ldn.sub2 && g + 1 < S.seg_part[lsn] && Ldn.K * staged_bytes(Ldn.d) > (64LL << 20)) {
+                    int dx, dy, dz;
+                    active_domain(Ldn, qn - S.seg_base[lsn], (int)((S.seg_t0[lsn] + g + 1) & 7), dx, dy, dz);
+                    const int32_t *cp = Ldn.counts + domain_index(Ldn.nd, dx, dy, dz) * kCountStride;
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(cp));
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(cp + 8));
+                }
+            }
+        }
         // rank and pick the site: 4 domains per warp, 8 lanes each
         for (int base = warp * 4; base < nwork; base += kWarps * 4) {
             const int i = base + (lane & 3);

@@ -47,6 +47,17 @@ def int8_bytes_per_event(d: int) -> int:
     return d ** 3 + 6 * d * d
 
 
+# The bytes a design would move if it staged only what the site search reads:
+# the count line, the d/2 planes of the chosen half, the plane beyond them and
+# that half's x, y and z ghost words (this design stages the whole block before
+# the half is known, to hide the copies under step 1).
+def half_domain_floor_bytes(d: int) -> int:
+    half = d // 2
+    plane = d * d // 8
+    ghosts = (2 * half * d + 2 * half * d + d * d) // 8
+    return 14 * 4 + half * plane + plane + ghosts
+
+
 # ---------------------------------------------------------------------------
 # Clock sampling (NVML through ctypes, falling back to nvidia-smi)
 # ---------------------------------------------------------------------------
@@ -627,6 +638,9 @@ def run_gpu(args, world, rank, local, pg):
                          "frac": achieved / peak, "traffic": ncu_traffic("spkmc-1024^3-d16", launch_cycles),
                          "peak_kind": peak_kind, "kernel": "spkmc_cycles_kernel",
                          "bytes_per_event": bpe, "kernel_ms_per_launch": kernel_ms,
+                         "frac_vs_half_domain_floor": launch_cycles * kact * half_domain_floor_bytes(D_BENCH)
+                         / (kernel_ms / 1e3) / 1e9 / peak,
+                         "half_domain_floor_bytes_per_event": half_domain_floor_bytes(D_BENCH),
                          "cycles_per_launch": launch_cycles,
                          "int8_equivalent_GBps": launch_cycles * kact * int8_bytes_per_event(D_BENCH) / (kernel_ms / 1e3) / 1e9},
             "cpu_baseline": cpu,

@@ -13,6 +13,8 @@ def test_bytes_per_event():
     assert bench.bytes_per_event(8) == 56 + (512 + 384) // 8
     # the int8 layout that the bit-packed one is compared with
     assert bench.int8_bytes_per_event(16) == 5632
+    # count line + 8 planes + the plane beyond + x, y (2 x 8 words) and z (one face) ghosts of the half
+    assert bench.half_domain_floor_bytes(16) == 56 + 256 + 32 + 32 + 32 + 32 == 440
 
 
 def _write_traffic(root, entry):

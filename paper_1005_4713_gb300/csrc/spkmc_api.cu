@@ -27,6 +27,10 @@ namespace {
 
 thread_local std::string g_last_error = "no error";
 
+// The grid-barrier counter (first 256 bytes) and the per-CTA counters of
+// finished cycles for the row waits.
+constexpr size_t kBarBytes = 256 + sizeof(unsigned) * kDoneStride * kMaxDoneCtas;
+
 int fail(int code, const char *fmt, ...)
 {
     char buf[512];
@@ -371,7 +375,7 @@ int batch_new(int capacity, const spkmc_config *cfg, spkmc_batch **out)
     if ((e = cudaMalloc(&b->d_desc, sizeof(LatticeDesc) * capacity)) != cudaSuccess ||
         (e = cudaMalloc(&b->d_state, sizeof(LatticeState) * capacity)) != cudaSuccess ||
         (e = cudaMalloc(&b->d_seg, sizeof(Segment) * capacity)) != cudaSuccess ||
-        (e = cudaMalloc(&b->d_bar, 256)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_bar, kBarBytes)) != cudaSuccess ||
         (e = cudaMalloc(&b->d_err, 256)) != cudaSuccess ||
         (e = cudaMalloc(&b->d_MB, 256)) != cudaSuccess ||
         (e = cudaMalloc(&b->d_obs, sizeof(spkmc_obs) * capacity)) != cudaSuccess ||
@@ -624,7 +628,10 @@ int run(spkmc_batch *b, long long cycles, const RecReq *rq = nullptr)
             if (grid >= gmax) return fail(SPKMC_EINVAL, "too many small lattices for one launch");
             grid = std::min(gmax, grid * 2);
         }
-        CUDA_TRY(cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned), b->stream), "reset barrier");
+        CUDA_TRY(cudaMemsetAsync(b->d_bar, 0,
+                                 256 + sizeof(unsigned) * kDoneStride * (size_t)std::min<long long>(grid, kMaxDoneCtas),
+                                 b->stream),
+                 "reset barrier");
         LaunchParams P{};
         P.desc = b->d_desc;
         P.state = b->d_state;
@@ -635,6 +642,7 @@ int run(spkmc_batch *b, long long cycles, const RecReq *rq = nullptr)
         P.Q = Q;
         P.ncycles = n;
         P.bar = b->d_bar;
+        P.done = nullptr; // set below when the row waits apply
         P.err = b->d_err;
         P.timeout_ns = b->cfg.barrier_timeout_ns > 0 ? b->cfg.barrier_timeout_ns : 2000000000LL;
         P.skip_cta = b->cfg.debug_skip_arrival_cta;
@@ -650,6 +658,9 @@ int run(spkmc_batch *b, long long cycles, const RecReq *rq = nullptr)
         }
         // two random colours: consecutive cycles may use face-adjacent colours
         if (P.sub2_any) P.parity0 = -1;
+        // eight colours with a shared t % 2: after an even cycle, wait only for
+        // the CTAs that share rows
+        if (P.parity0 >= 0 && !P.sub2_any && grid <= kMaxDoneCtas) P.done = b->d_bar + 64;
         if (rq) {
             P.rec = rq->rec;
             P.rec_every = rq->every;
@@ -1519,7 +1530,7 @@ extern "C" int spkmc_run_cycles_noalloc(const spkmc_params *p, int8_t *dev_spins
     Segment *d_seg = reinterpret_cast<Segment *>(base + off);
     off += up(sizeof(Segment));
     unsigned *d_bar = reinterpret_cast<unsigned *>(base + off);
-    off += 256;
+    off += up(kBarBytes);
     int *d_err = reinterpret_cast<int *>(base + off);
     off += 256;
     const size_t lattice_at = off;
@@ -1576,7 +1587,9 @@ extern "C" int spkmc_run_cycles_noalloc(const spkmc_params *p, int8_t *dev_spins
     long long left = ncycles, t = state->cycle;
     while (left > 0) {
         const long long n = std::min(left, 1LL << 18);
-        CUDA_TRY(cudaMemsetAsync(d_bar, 0, sizeof(unsigned), s), "reset barrier");
+        CUDA_TRY(cudaMemsetAsync(d_bar, 0,
+                                 256 + sizeof(unsigned) * kDoneStride * (size_t)std::min<long long>(grid, kMaxDoneCtas), s),
+                 "reset barrier");
         LaunchParams P{};
         P.desc = d_desc;
         P.state = d_state;
@@ -1587,6 +1600,7 @@ extern "C" int spkmc_run_cycles_noalloc(const spkmc_params *p, int8_t *dev_spins
         P.Q = sz.Kact;
         P.ncycles = n;
         P.bar = d_bar;
+        P.done = nullptr;
         P.err = d_err;
         P.timeout_ns = 2000000000LL;
         P.skip_cta = -1;
@@ -1595,6 +1609,7 @@ extern "C" int spkmc_run_cycles_noalloc(const spkmc_params *p, int8_t *dev_spins
         P.exact_any = p->rmax_mode == SPKMC_RMAX_EXACT;
         P.sub2_any = D.sub2;
         if (D.sub2) P.parity0 = -1;
+        if (P.parity0 >= 0 && !P.sub2_any && grid <= kMaxDoneCtas) P.done = d_bar + 64;
         if ((rc = launch_cycles(P, (int)grid, s, grid > 1)) != SPKMC_OK) return helper_fail(rc, "persistent cycle launch");
         left -= n;
         t += n;

@@ -38,6 +38,9 @@ constexpr int kMaxEdge = 16;
 constexpr int kPadRow = kMaxEdge + 2;           // padded rows per axis
 constexpr int kPadWords = kPadRow * kPadRow;    // words of one padded domain
 constexpr int kMaxSegPerCta = 64;               // lattices one CTA may touch
+constexpr int kMaxDoneCtas = 4096;              // CTAs of a launch that can use the row waits
+constexpr int kDoneStride = 32;                 // one counter per 128-byte line: CTAs publish and
+                                                // poll without sharing a line
 
 struct LatticeDesc {
     uint16_t *cells;
@@ -107,6 +110,9 @@ struct LaunchParams {
     int64_t Q;            // total items
     int64_t ncycles;      // grid cycles of this launch
     unsigned *bar;        // grid-barrier arrival counter (zero at launch)
+    unsigned *done;       // per CTA c at done[c * kDoneStride]: cycles it has finished in this launch
+                          // (zero at launch), for the wait on the CTAs that share its rows after an
+                          // even cycle; nullptr = none
     int *err;             // first error code raised on the device
     long long timeout_ns; // barrier time limit
     int skip_cta;         // debug: CTA that never arrives (-1 = none)

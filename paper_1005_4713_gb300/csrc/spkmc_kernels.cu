@@ -78,6 +78,7 @@ struct CtaShared {
     int bulk_bytes;
     int early_bytes; // bytes requested at the start of the cycle (one-round CTAs)
     int ok;
+    int nb_lo, nb_hi; // CTAs whose items share a domain row with this CTA's (this one included)
     WorkItem work[kThreads];
 };
 
@@ -145,6 +146,51 @@ __device__ bool grid_barrier(const LaunchParams &P, CtaShared &S, unsigned &epoc
     }
     __syncthreads();
     return *reinterpret_cast<volatile int *>(&S.ok) != 0;
+}
+
+// After an even cycle t (eight colours), colour t + 1 differs from colour t
+// in the x parity bit alone: the active domains of cycle t + 1 in a row of
+// domains (fixed dy, dz) are the x neighbours of those of cycle t in the same
+// row.  Everything cycle t + 1 reads or moves that the flips of cycle t wrote
+// -- the blocks and ghost faces it stages, the count lines of step 1, the
+// rows two steps out along x that its flip step reads, the count lines of its
+// x neighbours, which the flips of cycle t rewrote -- lies in the same row;
+// its rows two steps out along y or z and its diagonal domains have colours
+// t + 1 ^ 2, ^ 4, ^ 3, ^ 5 and ^ 6, which cycle t did not touch.  So a CTA
+// need not wait for the whole grid, only for the CTAs whose items share a row
+// with its own: it publishes the cycles it has finished (a release), then
+// waits (acquires) until those CTAs have finished cycle g.  Each CTA's
+// counter has a 128-byte line of its own (with neighbouring CTAs' counters in
+// one line, the publishing and polling of 300 CTAs contended there and the
+// waits cost more than the grid barrier they replace).  Bounded like the grid
+// barrier; returns false on a timeout or another CTA's error.
+__device__ bool row_wait(const LaunchParams &P, CtaShared &S, long long g)
+{
+    __syncthreads();
+    if (threadIdx.x == 0 && (int)blockIdx.x != P.skip_cta)
+        st_release_u32(&P.done[(long long)blockIdx.x * kDoneStride], (unsigned)(g + 1));
+    int ok = 1;
+    const int c = S.nb_lo + (int)threadIdx.x;
+    if (c <= S.nb_hi && c != (int)blockIdx.x) {
+        const long long t0 = global_timer_ns();
+        unsigned polls = 0;
+        while (ld_acquire_u32(&P.done[(long long)c * kDoneStride]) < (unsigned)(g + 1)) {
+            ++polls;
+            if ((polls & 15u) == 0) {
+                if (ld_volatile_int(P.err) != 0) {
+                    ok = 0;
+                    break;
+                }
+                if (global_timer_ns() - t0 > P.timeout_ns || polls > (1u << 28)) {
+                    raise_error(P.err, SPKMC_ETIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+            __nanosleep(32);
+        }
+    }
+    return __syncthreads_and(ok) != 0;
 }
 
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
@@ -1352,6 +1398,30 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
         S.seg_base[n] = (i < P.nseg) ? P.seg[i].base : P.Q;
         S.nsegc = n;
         mbar_init(&S.mbar, 1);
+        // the CTAs whose items share a domain row (half items of one lattice,
+        // fixed dy and dz) with this CTA's first and last items
+        S.nb_lo = S.nb_hi = (int)blockIdx.x;
+        if (P.done && S.ok && n > 0 && lo < hi) {
+            auto row_edge = [&](long long q, bool end) {
+                int j = 0;
+                while (j + 1 < P.nseg && P.seg[j + 1].base <= q) ++j;
+                const long long sb = P.seg[j].base, h = P.desc[P.seg[j].slot].half;
+                const long long r0 = sb + ((q - sb) / h) * h;
+                return end ? r0 + h - 1 : r0;
+            };
+            auto owner = [&](long long q) {
+                long long c = (q * G) / P.Q;
+                while (c + 1 < G && (P.Q * (c + 1)) / G <= q) ++c;
+                while (c > 0 && (P.Q * c) / G > q) --c;
+                return (int)c;
+            };
+            S.nb_lo = owner(row_edge(lo, false));
+            S.nb_hi = owner(row_edge(hi - 1, true));
+            if (S.nb_hi - S.nb_lo + 1 > kThreads) { // cannot happen with a segment table the host accepted
+                raise_error(P.err, SPKMC_EINTERNAL);
+                S.ok = 0;
+            }
+        }
     }
     __syncthreads();
     if (!S.ok) return; // the host sizes the grid so that this cannot happen
@@ -1488,9 +1558,12 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
             // there the exact R_max's barrier, which a CTA reaches only after
             // its flips of cycle t, or this one must come first.
             const bool odd = P.parity0 >= 0 && (((long long)P.parity0 + g) & 1LL) == 1LL;
+            const bool even = P.parity0 >= 0 && !odd;
             const bool skip = odd && (P.exact_any || (P.phase4 >= 0 && (((long long)P.phase4 + g) & 3LL) == 3LL));
             if (skip) {
                 __syncthreads();
+            } else if (even && P.done) {
+                if (!row_wait(P, S, g)) return;
             } else if (!grid_barrier(P, S, epoch)) {
                 return;
             }

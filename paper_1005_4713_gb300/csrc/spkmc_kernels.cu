@@ -325,6 +325,7 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsign
 // wait goes on, bounded again); returns false if they never completed.
 __device__ bool mbar_wait_bounded(const LaunchParams &P, unsigned long long *m, unsigned parity)
 {
+    if (mbar_try_wait(m, parity)) return true; // the usual case: the copies have landed
     const long long t0 = global_timer_ns();
     bool raised = false;
     for (unsigned polls = 0;; ++polls) {

@@ -31,8 +31,9 @@
 //                       ghost faces;
 //   grid barrier        (step 6: the flips are visible) -- skipped after an
 //                       odd cycle t when that is safe (see the loop).
-// The clock (step 5) of a lattice is advanced one cycle behind by the last
-// thread of the CTA that holds the lattice's first active domain.
+// The clock (step 5) of a lattice is advanced by the last thread of the CTA
+// that holds the lattice's first active domain: during the flip step of the
+// cycle when the CTA stages its domains in one round, else one cycle behind.
 #include "spkmc_device.cuh"
 
 namespace spkmc {
@@ -1265,7 +1266,11 @@ __device__ __forceinline__ void phase_b_round(const LaunchParams &P, CtaShared &
                 __syncthreads();
                 if (!*reinterpret_cast<volatile int *>(&S.ok)) return;
             }
-            if (nwork == 0) return;
+            if (nwork == 0) {
+                // step 5 of this cycle (see the flip step below)
+                if (threadIdx.x == kThreads - 1) clock_catch_up(P, S, g + 1, lo, true);
+                return;
+            }
         } else {
             if (nwork == 0) return;
             // stage the blocks of every domain that flips in this round at once
@@ -1316,6 +1321,11 @@ __device__ __forceinline__ void phase_b_round(const LaunchParams &P, CtaShared &
         __syncthreads();
         // flips and class moves, one thread per domain
         int fls = -1, fdM = 0, fdB = 0;
+        // step 5 of this cycle, and the draw of the next, on the last thread,
+        // which has no domain here: the division and the logarithm run beside
+        // the flips instead of beside step 1 of the next cycle, where they
+        // could hold up the CTA barrier after step 1
+        if (early && threadIdx.x == kThreads - 1) clock_catch_up(P, S, g + 1, lo, true);
         if (threadIdx.x < nwork) {
             const WorkItem w = S.work[threadIdx.x];
             if (w.site >= 0) {
@@ -1528,8 +1538,9 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
             if (!*reinterpret_cast<volatile int *>(&S.ok)) return;
         }
         // step 5 one cycle behind, on a thread that normally has no domain
-        // in step 1
-        if (threadIdx.x == kThreads - 1) clock_catch_up(P, S, g, lo, true);
+        // in step 1 (a one-round CTA with domains took it during the last
+        // flip step)
+        if (threadIdx.x == kThreads - 1 && (!early || g == 0 || lo >= hi)) clock_catch_up(P, S, g, lo, true);
         phase_a(P, S, stage, g, lo, hi, early, line);
         __syncthreads();
         for (int i = threadIdx.x; i < S.nsegc; i += blockDim.x) {

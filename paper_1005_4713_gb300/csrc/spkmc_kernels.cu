@@ -618,9 +618,12 @@ __device__ __forceinline__ int select_site(const WorkItem &w, const unsigned cha
     case 8: class_bits<8>(w, stage, o, cb); break;
     default: class_bits<16>(w, stage, o, cb); break;
     }
-    int tot = 0;
+    int pc[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) tot += __popc(cb.m[i]);
+    for (int i = 0; i < 8; ++i) pc[i] = __popc(cb.m[i]);
+    const int s01 = pc[0] + pc[1], s23 = pc[2] + pc[3], s45 = pc[4] + pc[5], s67 = pc[6] + pc[7];
+    const int s03 = s01 + s23;
+    const int tot = s03 + s45 + s67;
     int incl = tot;
 #pragma unroll
     for (int off = 1; off < 8; off <<= 1) {
@@ -632,19 +635,21 @@ __device__ __forceinline__ int select_site(const WorkItem &w, const unsigned cha
     const unsigned who = __ballot_sync(kFull, mine) & grp;
     int site = 0;
     if (mine) {
-        // the word that holds the site, then one search in it
-        int jj = w.j - excl, at = 0, wi = 0;
-        uint32_t word = 0;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int pc = __popc(cb.m[i]);
-            const bool here = jj >= 0 && jj < pc;
-            word = here ? cb.m[i] : word;
-            wi = here ? i : wi;
-            at = here ? jj : at;
-            jj -= pc;
-        }
-        site = cb.base + wi * cb.stride + nth_set_bit(word, at) + cb.offset;
+        // the word that holds the site, by a binary search on the bit
+        // counts of the lane's halves, pairs and words; then one search in it
+        int jj = w.j - excl;
+        const bool h1 = jj >= s03;
+        jj -= h1 ? s03 : 0;
+        const int sp = h1 ? s45 : s01;
+        const bool h2 = jj >= sp;
+        jj -= h2 ? sp : 0;
+        const int pf = h1 ? (h2 ? pc[6] : pc[4]) : (h2 ? pc[2] : pc[0]);
+        const bool h3 = jj >= pf;
+        jj -= h3 ? pf : 0;
+        const uint32_t wa = h1 ? (h2 ? cb.m[6] : cb.m[4]) : (h2 ? cb.m[2] : cb.m[0]);
+        const uint32_t wb = h1 ? (h2 ? cb.m[7] : cb.m[5]) : (h2 ? cb.m[3] : cb.m[1]);
+        const int wi = (h1 ? 4 : 0) + (h2 ? 2 : 0) + (h3 ? 1 : 0);
+        site = cb.base + wi * cb.stride + nth_set_bit(h3 ? wb : wa, jj) + cb.offset;
     }
     site = __shfl_sync(kFull, site, who ? __ffs(who) - 1 : lane);
     return who ? site : -1;

@@ -121,7 +121,6 @@ struct LaunchParams {
     int exact_any;        // some lattice pads to the exact R_max: reduce before the events
     int sub2_any;         // some lattice uses two random colours: draw colours, recount
     int rec_n;            // records per lattice (rec_every > 0)
-    int phase4;           // t % 4 shared by all running lattices at launch, -1 if mixed or unknown
     int64_t rec_every;    // record after every rec_every cycles of the launch; 0 = none
     ObsRaw *rec;          // [slot][rec_n] records
 };

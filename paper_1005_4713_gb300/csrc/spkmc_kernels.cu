@@ -1569,14 +1569,20 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
             // After an odd cycle t, colour t + 1 shares no block, count or
             // ghost word with the flips of colour t (the colours differ in two
             // or three parity bits), so its staging and step 1 may start at
-            // once.  Its flip step may still read spins of colour t (the
-            // lateral neighbour of a moved site, in a domain diagonal to
-            // both) when the colours differ in two bits (t = 1, 5 mod 8):
-            // there the exact R_max's barrier, which a CTA reaches only after
-            // its flips of cycle t, or this one must come first.
+            // once.  The flip steps are another matter.  A flip reads the
+            // spins of the domains diagonal to its own and moves the classes
+            // of sites next to both, so the flip steps of two colours that
+            // differ in two bits must not overlap: cycles t and t + 1 for
+            // t = 1, 5 mod 8, and cycles t and t + 2 for t = 2, 3, 6, 7
+            // mod 8 (their colours differ in the y and z bits).  With the
+            // exact R_max, barrier 1 of cycle t + 1, which a CTA reaches only
+            // after its flips of cycle t, orders both.  Without it (the
+            // bounds of Sec. 3.2 step 4b), the whole grid meets after every
+            // odd cycle; the row waits after even cycles order the rest
+            // (tests/test_sync_schedule.py checks the schedule).
             const bool odd = P.parity0 >= 0 && (((long long)P.parity0 + g) & 1LL) == 1LL;
             const bool even = P.parity0 >= 0 && !odd;
-            const bool skip = odd && (P.exact_any || (P.phase4 >= 0 && (((long long)P.phase4 + g) & 3LL) == 3LL));
+            const bool skip = odd && P.exact_any;
             if (skip) {
                 __syncthreads();
             } else if (even && P.done) {

@@ -1,0 +1,228 @@
+"""Model check of the cycle kernel's synchronisation between CTAs (host
+logic, no GPU).
+
+The kernel runs many spkMC cycles (Sec. 3.1 steps 1-6, eight colours in
+rotation, Sec. 3.2 step 4a) in one launch.  Each CTA holds a contiguous range
+of the colour's active domains in (ax, ay, az) order, the same range in every
+cycle.  Between cycles it does not always wait for the whole grid:
+  - within a cycle, with the exact R_max, every CTA's step 1 precedes every
+    CTA's prepass and flip step (barrier 1, Sec. 3.1 step 2);
+  - after an even cycle, a CTA waits for the CTAs that share a row of domains
+    (fixed dy, dz) with its own items (the row waits);
+  - after an odd cycle t it waits for nobody with the exact R_max (barrier 1
+    of the next cycle orders what must be ordered); with the bounds of
+    Sec. 3.2 step 4b, which have no barrier 1, the whole grid meets.
+
+This test builds, on small lattices and for several grid sizes, every access
+of every cycle at the granularity of a domain's rows, each of its six ghost
+faces, and its count line:
+  - staging and step 1 read the rows, the ghost faces and the count line of
+    the active domain;
+  - the flip step reads the rows of its face and edge neighbours (sites two
+    steps out, diagonal sites), XORs bits into its own rows and into the
+    ghost faces of its face neighbours that mirror it, adds class moves to
+    their count lines (atomics, which commute among themselves) and stores its
+    own count line (a plain store).
+Each pair of accesses of different CTAs in different cycles that conflict
+(a write against a read, or a plain store against any write) must be ordered
+by the kernel's happens-before relation: program order in each CTA, barrier 1,
+the row waits and the grid barriers.  A plausible mistake in the schedule --
+the row wait taken after odd cycles instead of even ones, the row wait
+narrowed to the CTA itself, or, with the bounds, the grid barrier skipped
+after t = 3, 7 mod 8 (where cycles t + 1 and t + 2 follow without one, so
+the flip steps of cycles t - 1 and t + 1, and of t and t + 2, whose colours
+differ in the y and z bits, could overlap) -- must fail it."""
+import itertools
+
+import pytest
+
+
+def items(nd):
+    h = nd // 2
+    return h * h * h
+
+
+def domain_of(a, c, nd):
+    """Active domain of item a in colour c (parity bits x, y, z)."""
+    h = nd // 2
+    ax, ay, az = a % h, (a // h) % h, a // (h * h)
+    return (2 * ax + (c & 1), 2 * ay + ((c >> 1) & 1), 2 * az + ((c >> 2) & 1))
+
+
+def shift(d, delta, nd):
+    return tuple((d[i] + delta[i]) % nd for i in range(3))
+
+
+UNIT = [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]
+EDGE = [tuple(sa * (i == a) + sb * (i == b) for i in range(3))
+        for a, b in itertools.combinations(range(3), 2) for sa in (-1, 1) for sb in (-1, 1)]
+
+
+def accesses(dom, nd):
+    """(phase, object, kind) of one active domain's cycle; phase 0 = staging and
+    step 1, phase 1 = prepass and flip step; kind r = read, a = atomic write,
+    w = plain write.  A block is its rows and its six ghost faces; ghost face
+    i of D mirrors the boundary plane of D's neighbour across direction i."""
+    faces = [shift(dom, u, nd) for u in UNIT]
+    edges = [shift(dom, e, nd) for e in EDGE]
+    acc = [(0, ("rows", dom), "r")] + [(0, ("ghost", dom, i), "r") for i in range(6)]
+    acc += [(0, ("cnt", dom), "r")]
+    # the flip step reads the rows of the face and edge neighbours
+    acc += [(1, ("rows", f), "r") for f in faces] + [(1, ("rows", e), "r") for e in edges]
+    # and writes the flipped bit, the ghost face of each face neighbour that
+    # mirrors this domain (direction i ^ 1 seen from the neighbour), the class
+    # moves of the neighbours' sites and its own count line
+    acc += [(1, ("rows", dom), "a")] + [(1, ("ghost", f, i ^ 1), "a") for i, f in enumerate(faces)]
+    acc += [(1, ("cnt", f), "a") for f in faces] + [(1, ("cnt", dom), "w")]
+    return acc
+
+
+def conflict(k1, k2):
+    if k1 == "r" and k2 == "r":
+        return False
+    if k1 == "a" and k2 == "a":
+        return False  # atomic adds and XORs commute
+    return True
+
+
+def cta_ranges(nd, G):
+    Q = items(nd)
+    return [(Q * b // G, Q * (b + 1) // G) for b in range(G)]
+
+
+def owner(a, ranges):
+    for b, (lo, hi) in enumerate(ranges):
+        if lo <= a < hi:
+            return b
+    raise AssertionError(a)
+
+
+def row_wait_set(b, ranges, nd):
+    """CTAs that hold items of a row (fixed ay, az) that CTA b holds items of."""
+    lo, hi = ranges[b]
+    if lo >= hi:
+        return {b}
+    h = nd // 2
+    r0, r1 = (lo // h) * h, (hi - 1) // h * h + h - 1
+    return {owner(r0, ranges), owner(r1, ranges)} | set(range(owner(r0, ranges), owner(r1, ranges) + 1))
+
+
+def end_sync(t, mode):
+    """What the kernel does after cycle t (t = the lattice's cycle index)."""
+    if t % 2 == 0:
+        return "row"
+    return "none" if mode == "exact" else "grid"
+
+
+def happens_before(nd, G, mode, t0, ncycles, end_rule=end_sync, row_rule=row_wait_set):
+    """Reachability between the events of every CTA's cycles: node (b, g, k)
+    with k = 0 start, 1 end of step 1 (arrival), 2 start of the prepass,
+    3 end of the flip step.  Returns a function hb(u, v)."""
+    ranges = cta_ranges(nd, G)
+    succ = {}
+
+    def edge(u, v):
+        succ.setdefault(u, set()).add(v)
+
+    for b in range(G):
+        for g in range(ncycles):
+            edge((b, g, 0), (b, g, 1))
+            edge((b, g, 1), (b, g, 2))
+            edge((b, g, 2), (b, g, 3))
+            if g + 1 < ncycles:
+                edge((b, g, 3), (b, g + 1, 0))
+    for g in range(ncycles):
+        t = t0 + g
+        if mode == "exact":
+            for x in range(G):
+                for y in range(G):
+                    edge((y, g, 1), (x, g, 2))
+        if g + 1 < ncycles:
+            kind = end_rule(t, mode)
+            for x in range(G):
+                if kind == "grid":
+                    src = range(G)
+                elif kind == "row":
+                    src = row_rule(x, ranges, nd)
+                else:
+                    src = ()
+                for y in src:
+                    edge((y, g, 3), (x, g + 1, 0))
+    reach = {}
+
+    def closure(u):
+        if u in reach:
+            return reach[u]
+        seen, stack = set(), [u]
+        while stack:
+            w = stack.pop()
+            for v in succ.get(w, ()):
+                if v not in seen:
+                    seen.add(v)
+                    stack.append(v)
+        reach[u] = seen
+        return seen
+
+    return ranges, lambda u, v: v in closure(u)
+
+
+def unordered_conflicts(nd, G, mode, t0, ncycles, **kw):
+    ranges, hb = happens_before(nd, G, mode, t0, ncycles, **kw)
+    Q = items(nd)
+    by_obj = {}  # object -> list of (g, cta, phase, kind)
+    for g in range(ncycles):
+        c = (t0 + g) % 8
+        for a in range(Q):
+            b = owner(a, ranges)
+            for ph, obj, kind in accesses(domain_of(a, c, nd), nd):
+                by_obj.setdefault(obj, []).append((g, b, ph, kind))
+    bad = []
+    for obj, acc in by_obj.items():
+        for (g1, b1, p1, k1), (g2, b2, p2, k2) in itertools.combinations(sorted(acc), 2):
+            if g1 == g2 or b1 == b2 or not conflict(k1, k2):
+                continue
+            # the earlier cycle's access must end before the later one starts
+            u = (b1, g1, 1 if p1 == 0 else 3)
+            v = (b2, g2, 0 if p2 == 0 else 2)
+            if not hb(u, v):
+                bad.append((obj, (g1, b1, p1, k1), (g2, b2, p2, k2)))
+    return bad
+
+
+CASES = [(4, 3), (8, 3), (8, 5), (8, 7), (8, 16), (12, 20)]
+
+
+@pytest.mark.parametrize("mode", ["exact", "bound"])
+@pytest.mark.parametrize("nd,G", CASES)
+@pytest.mark.parametrize("t0", [0, 1, 3, 6])
+def test_kernel_schedule_orders_every_conflict(nd, G, mode, t0):
+    assert unordered_conflicts(nd, G, mode, t0, 12) == []
+
+
+def test_row_waits_after_odd_cycles_fail():
+    def swapped(t, mode):
+        r = end_sync(t, mode)
+        return "row" if t % 2 == 1 and r == "none" else ("none" if r == "row" else r)
+    assert unordered_conflicts(8, 5, "exact", 0, 12, end_rule=swapped)
+
+
+def test_bound_modes_need_a_barrier_after_every_odd_cycle():
+    def skip_3_7(t, mode):  # the barrier after t = 3, 7 mod 8 skipped
+        r = end_sync(t, mode)
+        return "none" if r == "grid" and t % 4 == 3 else r
+
+    def skip_1_5(t, mode):
+        r = end_sync(t, mode)
+        return "none" if r == "grid" and t % 4 == 1 else r
+    assert unordered_conflicts(8, 5, "bound", 0, 12, end_rule=skip_1_5)
+    bad = unordered_conflicts(8, 5, "bound", 0, 12, end_rule=skip_3_7)
+    assert bad
+    # without the barrier after t = 3, 7 what goes unordered is the flip steps
+    # of cycles t - 1 and t + 1, or t and t + 2: colours two cycles apart that
+    # differ in the y and z bits
+    assert all(p1 == p2 == 1 for _, (g1, b1, p1, k1), (g2, b2, p2, k2) in bad)
+    assert {(g1 % 8, g2 % 8) for _, (g1, *_), (g2, *_) in bad} <= {(2, 4), (3, 5), (6, 0), (7, 1)}
+
+
+def test_row_wait_on_the_cta_alone_fails():
+    assert unordered_conflicts(8, 5, "exact", 0, 12, row_rule=lambda b, ranges, nd: {b})

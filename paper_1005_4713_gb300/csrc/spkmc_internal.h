@@ -39,6 +39,7 @@ constexpr int kPadRow = kMaxEdge + 2;           // padded rows per axis
 constexpr int kPadWords = kPadRow * kPadRow;    // words of one padded domain
 constexpr int kMaxSegPerCta = 64;               // lattices one CTA may touch
 constexpr int kMaxDoneCtas = 4096;              // CTAs of a launch that can use the row waits
+constexpr int kMaxYz = 128;         // CTAs a yz wait lists before it waits for every CTA
 constexpr int kDoneStride = 32;                 // one counter per 128-byte line: CTAs publish and
                                                 // poll without sharing a line
 
@@ -121,6 +122,7 @@ struct LaunchParams {
     int exact_any;        // some lattice pads to the exact R_max: reduce before the events
     int sub2_any;         // some lattice uses two random colours: draw colours, recount
     int rec_n;            // records per lattice (rec_every > 0)
+    int phase4;           // t % 4 shared by all running lattices at launch, -1 if mixed or unknown
     int64_t rec_every;    // record after every rec_every cycles of the launch; 0 = none
     ObsRaw *rec;          // [slot][rec_n] records
 };

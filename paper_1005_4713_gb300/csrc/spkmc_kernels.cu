@@ -80,6 +80,8 @@ struct CtaShared {
     int early_bytes; // bytes requested at the start of the cycle (one-round CTAs)
     int ok;
     int nb_lo, nb_hi; // CTAs whose items share a domain row with this CTA's (this one included)
+    int nyz;          // CTAs of the yz wait (below), in yz[]; -1: every CTA
+    short yz[kMaxYz];
     WorkItem work[kThreads];
 };
 
@@ -173,6 +175,45 @@ __device__ bool row_wait(const LaunchParams &P, CtaShared &S, long long g)
     int ok = 1;
     const int c = S.nb_lo + (int)threadIdx.x;
     if (c <= S.nb_hi && c != (int)blockIdx.x) {
+        const long long t0 = global_timer_ns();
+        unsigned polls = 0;
+        while (ld_acquire_u32(&P.done[(long long)c * kDoneStride]) < (unsigned)(g + 1)) {
+            ++polls;
+            if ((polls & 15u) == 0) {
+                if (ld_volatile_int(P.err) != 0) {
+                    ok = 0;
+                    break;
+                }
+                if (global_timer_ns() - t0 > P.timeout_ns || polls > (1u << 28)) {
+                    raise_error(P.err, SPKMC_ETIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+            __nanosleep(32);
+        }
+    }
+    return __syncthreads_and(ok) != 0;
+}
+
+// After an odd cycle t = 3, 7 mod 8 with the bounds of Sec. 3.2 step 4b (no
+// barrier 1): the flip steps of cycles t - 1 and t + 1, and of t and t + 2,
+// whose colours differ in the y and z bits, read and write yz-diagonal
+// domains, so a CTA waits for the CTAs holding the rows one y step back, in
+// its own plane and one z step either way (S.yz), to have finished cycle t.
+// The grid barrier after t = 1, 5 mod 8 still bounds the drift of any two
+// CTAs to four cycles, as the ring of exact R_max maxima needs.  Bounded like
+// the grid barrier; returns false on a timeout or another CTA's error.
+__device__ bool yz_wait(const LaunchParams &P, CtaShared &S, long long g)
+{
+    __syncthreads();
+    if (threadIdx.x == 0 && (int)blockIdx.x != P.skip_cta)
+        st_release_u32(&P.done[(long long)blockIdx.x * kDoneStride], (unsigned)(g + 1));
+    int ok = 1;
+    const int n = S.nyz < 0 ? (int)gridDim.x : S.nyz;
+    for (int i = threadIdx.x; i < n && ok; i += blockDim.x) {
+        const int c = S.nyz < 0 ? i : S.yz[i];
+        if (c == (int)blockIdx.x) continue;
         const long long t0 = global_timer_ns();
         unsigned polls = 0;
         while (ld_acquire_u32(&P.done[(long long)c * kDoneStride]) < (unsigned)(g + 1)) {
@@ -1417,6 +1458,13 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
         // the CTAs whose items share a domain row (half items of one lattice,
         // fixed dy and dz) with this CTA's first and last items
         S.nb_lo = S.nb_hi = (int)blockIdx.x;
+        // the CTA that holds item q
+        auto owner = [&](long long q) {
+            long long c = (q * G) / P.Q;
+            while (c + 1 < G && (P.Q * (c + 1)) / G <= q) ++c;
+            while (c > 0 && (P.Q * c) / G > q) --c;
+            return (int)c;
+        };
         if (P.done && S.ok && n > 0 && lo < hi) {
             auto row_edge = [&](long long q, bool end) {
                 int j = 0;
@@ -1425,17 +1473,41 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
                 const long long r0 = sb + ((q - sb) / h) * h;
                 return end ? r0 + h - 1 : r0;
             };
-            auto owner = [&](long long q) {
-                long long c = (q * G) / P.Q;
-                while (c + 1 < G && (P.Q * (c + 1)) / G <= q) ++c;
-                while (c > 0 && (P.Q * c) / G > q) --c;
-                return (int)c;
-            };
             S.nb_lo = owner(row_edge(lo, false));
             S.nb_hi = owner(row_edge(hi - 1, true));
             if (S.nb_hi - S.nb_lo + 1 > kThreads) { // cannot happen with a segment table the host accepted
                 raise_error(P.err, SPKMC_EINTERNAL);
                 S.ok = 0;
+            }
+        }
+        // The CTAs of the yz wait (one lattice, the bounds of Sec. 3.2 step
+        // 4b; see the kernel loop): those holding, for a row of this CTA's
+        // items at (ay, az), the rows (ay - 1, ay) of the planes (az - 1, az,
+        // az + 1), each index wrapping.  A run of rows within one plane (with
+        // the row ay = 0 on its own when it wraps) maps to a run of whole rows
+        // in each image plane, whose owners are a contiguous range of CTAs.
+        S.nyz = 0;
+        if (P.done && P.nseg == 1 && S.ok && lo < hi) {
+            const long long h = P.desc[P.seg[0].slot].half;
+            const long long r0 = lo / h, r1 = (hi - 1) / h;
+            for (int dz = -1; dz <= 1 && S.nyz >= 0; ++dz) {
+                for (int dy = -1; dy <= 0 && S.nyz >= 0; ++dy) {
+                    for (long long r = r0; r <= r1 && S.nyz >= 0;) {
+                        const long long ay = r % h, az = r / h;
+                        long long e = (az + 1) * h - 1 < r1 ? (az + 1) * h - 1 : r1;
+                        if (dy < 0 && ay == 0) e = r;
+                        const long long first = ((ay + dy + h) % h + h * (((az + dz) % h + h) % h)) * h;
+                        const int c0 = owner(first), c1 = owner(first + (e - r + 1) * h - 1);
+                        for (int c = c0; c <= c1 && S.nyz >= 0; ++c) {
+                            bool seen = false;
+                            for (int i = 0; i < S.nyz; ++i) seen = seen || S.yz[i] == c;
+                            if (seen) continue;
+                            if (S.nyz == kMaxYz) S.nyz = -1; // too many: wait for every CTA
+                            else S.yz[S.nyz++] = (short)c;
+                        }
+                        r = e + 1;
+                    }
+                }
             }
         }
     }
@@ -1577,16 +1649,23 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
             // mod 8 (their colours differ in the y and z bits).  With the
             // exact R_max, barrier 1 of cycle t + 1, which a CTA reaches only
             // after its flips of cycle t, orders both.  Without it (the
-            // bounds of Sec. 3.2 step 4b), the whole grid meets after every
-            // odd cycle; the row waits after even cycles order the rest
-            // (tests/test_sync_schedule.py checks the schedule).
+            // bounds of Sec. 3.2 step 4b), the whole grid meets after
+            // t = 1, 5 mod 8 and, for one lattice whose t mod 4 the launch
+            // knows, a CTA waits after t = 3, 7 mod 8 only for the CTAs of
+            // its yz-diagonal domains (yz_wait); otherwise the whole grid
+            // meets there too.  The row waits after even cycles order the
+            // rest (tests/test_sync_schedule.py checks the schedule).
             const bool odd = P.parity0 >= 0 && (((long long)P.parity0 + g) & 1LL) == 1LL;
             const bool even = P.parity0 >= 0 && !odd;
             const bool skip = odd && P.exact_any;
+            const bool yz = odd && !P.exact_any && P.done && P.nseg == 1 && P.phase4 >= 0 &&
+                            (((long long)P.phase4 + g) & 3LL) == 3LL;
             if (skip) {
                 __syncthreads();
             } else if (even && P.done) {
                 if (!row_wait(P, S, g)) return;
+            } else if (yz) {
+                if (!yz_wait(P, S, g)) return;
             } else if (!grid_barrier(P, S, epoch)) {
                 return;
             }

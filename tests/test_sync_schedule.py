@@ -144,6 +144,8 @@ def happens_before(nd, G, mode, t0, ncycles, end_rule=end_sync, row_rule=row_wai
                     src = range(G)
                 elif kind == "row":
                     src = row_rule(x, ranges, nd)
+                elif isinstance(kind, tuple) and kind[0] == "set":
+                    src = kind[1][x]
                 else:
                     src = ()
                 for y in src:
@@ -226,3 +228,112 @@ def test_bound_modes_need_a_barrier_after_every_odd_cycle():
 
 def test_row_wait_on_the_cta_alone_fails():
     assert unordered_conflicts(8, 5, "exact", 0, 12, row_rule=lambda b, ranges, nd: {b})
+
+
+def yz_wait_set(b, ranges, nd):
+    """CTAs that hold the items one row back (y - 1, wrapping within the plane)
+    or in the same row, in the same plane or one plane either way (z +- 1,
+    wrapping), of any item of CTA b: the CTAs whose flips two cycles apart
+    from b's touch domains yz-diagonal to b's."""
+    lo, hi = ranges[b]
+    h = nd // 2
+    Q = h ** 3
+    out = {b}
+    for a in range(lo, hi):
+        ax, ay, az = a % h, (a // h) % h, a // (h * h)
+        for dy in (-1, 0):
+            for dz in (-1, 0, 1):
+                a2 = ax + h * ((ay + dy) % h) + h * h * ((az + dz) % h)
+                out.add(owner(a2, ranges))
+    return out
+
+
+def local_3_7(t, mode):
+    """Bound modes with the grid barrier after t = 1, 5 mod 8 and the yz wait
+    after t = 3, 7."""
+    if t % 2 == 0:
+        return "row"
+    if mode == "exact":
+        return "none"
+    return "yz" if t % 4 == 3 else "grid"
+
+
+@pytest.mark.parametrize("nd,G", CASES)
+@pytest.mark.parametrize("t0", [0, 1, 3, 6])
+def test_bound_modes_with_yz_waits_after_t_3_7(nd, G, t0):
+    ranges = cta_ranges(nd, G)
+    yz = {b: yz_wait_set(b, ranges, nd) for b in range(G)}
+
+    def rule(t, mode):
+        r = local_3_7(t, mode)
+        return ("set", yz) if r == "yz" else r
+    assert unordered_conflicts(nd, G, "bound", t0, 12, end_rule=rule) == []
+
+
+def test_yz_wait_without_the_plane_neighbours_fails():
+    nd, G = 8, 5
+    ranges = cta_ranges(nd, G)
+
+    def same_plane(b, ranges_, nd_):
+        lo, hi = ranges_[b]
+        h = nd_ // 2
+        out = {b}
+        for a in range(lo, hi):
+            ax, ay, az = a % h, (a // h) % h, a // (h * h)
+            for dy in (-1, 0):
+                out.add(owner(ax + h * ((ay + dy) % h) + h * h * az, ranges_))
+        return out
+    sets = {b: same_plane(b, ranges, nd) for b in range(G)}
+
+    def rule(t, mode):
+        r = local_3_7(t, mode)
+        return ("set", sets) if r == "yz" else r
+    assert unordered_conflicts(nd, G, "bound", 0, 12, end_rule=rule)
+
+
+def yz_wait_rows(b, ranges, nd, max_list=128):
+    """The kernel's yz wait set (`yz_wait` in spkmc_kernels.cu): each run of
+    the CTA's rows within one plane (the row ay = 0 on its own when the y
+    shift wraps it) maps, for dy in (-1, 0) and dz in (-1, 0, 1), to a run of
+    whole rows of the image plane; every CTA holding an item of it is waited
+    for (every CTA when the list would pass max_list)."""
+    lo, hi = ranges[b]
+    h = nd // 2
+    out = []
+    if lo >= hi:
+        return {b}
+    r0, r1 = lo // h, (hi - 1) // h
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0):
+            r = r0
+            while r <= r1:
+                ay, az = r % h, r // h
+                e = min((az + 1) * h - 1, r1)
+                if dy < 0 and ay == 0:
+                    e = r
+                first = (((ay + dy) % h) + h * ((az + dz) % h)) * h
+                c0, c1 = owner(first, ranges), owner(first + (e - r + 1) * h - 1, ranges)
+                for c in range(c0, c1 + 1):
+                    if c not in out:
+                        out.append(c)
+                r = e + 1
+    if len(out) > max_list:
+        return set(range(len(ranges)))
+    return set(out) | {b}
+
+
+@pytest.mark.parametrize("nd,G", CASES + [(16, 30)])
+@pytest.mark.parametrize("t0", [0, 3])
+def test_kernel_yz_wait_set_covers_the_exact_one_and_orders_every_conflict(nd, G, t0):
+    ranges = cta_ranges(nd, G)
+    rows = {b: yz_wait_rows(b, ranges, nd) for b in range(G)}
+    for b in range(G):
+        assert yz_wait_set(b, ranges, nd) <= rows[b]
+
+    def rule(t, mode):
+        r = local_3_7(t, mode)
+        return ("set", rows) if r == "yz" else r
+    assert unordered_conflicts(nd, G, "bound", t0, 12, end_rule=rule) == []
+    # a list too short to hold the set falls back to every CTA, which is safe
+    full = {b: yz_wait_rows(b, ranges, nd, max_list=1) for b in range(G)}
+    assert all(full[b] == set(range(G)) or len(rows[b]) <= 1 for b in range(G))

@@ -1487,7 +1487,7 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
         // the row ay = 0 on its own when it wraps) maps to a run of whole rows
         // in each image plane, whose owners are a contiguous range of CTAs.
         S.nyz = 0;
-        if (P.done && P.nseg == 1 && S.ok && lo < hi) {
+        if (!P.exact_any && P.done && P.nseg == 1 && S.ok && lo < hi) {
             const long long h = P.desc[P.seg[0].slot].half;
             const long long r0 = lo / h, r1 = (hi - 1) / h;
             for (int dz = -1; dz <= 1 && S.nyz >= 0; ++dz) {

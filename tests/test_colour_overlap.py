@@ -5,11 +5,12 @@ parity bits of the domain coordinates).
 A flip moves the class of each neighbour site j of the flipped site, and
 the new class depends on the spins of all of j's neighbours.  Two colours
 whose flips may run at the same time must therefore have no site j next to
-both of them.  The cycle kernel lets cycle t + 1 (t odd) start without a
-grid barrier; without the exact R_max's barrier in between, the flips of the
-two cycles may overlap, which is safe only when the colours differ in all
+both of them.  Two consecutive cycles t, t + 1 (t odd) whose flips are not
+ordered by a barrier may overlap safely only when their colours differ in all
 three parity bits (t = 3, 7 mod 8).  This test enumerates the sites of a
-small lattice to confirm that statement for every pair of colours."""
+small lattice to confirm that statement for every pair of colours.  Whether
+the cycle kernel's barriers and waits order everything that must be ordered,
+across all cycles and CTAs, is checked by tests/test_sync_schedule.py."""
 import itertools
 
 import pytest

@@ -337,3 +337,108 @@ def test_kernel_yz_wait_set_covers_the_exact_one_and_orders_every_conflict(nd, G
     # a list too short to hold the set falls back to every CTA, which is safe
     full = {b: yz_wait_rows(b, ranges, nd, max_list=1) for b in range(G)}
     assert all(full[b] == set(range(G)) or len(rows[b]) <= 1 for b in range(G))
+
+
+# ---- several lattices in one launch (the batched ensembles and the served
+# stream): the lattices' active domains are concatenated in one item range,
+# each lattice keeps its own cycle index (all with the launch's parity), the
+# row waits use the segment-aware row edges, and with the bounds the grid
+# meets after every odd cycle (the yz wait is for single-lattice launches).
+
+def batch_unordered_conflicts(nds, t0s, modes, G, ncycles, own_rows_only=False):
+    assert len({t % 2 for t in t0s}) == 1  # the row waits need one parity
+    bases, Q = [], 0
+    for nd in nds:
+        bases.append(Q)
+        Q += items(nd)
+    ranges = [(Q * b // G, Q * (b + 1) // G) for b in range(G)]
+    exact_any = "exact" in modes
+
+    def seg_of(q):
+        j = 0
+        while j + 1 < len(bases) and bases[j + 1] <= q:
+            j += 1
+        return j
+
+    def row_edge(q, end):
+        j = seg_of(q)
+        h = nds[j] // 2
+        r0 = bases[j] + ((q - bases[j]) // h) * h
+        return r0 + h - 1 if end else r0
+
+    def rows(b, ranges_, nd_):
+        lo, hi = ranges_[b]
+        if lo >= hi or own_rows_only:
+            return {b}
+        c0, c1 = owner(row_edge(lo, False), ranges_), owner(row_edge(hi - 1, True), ranges_)
+        return set(range(c0, c1 + 1))
+
+    def rule(t, mode):  # t = the launch's cycle with the shared parity
+        if t % 2 == 0:
+            return "row"
+        return "none" if exact_any else "grid"
+
+    succ = {}
+
+    def edge(u, v):
+        succ.setdefault(u, set()).add(v)
+    for b in range(G):
+        for g in range(ncycles):
+            edge((b, g, 0), (b, g, 1))
+            edge((b, g, 1), (b, g, 2))
+            edge((b, g, 2), (b, g, 3))
+            if g + 1 < ncycles:
+                edge((b, g, 3), (b, g + 1, 0))
+    for g in range(ncycles):
+        if exact_any:
+            for x in range(G):
+                for y in range(G):
+                    edge((y, g, 1), (x, g, 2))
+        if g + 1 < ncycles:
+            kind = rule(t0s[0] + g, None)
+            for x in range(G):
+                src = range(G) if kind == "grid" else (rows(x, ranges, None) if kind == "row" else ())
+                for y in src:
+                    edge((y, g, 3), (x, g + 1, 0))
+    reach = {}
+
+    def hb2(u, v):
+        if u not in reach:
+            seen, stack = set(), [u]
+            while stack:
+                w = stack.pop()
+                for n in succ.get(w, ()):
+                    if n not in seen:
+                        seen.add(n)
+                        stack.append(n)
+            reach[u] = seen
+        return v in reach[u]
+
+    by_obj = {}
+    for g in range(ncycles):
+        for j, nd in enumerate(nds):
+            c = (t0s[j] + g) % 8
+            for a in range(items(nd)):
+                b = owner(bases[j] + a, ranges)
+                for ph, obj, kind in accesses(domain_of(a, c, nd), nd):
+                    by_obj.setdefault((j,) + obj, []).append((g, b, ph, kind))
+    bad = []
+    for obj, acc in by_obj.items():
+        for (g1, b1, p1, k1), (g2, b2, p2, k2) in itertools.combinations(sorted(acc), 2):
+            if g1 == g2 or b1 == b2 or not conflict(k1, k2):
+                continue
+            if not hb2((b1, g1, 1 if p1 == 0 else 3), (b2, g2, 0 if p2 == 0 else 2)):
+                bad.append((obj, (g1, b1, p1, k1), (g2, b2, p2, k2)))
+    return bad
+
+
+@pytest.mark.parametrize("nds,t0s", [((4, 8), (0, 2)), ((8, 4, 4), (1, 5, 3)), ((4, 4, 8), (6, 0, 2))])
+@pytest.mark.parametrize("modes", [("exact",), ("bound",), ("exact", "bound")])
+@pytest.mark.parametrize("G", [3, 5, 9])
+def test_batched_launch_schedule_orders_every_conflict(nds, t0s, modes, G):
+    mode_of = [modes[i % len(modes)] for i in range(len(nds))]
+    assert batch_unordered_conflicts(nds, t0s, mode_of, G, 10) == []
+
+
+def test_batched_row_wait_on_the_cta_alone_fails():
+    assert batch_unordered_conflicts((4, 8), (0, 2), ("exact", "exact"), 5, 10, own_rows_only=True)

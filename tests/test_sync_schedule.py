@@ -23,6 +23,10 @@ faces, and its count line:
     ghost faces of its face neighbours that mirror it, adds class moves to
     their count lines (atomics, which commute among themselves) and stores its
     own count line (a plain store).
+  - the ring of exact R_max maxima: every CTA's maximum of cycle t into slot
+    t mod 16 (an atomic), the clear of slot t + 4 by the CTA holding the
+    first domain, and the read of slot t (exact, after barrier 1) or t - 8
+    (the learned bound, at the start of the cycle).
 Each pair of accesses of different CTAs in different cycles that conflict
 (a write against a read, or a plain store against any write) must be ordered
 by the kernel's happens-before relation: program order in each CTA, barrier 1,
@@ -168,6 +172,22 @@ def happens_before(nd, G, mode, t0, ncycles, end_rule=end_sync, row_rule=row_wai
     return ranges, lambda u, v: v in closure(u)
 
 
+def ring_accesses(t, b, first, mode):
+    """The ring of exact R_max maxima (16 slots, cycle t in slot t mod 16): in
+    cycle t every CTA takes its maximum into slot t after step 1 (an atomic);
+    the CTA holding the lattice's first domain clears slot t + 4 in its prepass
+    (a plain store); the exact mode reads slot t in the prepass, after barrier
+    1, and the learned bound reads slot t - 8 at the start of the cycle."""
+    acc = [(0, ("ring", t % 16), "a")]
+    if b == first:
+        acc.append((1, ("ring", (t + 4) % 16), "w"))
+    if mode == "exact":
+        acc.append((1, ("ring", t % 16), "r"))
+    else:
+        acc.append((0, ("ring", (t - 8) % 16), "r"))
+    return acc
+
+
 def unordered_conflicts(nd, G, mode, t0, ncycles, **kw):
     ranges, hb = happens_before(nd, G, mode, t0, ncycles, **kw)
     Q = items(nd)
@@ -178,6 +198,14 @@ def unordered_conflicts(nd, G, mode, t0, ncycles, **kw):
             b = owner(a, ranges)
             for ph, obj, kind in accesses(domain_of(a, c, nd), nd):
                 by_obj.setdefault(obj, []).append((g, b, ph, kind))
+        # the ring (every CTA with items takes part; the first domain's CTA clears)
+        for b in range(G):
+            if ranges[b][0] < ranges[b][1]:
+                for ph, obj, kind in ring_accesses(t0 + g, b, owner(0, ranges), mode):
+                    # a learned read of a slot written before the launch is not a conflict here
+                    if kind == "r" and mode != "exact" and g < 8:
+                        continue
+                    by_obj.setdefault(obj, []).append((g, b, ph, kind))
     bad = []
     for obj, acc in by_obj.items():
         for (g1, b1, p1, k1), (g2, b2, p2, k2) in itertools.combinations(sorted(acc), 2):
@@ -191,7 +219,7 @@ def unordered_conflicts(nd, G, mode, t0, ncycles, **kw):
     return bad
 
 
-CASES = [(4, 3), (8, 3), (8, 5), (8, 7), (8, 16), (12, 20)]
+CASES = [(4, 3), (8, 3), (8, 5), (8, 7), (8, 16), (12, 20), (16, 30)]
 
 
 @pytest.mark.parametrize("mode", ["exact", "bound"])
@@ -322,7 +350,7 @@ def yz_wait_rows(b, ranges, nd, max_list=128):
     return set(out) | {b}
 
 
-@pytest.mark.parametrize("nd,G", CASES + [(16, 30)])
+@pytest.mark.parametrize("nd,G", CASES)
 @pytest.mark.parametrize("t0", [0, 3])
 def test_kernel_yz_wait_set_covers_the_exact_one_and_orders_every_conflict(nd, G, t0):
     ranges = cta_ranges(nd, G)
@@ -442,3 +470,23 @@ def test_batched_launch_schedule_orders_every_conflict(nds, t0s, modes, G):
 
 def test_batched_row_wait_on_the_cta_alone_fails():
     assert batch_unordered_conflicts((4, 8), (0, 2), ("exact", "exact"), 5, 10, own_rows_only=True)
+
+
+def test_without_the_barriers_after_t_1_5_the_ring_races():
+    # on a lattice large enough that the yz waits are local, waiting only
+    # locally after every odd cycle lets the CTAs drift more than four cycles
+    # apart, and the clear of a ring slot races with its maxima and reads
+    nd, G = 16, 30
+    ranges = cta_ranges(nd, G)
+    yz = {b: yz_wait_rows(b, ranges, nd) for b in range(G)}
+    assert max(len(v) for v in yz.values()) < G // 2
+
+    def all_local(t, mode):
+        return "row" if t % 2 == 0 else ("set", yz)
+    bad = unordered_conflicts(nd, G, "bound", 0, 20, end_rule=all_local)
+    assert any(obj[0] == "ring" for obj, *_ in bad)
+
+    def committed(t, mode):
+        r = local_3_7(t, mode)
+        return ("set", yz) if r == "yz" else r
+    assert unordered_conflicts(nd, G, "bound", 0, 20, end_rule=committed) == []

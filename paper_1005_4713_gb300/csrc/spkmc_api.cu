@@ -259,7 +259,6 @@ struct spkmc_batch {
     int max_blocks_per_sm = 0;
     int last_grid = 0;
     int sticky_error = SPKMC_OK;
-    bool phase_unknown = false; // launches being captured for replays at other t % 4
     std::vector<Segment> uploaded_seg; // segment table currently on the device
     long long live_bytes = 0;
     // second stream and events of the layer-pipelined spin write (made on
@@ -539,15 +538,14 @@ int admit(spkmc_batch *b, const spkmc_params *p, long long cycles, int slot_hint
 }
 
 // The flat table of the running lattices (those with cycles left), their
-// total active domains Q and the shared cycle parity and t % 4 (-1 if mixed), uploaded
+// total active domains Q and the shared cycle parity (-1 if mixed), uploaded
 // to the device if it changed (which synchronises the stream first: the
 // pinned staging copy is reused).
-int segment_table(spkmc_batch *b, std::vector<Segment> &segs, long long &Q, int &parity, int &phase4)
+int segment_table(spkmc_batch *b, std::vector<Segment> &segs, long long &Q, int &parity)
 {
     segs.clear();
     Q = 0;
     parity = -2;
-    phase4 = -2;
     for (int i = 0; i < b->capacity; ++i) {
         Slot &s = b->slots[i];
         if (!s.live || s.budget == 0) continue;
@@ -559,8 +557,6 @@ int segment_table(spkmc_batch *b, std::vector<Segment> &segs, long long &Q, int 
         Q += s.sz.Kact;
         const int par = (int)(s.t & 1);
         parity = parity == -2 ? par : (parity == par ? parity : -1);
-        const int ph = (int)(s.t & 3);
-        phase4 = phase4 == -2 ? ph : (phase4 == ph ? phase4 : -1);
     }
     const int nseg = (int)segs.size();
     if (nseg == 0) return SPKMC_OK;
@@ -598,8 +594,8 @@ int run(spkmc_batch *b, long long cycles, const RecReq *rq = nullptr)
         const long long n = std::min(cycles, kChunk);
         std::vector<Segment> segs;
         long long Q = 0;
-        int parity = -2, phase4 = -2;
-        int rc0 = segment_table(b, segs, Q, parity, phase4);
+        int parity = -2;
+        int rc0 = segment_table(b, segs, Q, parity);
         if (rc0) return rc0;
         const int nseg = (int)segs.size();
         if (nseg == 0) return SPKMC_OK;
@@ -638,7 +634,6 @@ int run(spkmc_batch *b, long long cycles, const RecReq *rq = nullptr)
         P.seg = b->d_seg;
         P.nseg = nseg;
         P.parity0 = parity < 0 ? -1 : parity;
-        P.phase4 = phase4 < 0 || b->phase_unknown ? -1 : phase4;
         P.Q = Q;
         P.ncycles = n;
         P.bar = b->d_bar;
@@ -1082,18 +1077,15 @@ int spkmc_graph_create(spkmc_t *h, int64_t cycles_per_step, int32_t steps, spkmc
     if (rc) return rc;
     std::vector<Segment> segs;
     long long Q = 0;
-    int parity = -2, phase4 = -2;
-    if ((rc = segment_table(b, segs, Q, parity, phase4)) != SPKMC_OK) return rc; // uploads outside the capture
+    int parity = -2;
+    if ((rc = segment_table(b, segs, Q, parity)) != SPKMC_OK) return rc; // uploads outside the capture
     Slot &s = b->slots[h->slot];
     const long long t_saved = s.t, budget_saved = s.budget;
     CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-    // a replay that does not advance t by a multiple of 4 cannot bake in t % 4
-    b->phase_unknown = (cycles_per_step * (long long)steps) % 4 != 0;
     for (int i = 0; i < steps && rc == SPKMC_OK; ++i) {
         rc = run(b, cycles_per_step);
         if (rc == SPKMC_OK && host_obs) rc = spkmc_observables_async(h, host_obs + i);
     }
-    b->phase_unknown = false;
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(b->stream, &graph);
     s.t = t_saved; // nothing ran yet
@@ -1596,7 +1588,6 @@ extern "C" int spkmc_run_cycles_noalloc(const spkmc_params *p, int8_t *dev_spins
         P.seg = d_seg;
         P.nseg = 1;
         P.parity0 = (int)(t & 1);
-        P.phase4 = (int)(t & 3);
         P.Q = sz.Kact;
         P.ncycles = n;
         P.bar = d_bar;

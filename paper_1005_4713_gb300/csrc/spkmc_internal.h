@@ -39,7 +39,7 @@ constexpr int kPadRow = kMaxEdge + 2;           // padded rows per axis
 constexpr int kPadWords = kPadRow * kPadRow;    // words of one padded domain
 constexpr int kMaxSegPerCta = 64;               // lattices one CTA may touch
 constexpr int kMaxDoneCtas = 4096;              // CTAs of a launch that can use the row waits
-constexpr int kMaxYz = 128;         // CTAs a yz wait lists before it waits for every CTA
+constexpr int kMaxNear = 128;       // CTAs a near wait lists before it waits for every CTA
 constexpr int kDoneStride = 32;                 // one counter per 128-byte line: CTAs publish and
                                                 // poll without sharing a line
 
@@ -63,7 +63,7 @@ struct LatticeDesc {
 };
 
 constexpr double kBoundSlack = 1.0 + 0x1p-32; // rounding cover of the R_max bounds
-constexpr int kRmaxRing = 16;                 // exact R_max of cycle t in slot t % 16
+constexpr int kRmaxRing = 32;                 // exact R_max of cycle t in slot t % 32
 
 // Per-lattice state written by the persistent kernel.
 struct LatticeState {
@@ -74,9 +74,9 @@ struct LatticeState {
     unsigned long long null_fx_lo;  // sum of floor(r_0k * 2^64), 128-bit
     unsigned long long null_fx_hi;
     int64_t budget;                 // cycles left; < 0 = unlimited
-    unsigned long long rmax[kRmaxRing]; // exact R_max bit patterns of cycle t in slot t % 16:
+    unsigned long long rmax[kRmaxRing]; // exact R_max bit patterns of cycle t in slot t % 32:
                                         // written at t, read at t (exact) or t + 8
-                                        // (learned), cleared at t - 12
+                                        // (learned), cleared at t + 24
     long long M;                    // sum of spins, kept exact flip by flip
     long long B;                    // forward bond sum, kept exact flip by flip
 };
@@ -122,7 +122,6 @@ struct LaunchParams {
     int exact_any;        // some lattice pads to the exact R_max: reduce before the events
     int sub2_any;         // some lattice uses two random colours: draw colours, recount
     int rec_n;            // records per lattice (rec_every > 0)
-    int phase4;           // t % 4 shared by all running lattices at launch, -1 if mixed or unknown
     int64_t rec_every;    // record after every rec_every cycles of the launch; 0 = none
     ObsRaw *rec;          // [slot][rec_n] records
 };

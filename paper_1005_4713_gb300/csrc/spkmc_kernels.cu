@@ -80,8 +80,8 @@ struct CtaShared {
     int early_bytes; // bytes requested at the start of the cycle (one-round CTAs)
     int ok;
     int nb_lo, nb_hi; // CTAs whose items share a domain row with this CTA's (this one included)
-    int nyz;          // CTAs of the yz wait (below), in yz[]; -1: every CTA
-    short yz[kMaxYz];
+    int nnear;        // CTAs of the near wait (below), in near[]; -1: every CTA
+    short near[kMaxNear];
     WorkItem work[kThreads];
 };
 
@@ -196,23 +196,22 @@ __device__ bool row_wait(const LaunchParams &P, CtaShared &S, long long g)
     return __syncthreads_and(ok) != 0;
 }
 
-// After an odd cycle t = 3, 7 mod 8 with the bounds of Sec. 3.2 step 4b (no
-// barrier 1): the flip steps of cycles t - 1 and t + 1, and of t and t + 2,
-// whose colours differ in the y and z bits, read and write yz-diagonal
-// domains, so a CTA waits for the CTAs holding the rows one y step back, in
-// its own plane and one z step either way (S.yz), to have finished cycle t.
-// The grid barrier after t = 1, 5 mod 8 still bounds the drift of any two
-// CTAs to four cycles, as the ring of exact R_max maxima needs.  Bounded like
-// the grid barrier; returns false on a timeout or another CTA's error.
-__device__ bool yz_wait(const LaunchParams &P, CtaShared &S, long long g)
+// After an odd cycle with the bounds of Sec. 3.2 step 4b (no barrier 1), a
+// CTA waits for the CTAs holding the rows within one y step of its own rows,
+// in its own plane and one z step either way (S.near), to have finished the
+// cycle.  That orders the flip steps of colours one or two cycles apart that
+// differ in two bits (they read and write domains diagonal to each other) and
+// the y and z neighbours that the next colour stages and counts.  Bounded
+// like the grid barrier; returns false on a timeout or another CTA's error.
+__device__ bool near_wait(const LaunchParams &P, CtaShared &S, long long g)
 {
     __syncthreads();
     if (threadIdx.x == 0 && (int)blockIdx.x != P.skip_cta)
         st_release_u32(&P.done[(long long)blockIdx.x * kDoneStride], (unsigned)(g + 1));
     int ok = 1;
-    const int n = S.nyz < 0 ? (int)gridDim.x : S.nyz;
+    const int n = S.nnear < 0 ? (int)gridDim.x : S.nnear;
     for (int i = threadIdx.x; i < n && ok; i += blockDim.x) {
-        const int c = S.nyz < 0 ? i : S.yz[i];
+        const int c = S.nnear < 0 ? i : S.near[i];
         if (c == (int)blockIdx.x) continue;
         const long long t0 = global_timer_ns();
         unsigned polls = 0;
@@ -1239,8 +1238,8 @@ __device__ __forceinline__ void phase_b_round(const LaunchParams &P, CtaShared &
                 if (a == 0) {
                     S.seg_rnow[ls] = R; // the clock moves once this cycle (step 5)
                     S.seg_tick[ls] = 1;
-                    // slot of cycle t - 12, last read at t - 4: free for t + 4
-                    P.state[slot].rmax[(t + 4) & (kRmaxRing - 1)] = 0ULL;
+                    // slot of cycle t - 24, last read at t - 16: free for t + 8
+                    P.state[slot].rmax[(t + 8) & (kRmaxRing - 1)] = 0ULL;
                 }
             } else {
                 ls = -1;
@@ -1480,30 +1479,32 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
                 S.ok = 0;
             }
         }
-        // The CTAs of the yz wait (one lattice, the bounds of Sec. 3.2 step
-        // 4b; see the kernel loop): those holding, for a row of this CTA's
-        // items at (ay, az), the rows (ay - 1, ay) of the planes (az - 1, az,
-        // az + 1), each index wrapping.  A run of rows within one plane (with
-        // the row ay = 0 on its own when it wraps) maps to a run of whole rows
-        // in each image plane, whose owners are a contiguous range of CTAs.
-        S.nyz = 0;
+        // The CTAs of the near wait (one lattice, the bounds of Sec. 3.2
+        // step 4b; see the kernel loop): those holding, for a row of this
+        // CTA's items at (ay, az), the rows ay - 1, ay, ay + 1 of the planes
+        // az - 1, az, az + 1, each index wrapping.  A run of rows within one
+        // plane (with the row that a y step wraps taken on its own) maps to a
+        // run of whole rows in each image plane, whose owners are a
+        // contiguous range of CTAs.
+        S.nnear = 0;
         if (!P.exact_any && P.done && P.nseg == 1 && S.ok && lo < hi) {
             const long long h = P.desc[P.seg[0].slot].half;
             const long long r0 = lo / h, r1 = (hi - 1) / h;
-            for (int dz = -1; dz <= 1 && S.nyz >= 0; ++dz) {
-                for (int dy = -1; dy <= 0 && S.nyz >= 0; ++dy) {
-                    for (long long r = r0; r <= r1 && S.nyz >= 0;) {
+            for (int dz = -1; dz <= 1 && S.nnear >= 0; ++dz) {
+                for (int dy = -1; dy <= 1 && S.nnear >= 0; ++dy) {
+                    for (long long r = r0; r <= r1 && S.nnear >= 0;) {
                         const long long ay = r % h, az = r / h;
                         long long e = (az + 1) * h - 1 < r1 ? (az + 1) * h - 1 : r1;
-                        if (dy < 0 && ay == 0) e = r;
+                        if ((dy < 0 && ay == 0) || (dy > 0 && ay == h - 1)) e = r;
+                        else if (dy > 0 && e > az * h + h - 2) e = az * h + h - 2;
                         const long long first = ((ay + dy + h) % h + h * (((az + dz) % h + h) % h)) * h;
                         const int c0 = owner(first), c1 = owner(first + (e - r + 1) * h - 1);
-                        for (int c = c0; c <= c1 && S.nyz >= 0; ++c) {
+                        for (int c = c0; c <= c1 && S.nnear >= 0; ++c) {
                             bool seen = false;
-                            for (int i = 0; i < S.nyz; ++i) seen = seen || S.yz[i] == c;
+                            for (int k = 0; k < S.nnear; ++k) seen = seen || S.near[k] == c;
                             if (seen) continue;
-                            if (S.nyz == kMaxYz) S.nyz = -1; // too many: wait for every CTA
-                            else S.yz[S.nyz++] = (short)c;
+                            if (S.nnear == kMaxNear) S.nnear = -1; // too many: wait for every CTA
+                            else S.near[S.nnear++] = (short)c;
                         }
                         r = e + 1;
                     }
@@ -1556,10 +1557,11 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
                 double R = Ld.rbound;
                 if (Ld.rmode == SPKMC_RMAX_LEARNED) {
                     // exact R_max of this colour's previous visit, cycle t - 8,
-                    // final since the grid barriers that followed it
+                    // final since the grid barrier that the bounds take at
+                    // least every 8 cycles (see the kernel loop)
                     const long long t = S.seg_t0[i] + g;
                     const double h = __longlong_as_double(
-                        (long long)__ldcg(&P.state[S.seg_slot[i]].rmax[(t + 8) & (kRmaxRing - 1)]));
+                        (long long)__ldcg(&P.state[S.seg_slot[i]].rmax[(t - 8) & (kRmaxRing - 1)]));
                     if (h > 0.0) {
                         const double b = __dmul_rn(__dadd_rn(h, Ld.rmargin), kBoundSlack);
                         if (b < R) R = b;
@@ -1649,23 +1651,25 @@ __global__ void __launch_bounds__(kThreads, 2) spkmc_cycles_kernel(LaunchParams 
             // mod 8 (their colours differ in the y and z bits).  With the
             // exact R_max, barrier 1 of cycle t + 1, which a CTA reaches only
             // after its flips of cycle t, orders both.  Without it (the
-            // bounds of Sec. 3.2 step 4b), the whole grid meets after
-            // t = 1, 5 mod 8 and, for one lattice whose t mod 4 the launch
-            // knows, a CTA waits after t = 3, 7 mod 8 only for the CTAs of
-            // its yz-diagonal domains (yz_wait); otherwise the whole grid
-            // meets there too.  The row waits after even cycles order the
-            // rest (tests/test_sync_schedule.py checks the schedule).
+            // bounds of Sec. 3.2 step 4b), a CTA waits after an odd cycle for
+            // the CTAs of its near domains (near_wait, one lattice) or for the
+            // whole grid (several lattices), and the whole grid meets after
+            // every 8th cycle of the launch, which the ring of exact R_max
+            // maxima needs: the learned bound reads slot t - 8, which must be
+            // final, and slot t + 8 is cleared at t, before any CTA writes it.
+            // The row waits after even cycles order the rest
+            // (tests/test_sync_schedule.py checks the schedule and the ring).
             const bool odd = P.parity0 >= 0 && (((long long)P.parity0 + g) & 1LL) == 1LL;
             const bool even = P.parity0 >= 0 && !odd;
             const bool skip = odd && P.exact_any;
-            const bool yz = odd && !P.exact_any && P.done && P.nseg == 1 && P.phase4 >= 0 &&
-                            (((long long)P.phase4 + g) & 3LL) == 3LL;
+            const bool grid8 = !P.exact_any && (g & 7LL) == 7LL;
+            const bool near = odd && !P.exact_any && !grid8 && P.done && P.nseg == 1;
             if (skip) {
                 __syncthreads();
-            } else if (even && P.done) {
+            } else if (even && P.done && !grid8) {
                 if (!row_wait(P, S, g)) return;
-            } else if (yz) {
-                if (!yz_wait(P, S, g)) return;
+            } else if (near) {
+                if (!near_wait(P, S, g)) return;
             } else if (!grid_barrier(P, S, epoch)) {
                 return;
             }

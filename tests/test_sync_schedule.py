@@ -172,23 +172,23 @@ def happens_before(nd, G, mode, t0, ncycles, end_rule=end_sync, row_rule=row_wai
     return ranges, lambda u, v: v in closure(u)
 
 
-def ring_accesses(t, b, first, mode):
-    """The ring of exact R_max maxima (16 slots, cycle t in slot t mod 16): in
-    cycle t every CTA takes its maximum into slot t after step 1 (an atomic);
-    the CTA holding the lattice's first domain clears slot t + 4 in its prepass
-    (a plain store); the exact mode reads slot t in the prepass, after barrier
-    1, and the learned bound reads slot t - 8 at the start of the cycle."""
-    acc = [(0, ("ring", t % 16), "a")]
+def ring_accesses(t, b, first, mode, ring=32, clear=8):
+    """The ring of exact R_max maxima (cycle t in slot t mod ring): in cycle t
+    every CTA takes its maximum into slot t after step 1 (an atomic); the CTA
+    holding the lattice's first domain clears slot t + clear in its prepass (a
+    plain store); the exact mode reads slot t in the prepass, after barrier 1,
+    and the learned bound reads slot t - 8 at the start of the cycle."""
+    acc = [(0, ("ring", t % ring), "a")]
     if b == first:
-        acc.append((1, ("ring", (t + 4) % 16), "w"))
+        acc.append((1, ("ring", (t + clear) % ring), "w"))
     if mode == "exact":
-        acc.append((1, ("ring", t % 16), "r"))
+        acc.append((1, ("ring", t % ring), "r"))
     else:
-        acc.append((0, ("ring", (t - 8) % 16), "r"))
+        acc.append((0, ("ring", (t - 8) % ring), "r"))
     return acc
 
 
-def unordered_conflicts(nd, G, mode, t0, ncycles, **kw):
+def unordered_conflicts(nd, G, mode, t0, ncycles, ring=32, clear=8, **kw):
     ranges, hb = happens_before(nd, G, mode, t0, ncycles, **kw)
     Q = items(nd)
     by_obj = {}  # object -> list of (g, cta, phase, kind)
@@ -201,7 +201,7 @@ def unordered_conflicts(nd, G, mode, t0, ncycles, **kw):
         # the ring (every CTA with items takes part; the first domain's CTA clears)
         for b in range(G):
             if ranges[b][0] < ranges[b][1]:
-                for ph, obj, kind in ring_accesses(t0 + g, b, owner(0, ranges), mode):
+                for ph, obj, kind in ring_accesses(t0 + g, b, owner(0, ranges), mode, ring, clear):
                     # a learned read of a slot written before the launch is not a conflict here
                     if kind == "r" and mode != "exact" and g < 8:
                         continue
@@ -256,115 +256,6 @@ def test_bound_modes_need_a_barrier_after_every_odd_cycle():
 
 def test_row_wait_on_the_cta_alone_fails():
     assert unordered_conflicts(8, 5, "exact", 0, 12, row_rule=lambda b, ranges, nd: {b})
-
-
-def yz_wait_set(b, ranges, nd):
-    """CTAs that hold the items one row back (y - 1, wrapping within the plane)
-    or in the same row, in the same plane or one plane either way (z +- 1,
-    wrapping), of any item of CTA b: the CTAs whose flips two cycles apart
-    from b's touch domains yz-diagonal to b's."""
-    lo, hi = ranges[b]
-    h = nd // 2
-    Q = h ** 3
-    out = {b}
-    for a in range(lo, hi):
-        ax, ay, az = a % h, (a // h) % h, a // (h * h)
-        for dy in (-1, 0):
-            for dz in (-1, 0, 1):
-                a2 = ax + h * ((ay + dy) % h) + h * h * ((az + dz) % h)
-                out.add(owner(a2, ranges))
-    return out
-
-
-def local_3_7(t, mode):
-    """Bound modes with the grid barrier after t = 1, 5 mod 8 and the yz wait
-    after t = 3, 7."""
-    if t % 2 == 0:
-        return "row"
-    if mode == "exact":
-        return "none"
-    return "yz" if t % 4 == 3 else "grid"
-
-
-@pytest.mark.parametrize("nd,G", CASES)
-@pytest.mark.parametrize("t0", [0, 1, 3, 6])
-def test_bound_modes_with_yz_waits_after_t_3_7(nd, G, t0):
-    ranges = cta_ranges(nd, G)
-    yz = {b: yz_wait_set(b, ranges, nd) for b in range(G)}
-
-    def rule(t, mode):
-        r = local_3_7(t, mode)
-        return ("set", yz) if r == "yz" else r
-    assert unordered_conflicts(nd, G, "bound", t0, 12, end_rule=rule) == []
-
-
-def test_yz_wait_without_the_plane_neighbours_fails():
-    nd, G = 8, 5
-    ranges = cta_ranges(nd, G)
-
-    def same_plane(b, ranges_, nd_):
-        lo, hi = ranges_[b]
-        h = nd_ // 2
-        out = {b}
-        for a in range(lo, hi):
-            ax, ay, az = a % h, (a // h) % h, a // (h * h)
-            for dy in (-1, 0):
-                out.add(owner(ax + h * ((ay + dy) % h) + h * h * az, ranges_))
-        return out
-    sets = {b: same_plane(b, ranges, nd) for b in range(G)}
-
-    def rule(t, mode):
-        r = local_3_7(t, mode)
-        return ("set", sets) if r == "yz" else r
-    assert unordered_conflicts(nd, G, "bound", 0, 12, end_rule=rule)
-
-
-def yz_wait_rows(b, ranges, nd, max_list=128):
-    """The kernel's yz wait set (`yz_wait` in spkmc_kernels.cu): each run of
-    the CTA's rows within one plane (the row ay = 0 on its own when the y
-    shift wraps it) maps, for dy in (-1, 0) and dz in (-1, 0, 1), to a run of
-    whole rows of the image plane; every CTA holding an item of it is waited
-    for (every CTA when the list would pass max_list)."""
-    lo, hi = ranges[b]
-    h = nd // 2
-    out = []
-    if lo >= hi:
-        return {b}
-    r0, r1 = lo // h, (hi - 1) // h
-    for dz in (-1, 0, 1):
-        for dy in (-1, 0):
-            r = r0
-            while r <= r1:
-                ay, az = r % h, r // h
-                e = min((az + 1) * h - 1, r1)
-                if dy < 0 and ay == 0:
-                    e = r
-                first = (((ay + dy) % h) + h * ((az + dz) % h)) * h
-                c0, c1 = owner(first, ranges), owner(first + (e - r + 1) * h - 1, ranges)
-                for c in range(c0, c1 + 1):
-                    if c not in out:
-                        out.append(c)
-                r = e + 1
-    if len(out) > max_list:
-        return set(range(len(ranges)))
-    return set(out) | {b}
-
-
-@pytest.mark.parametrize("nd,G", CASES)
-@pytest.mark.parametrize("t0", [0, 3])
-def test_kernel_yz_wait_set_covers_the_exact_one_and_orders_every_conflict(nd, G, t0):
-    ranges = cta_ranges(nd, G)
-    rows = {b: yz_wait_rows(b, ranges, nd) for b in range(G)}
-    for b in range(G):
-        assert yz_wait_set(b, ranges, nd) <= rows[b]
-
-    def rule(t, mode):
-        r = local_3_7(t, mode)
-        return ("set", rows) if r == "yz" else r
-    assert unordered_conflicts(nd, G, "bound", t0, 12, end_rule=rule) == []
-    # a list too short to hold the set falls back to every CTA, which is safe
-    full = {b: yz_wait_rows(b, ranges, nd, max_list=1) for b in range(G)}
-    assert all(full[b] == set(range(G)) or len(rows[b]) <= 1 for b in range(G))
 
 
 # ---- several lattices in one launch (the batched ensembles and the served
@@ -472,21 +363,102 @@ def test_batched_row_wait_on_the_cta_alone_fails():
     assert batch_unordered_conflicts((4, 8), (0, 2), ("exact", "exact"), 5, 10, own_rows_only=True)
 
 
-def test_without_the_barriers_after_t_1_5_the_ring_races():
-    # on a lattice large enough that the yz waits are local, waiting only
-    # locally after every odd cycle lets the CTAs drift more than four cycles
-    # apart, and the clear of a ring slot races with its maxima and reads
-    nd, G = 16, 30
+def wide_wait_rows(b, ranges, nd, max_list=128):
+    """The kernel's wait set after an odd cycle with the bounds: every CTA
+    holding an item of the rows y - 1, y, y + 1 of the planes z - 1, z, z + 1
+    of a row (y, z) of CTA b (each index wrapping), built from row runs: a run
+    of b's rows within one plane maps to a run of whole rows of each image
+    plane, with the row that the y shift wraps taken on its own."""
+    lo, hi = ranges[b]
+    h = nd // 2
+    if lo >= hi:
+        return {b}
+    out = []
+    r0, r1 = lo // h, (hi - 1) // h
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            r = r0
+            while r <= r1:
+                ay, az = r % h, r // h
+                e = min((az + 1) * h - 1, r1)
+                if (dy < 0 and ay == 0) or (dy > 0 and ay == h - 1):
+                    e = r
+                elif dy > 0:
+                    e = min(e, az * h + h - 2)  # stop before the row that wraps
+                first = (((ay + dy) % h) + h * ((az + dz) % h)) * h
+                c0, c1 = owner(first, ranges), owner(first + (e - r + 1) * h - 1, ranges)
+                for c in range(c0, c1 + 1):
+                    if c not in out:
+                        out.append(c)
+                r = e + 1
+    if len(out) > max_list:
+        return set(range(len(ranges)))
+    return set(out) | {b}
+
+
+def wide_rule_for(t0, sets):
+    """The bound modes' schedule: the grid after every 8th cycle of the launch,
+    otherwise the row wait after even cycles and the wide wait after odd ones."""
+    def rule(t, mode):
+        g = t - t0
+        if mode != "exact" and g % 8 == 7:
+            return "grid"
+        if t % 2 == 0:
+            return "row"
+        return "none" if mode == "exact" else ("set", sets)
+    return rule
+
+
+@pytest.mark.parametrize("nd,G", CASES)
+@pytest.mark.parametrize("t0", [0, 1, 3, 6])
+def test_bound_modes_with_wide_waits_and_a_grid_barrier_every_8_cycles(nd, G, t0):
     ranges = cta_ranges(nd, G)
-    yz = {b: yz_wait_rows(b, ranges, nd) for b in range(G)}
-    assert max(len(v) for v in yz.values()) < G // 2
+    sets = {b: wide_wait_rows(b, ranges, nd) for b in range(G)}
+    assert unordered_conflicts(nd, G, "bound", t0, 20, end_rule=wide_rule_for(t0, sets)) == []
+    assert unordered_conflicts(nd, G, "exact", t0, 20, end_rule=wide_rule_for(t0, sets)) == []
 
-    def all_local(t, mode):
-        return "row" if t % 2 == 0 else ("set", yz)
-    bad = unordered_conflicts(nd, G, "bound", 0, 20, end_rule=all_local)
-    assert any(obj[0] == "ring" for obj, *_ in bad)
 
-    def committed(t, mode):
-        r = local_3_7(t, mode)
-        return ("set", yz) if r == "yz" else r
-    assert unordered_conflicts(nd, G, "bound", 0, 20, end_rule=committed) == []
+def test_a_grid_barrier_every_8_cycles_needs_the_32_slot_ring():
+    nd, G, t0 = 24, 60, 0
+    ranges = cta_ranges(nd, G)
+    sets = {b: wide_wait_rows(b, ranges, nd) for b in range(G)}
+    assert max(len(v) for v in sets.values()) < G // 2
+    rule = wide_rule_for(t0, sets)
+    assert unordered_conflicts(nd, G, "bound", t0, 24, end_rule=rule, ring=32, clear=8) == []
+    bad = unordered_conflicts(nd, G, "bound", t0, 24, end_rule=rule, ring=16, clear=4)
+    assert bad and all(obj[0] == "ring" for obj, *_ in bad)
+
+
+def test_a_near_wait_confined_to_the_own_plane_fails():
+    nd, G, t0 = 8, 5, 0
+    ranges = cta_ranges(nd, G)
+
+    def same_plane(b):
+        lo, hi = ranges[b]
+        h = nd // 2
+        out = {b}
+        for a in range(lo, hi):
+            ax, ay, az = a % h, (a // h) % h, a // (h * h)
+            for dy in (-1, 0, 1):
+                out.add(owner(ax + h * ((ay + dy) % h) + h * h * az, ranges))
+        return out
+    sets = {b: same_plane(b) for b in range(G)}
+    assert unordered_conflicts(nd, G, "bound", t0, 20, end_rule=wide_rule_for(t0, sets))
+
+
+def test_without_the_grid_barrier_every_8_cycles_only_the_ring_races():
+    # on a lattice large enough that the near waits are local, they order
+    # every block, ghost and count access, but without a grid barrier the
+    # CTAs drift apart and the clear of a ring slot races with its maxima and
+    # reads
+    nd, G, t0 = 24, 60, 0
+    ranges = cta_ranges(nd, G)
+    sets = {b: wide_wait_rows(b, ranges, nd) for b in range(G)}
+    assert max(len(v) for v in sets.values()) < G // 4
+
+    def no_grid(t, mode):
+        return "row" if t % 2 == 0 else ("set", sets)
+    bad = unordered_conflicts(nd, G, "bound", t0, 24, end_rule=no_grid)
+    assert bad and all(obj[0] == "ring" for obj, *_ in bad)
+    assert unordered_conflicts(nd, G, "bound", t0, 24, end_rule=wide_rule_for(t0, sets)) == []
+

@@ -204,13 +204,47 @@ def barrier(pg, device=None):
         pg.barrier()
 
 
+def _code_text(src: str) -> str:
+    """The code of a C++ source without its comments (string and character
+    literals kept as they are), one stripped line per non-empty line."""
+    out, i, n, quote = [], 0, len(src), None
+    while i < n:
+        c = src[i]
+        if quote:
+            out.append(c)
+            if c == "\\" and i + 1 < n:
+                out.append(src[i + 1])
+                i += 2
+                continue
+            if c == quote:
+                quote = None
+            i += 1
+        elif c in "\"'":
+            quote = c
+            out.append(c)
+            i += 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    lines = (line.strip() for line in "".join(out).splitlines())
+    return "\n".join(line for line in lines if line)
+
+
 def kernel_source_hash() -> str:
-    """Hash of the sources the cycle kernel is compiled from (its translation
-    unit and the headers it includes)."""
+    """Hash of the code the cycle kernel is compiled from (its translation
+    unit and the headers it includes), without comments or blank lines: an
+    edit of a comment leaves the captured traffic of the kernel valid."""
     h = hashlib.sha256()
     for f in ("spkmc_kernels.cu", "spkmc_device.cuh", "spkmc_internal.h"):
-        with open(os.path.join(ROOT, "paper_1005_4713_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1005_4713_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(f.encode() + b"\0" + _code_text(fh.read()).encode() + b"\0")
     return h.hexdigest()[:16]
 
 

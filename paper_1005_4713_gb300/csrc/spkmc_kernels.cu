@@ -25,12 +25,17 @@
 //                       rank into a half of the domain and a rank there; one
 //                       octet of lanes per domain classifies the chosen half
 //                       with a bit-sliced adder and picks the site by popc, an
-//                       octet scan and a bit search; one thread per domain
-//                       flips the site, moves the class counts of the site
-//                       and of its 6 neighbours and refreshes the neighbours'
-//                       ghost faces;
-//   grid barrier        (step 6: the flips are visible) -- skipped after an
-//                       odd cycle t when that is safe (see the loop).
+//                       octet scan, a binary search for the word and a bit
+//                       search; one thread per domain flips the site, moves
+//                       the class counts of the site and of its 6 neighbours
+//                       and refreshes the neighbours' ghost faces;
+//   end of cycle        (step 6: the flips are visible) -- not always the
+//                       whole grid: after an even cycle a CTA waits for the
+//                       CTAs sharing its rows of domains (row_wait); after an
+//                       odd one nothing with the exact R_max (barrier 1 of
+//                       the next cycle orders what must be ordered), and with
+//                       the bounds the CTAs of its near domains (near_wait),
+//                       with the whole grid every 8 cycles (see the loop).
 // The clock (step 5) of a lattice is advanced by the last thread of the CTA
 // that holds the lattice's first active domain: during the flip step of the
 // cycle when the CTA stages its domains in one round, else one cycle behind.

@@ -53,16 +53,33 @@ def test_kernel_source_hash_changes_with_the_sources(tmp_path, monkeypatch):
     (csrc / "spkmc_internal.h").write_text("b")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     h1 = bench.kernel_source_hash()
-    (csrc / "spkmc_kernels.cu").write_text("a ")
+    (csrc / "spkmc_kernels.cu").write_text("a1")
     h2 = bench.kernel_source_hash()
     assert h2 != h1
-    (csrc / "spkmc_device.cuh").write_text("c ")  # a header the cycle kernel includes
+    (csrc / "spkmc_device.cuh").write_text("c1")  # a header the cycle kernel includes
     assert bench.kernel_source_hash() not in (h1, h2)
     # the set-up kernels are another translation unit: not part of the hash
     (csrc / "spkmc_setup_kernels.cu").write_text("d")
     h3 = bench.kernel_source_hash()
-    (csrc / "spkmc_setup_kernels.cu").write_text("d ")
+    (csrc / "spkmc_setup_kernels.cu").write_text("d1")
     assert bench.kernel_source_hash() == h3
+
+
+def test_kernel_source_hash_ignores_comments_but_not_code(tmp_path, monkeypatch):
+    csrc = tmp_path / "paper_1005_4713_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "spkmc_device.cuh").write_text("int c;")
+    (csrc / "spkmc_internal.h").write_text("int b;")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    code = 'int a = 1;\nconst char *s = "// not a comment";\n'
+    (csrc / "spkmc_kernels.cu").write_text(code)
+    h = bench.kernel_source_hash()
+    (csrc / "spkmc_kernels.cu").write_text("// a comment\n" + code.replace("1;", "1; /* another */") + "\n\n")
+    assert bench.kernel_source_hash() == h
+    (csrc / "spkmc_kernels.cu").write_text(code.replace("not a comment", "still not"))
+    assert bench.kernel_source_hash() != h  # text inside a string literal is code
+    (csrc / "spkmc_kernels.cu").write_text(code.replace("1;", "2;"))
+    assert bench.kernel_source_hash() != h
 
 
 def test_binder_table_bins_by_edge_and_temperature():

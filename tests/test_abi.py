@@ -149,3 +149,28 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
         assert int(got[name]) == ctypes.sizeof(cls), name
         for fname, _ in cls._fields_:
             assert int(got[f"{name}.{fname}"]) == getattr(cls, fname).offset, (name, fname)
+
+
+def build_abi_example(tmp_path):
+    """tests/abi_example.c compiled and linked against the in-tree library."""
+    import subprocess
+    exe = tmp_path / "abi_example"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "abi_example.c"), "-L", os.path.dirname(_abi.LIB_PATH), "-lspkmc",
+                    "-Wl,-rpath," + os.path.dirname(_abi.LIB_PATH), "-o", str(exe)], check=True)
+    return str(exe)
+
+
+def test_c_program_links_and_fails_loudly_without_a_device(tmp_path):
+    import subprocess
+    import torch
+    exe = build_abi_example(tmp_path)
+    bad = subprocess.run([exe, "1"], capture_output=True, text=True)
+    assert bad.returncode == 2 and "usage" in bad.stderr
+    bad = subprocess.run([exe, "30", "8", "1", "0", "4.5", "1", "10"], capture_output=True, text=True)
+    assert bad.returncode == 1 and bad.stdout == ""
+    assert "spkmc_create" in bad.stderr  # L % (2d) != 0, or no device: the create call fails first
+    if not torch.cuda.is_available():
+        r = subprocess.run([exe], capture_output=True, text=True)
+        assert r.returncode == 1 and r.stdout == ""
+        assert "no CUDA device" in r.stderr

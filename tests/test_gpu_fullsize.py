@@ -70,3 +70,42 @@ def test_config_128_all_16000_cycles_in_one_recorded_launch(spec):
         assert np.array_equal(lat.spins(), st.spins)
         assert np.array_equal(lat.class_counts(), oracle.class_counts(spec.L, spec.d, st.spins))
         assert lat.check_counts() == 0
+
+
+def mem_available_gib() -> float:
+    with open("/proc/meminfo") as f:
+        for line in f:
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) / 2**20
+    return 0.0
+
+
+def test_2048_cube_beyond_32_bit_site_indices():
+    """2048^3 (8.6e9 sites, past 32-bit site indices), 16^3-site domains,
+    hot start seed 5: 262 144 active domains per cycle, so each CTA holds
+    several hundred and stages them in rounds, its frequency lines going
+    through the scratch lines.  One visit of each colour (8 cycles) in one
+    recorded launch, records every 2 cycles against the oracle, then the
+    spins bit for bit (one bit per site, compared in slabs) and the device's
+    own recheck of counts, ghost faces, M and B."""
+    if mem_available_gib() < 48:
+        pytest.skip("the oracle's 2048^3 lattice needs about 10 GB of host memory; less than 48 GB is free")
+    L, d, seed = 2048, 16, 5
+    every, nrec = 2, 4
+    rec = sp.obs_buffer(nrec)
+    with sp.Lattice(L, d, 1.0, 0.0, 4.5115, seed) as lat:
+        lat.run_recorded(every, nrec, rec)
+        lat.synchronize()
+        info = lat.info()  # the grid is sized at the first launch
+        assert info.K_act == (L // d // 2) ** 3 and info.grid_ctas > 0
+        assert -(-info.K_act // info.grid_ctas) > 256  # more than one staging round per CTA
+        st = oracle.State(L, d, 1.0, 0.0, 4.5115, seed)
+        compare_records(rec, nrec, every, st)
+        assert st.n_flip + st.n_null == 8 * info.K_act
+        bits = lat.spins_packed()
+        flat = st.spins.reshape(-1)
+        step = 1 << 27  # sites per slab, a multiple of 8
+        for i in range(0, flat.size, step):
+            want = np.packbits(flat[i:i + step] > 0, bitorder="little")
+            assert np.array_equal(bits[i // 8:i // 8 + want.size], want), i
+        assert lat.check_counts() == 0

@@ -262,7 +262,7 @@ def test_row_wait_on_the_cta_alone_fails():
 # stream): the lattices' active domains are concatenated in one item range,
 # each lattice keeps its own cycle index (all with the launch's parity), the
 # row waits use the segment-aware row edges, and with the bounds the grid
-# meets after every odd cycle (the yz wait is for single-lattice launches).
+# meets after every odd cycle (the near wait is for single-lattice launches).
 
 def batch_unordered_conflicts(nds, t0s, modes, G, ncycles, own_rows_only=False):
     assert len({t % 2 for t in t0s}) == 1  # the row waits need one parity

@@ -283,7 +283,8 @@ int spkmc_get_spins_packed(spkmc_t *h, uint8_t *host_bits, size_t nbytes);
 int spkmc_set_spins_packed(spkmc_t *h, const uint8_t *host_bits, size_t nbytes);
 /* Copy up to cap logged events (cycle-major, ascending k within a cycle);
  * n_out receives the number copied.  The log holds the first
- * event_log_capacity events after create or spkmc_clear_event_log. */
+ * event_log_capacity events after create, spkmc_clear_event_log or
+ * spkmc_set_state (which restarts it at the restored cycle). */
 int spkmc_get_event_log(spkmc_t *h, spkmc_event *buf, size_t cap, size_t *n_out);
 int spkmc_clear_event_log(spkmc_t *h);
 /* Checkpoint scalars (with get/set_spins the state is complete: the random

@@ -8,7 +8,9 @@ prescribed or self-learned bound of Sec. 3.2 step 4b), the colour scheme
 geometry.  The run is split into launches of random length.  After each
 launch the spins, M, B, the flip and null counters, the fixed-point null-rate
 sum and the clock are compared with the oracle; at the end, the whole event
-log and the device's recheck of its class counts and ghost faces.  The same
+log and the device's recheck of its class counts and ghost faces.  A third
+of the cases with several launches resume from a checkpoint in a new handle
+after their first launch.  The same
 random lattices also run together in batches (one persistent launch over
 all of them), each checked against its own oracle run."""
 import os
@@ -56,26 +58,37 @@ def test_random_case_matches_oracle(i):
     c = draw_case(i)
     st = oracle.State(c["L"], c["d"], c["J"], c["H"], c["T"], c["seed"], cold=c["cold"], rmax_mode=c["mode"],
                       sublattice=c["scheme"])
-    total = sum(c["chunks"])
-    with sp.Lattice(c["L"], c["d"], c["J"], c["H"], c["T"], c["seed"], cold=c["cold"],
-                    event_log_capacity=total * st.k_act, config=sp.make_config(**c["geometry"]),
-                    rmax_mode=MODES[c["mode"]], sublattice=SCHEMES[c["scheme"]], tuned=False) as lat:
-        logs = []
-        for n in c["chunks"]:
-            lat.run(n)
-            logs.append(st.run(n, log=True, threads=THREADS))
-            o = lat.observables()
-            assert o.cycle == st.cycle, c
-            assert (o.n_flip, o.n_null) == (st.n_flip, st.n_null), c
-            assert int(o.sum_null_rate_fx[0]) | (int(o.sum_null_rate_fx[1]) << 64) == st.null_fx, c
-            assert o.clock == pytest.approx(st.clock, rel=CLOCK_RTOL, abs=0.0), c
-            assert (o.M, o.B) == st.observables(), c
-            assert np.array_equal(lat.spins(), st.spins), c
-        ev = lat.event_log()
-        assert len(ev) == total * st.k_act, c
-        assert np.array_equal(log_as_array(ev), np.concatenate(logs).reshape(-1, 3)), c
-        assert lat.check_counts() == 0, c
-
+    chunks = c["chunks"]
+    # every third case with more than one launch moves to a new handle after
+    # its first launch: a checkpoint (state and spins) restored into a lattice
+    # created cold, whose event log restarts at the restored cycle
+    parts = [chunks[:1], chunks[1:]] if len(chunks) > 1 and i % 3 == 0 else [chunks]
+    state = spins = None
+    for k, part in enumerate(parts):
+        with sp.Lattice(c["L"], c["d"], c["J"], c["H"], c["T"], c["seed"], cold=c["cold"] or k > 0,
+                        event_log_capacity=sum(part) * st.k_act, config=sp.make_config(**c["geometry"]),
+                        rmax_mode=MODES[c["mode"]], sublattice=SCHEMES[c["scheme"]], tuned=False) as lat:
+            if k > 0:
+                lat.set_spins(spins)
+                lat.set_state(state)
+                assert lat.check_counts() == 0, c
+            logs = []
+            for n in part:
+                lat.run(n)
+                logs.append(st.run(n, log=True, threads=THREADS))
+                o = lat.observables()
+                assert o.cycle == st.cycle, c
+                assert (o.n_flip, o.n_null) == (st.n_flip, st.n_null), c
+                assert int(o.sum_null_rate_fx[0]) | (int(o.sum_null_rate_fx[1]) << 64) == st.null_fx, c
+                assert o.clock == pytest.approx(st.clock, rel=CLOCK_RTOL, abs=0.0), c
+                assert (o.M, o.B) == st.observables(), c
+                assert np.array_equal(lat.spins(), st.spins), c
+            ev = lat.event_log()
+            assert len(ev) == sum(part) * st.k_act, c
+            assert np.array_equal(ev["cycle"], np.repeat(np.arange(st.cycle - sum(part), st.cycle), st.k_act)), c
+            assert np.array_equal(log_as_array(ev), np.concatenate(logs).reshape(-1, 3)), c
+            assert lat.check_counts() == 0, c
+            state, spins = lat.state(), lat.spins()
 
 NBATCHES = 32
 

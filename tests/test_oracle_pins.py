@@ -285,6 +285,27 @@ def test_cold_start_first_cycle_closed_form():
     assert st.clock == pytest.approx(-math.log(xi) / (d ** 3 * r_up6), rel=1e-13)
 
 
+def test_first_clock_step_exactly():
+    """Step 5 with the reading of xi (never 0 or 1): xi = (2 (w0 >> 12) + 1)
+    2^-53 from the clock's own Philox word (numpy's generator).  From all +1
+    at H = 0 only class 13 is populated, so R_max = d^3 r_13 exactly (d^3 a
+    power of two, r_13 pinned by the closed form above), and the first clock
+    step is -ln(xi) / R_max bit for bit (the same libm logarithm).  Eight
+    seeds, so that some words have bit 11 clear: a xi built from w0 >> 11
+    differs from the reading by 2^-53 there."""
+    L, d, T = 16, 4, 4.5115
+    r13 = oracle.rates(1.0, 0.0, T)[13]
+    bit11_clear = 0
+    for seed in range(21, 29):
+        st = oracle.State(L, d, 1.0, 0.0, T, seed, cold=True)
+        st.run(1)
+        w0 = numpy_philox((0, 0, 2, 0), (seed, 0))[0]
+        xi = (2 * (w0 >> 12) + 1) * 2.0 ** -53
+        assert st.clock == -math.log(xi) / (d ** 3 * r13), seed
+        bit11_clear += (w0 >> 11) & 1 == 0
+    assert bit11_clear > 0
+
+
 def test_no_coupling_uniform_flips_and_clock():
     """J = H = 0: all rates 1/2, R_k = d^3/2 everywhere, never a null event,
     the flipped site is uniform over the domain, E[clock] = 2 n / d^3."""

@@ -1,6 +1,7 @@
 """Mistakes planted in the oracle must fail its pins.
 
-Each mutant below is one plausible slip in oracle/spkmc_oracle.c: a wrong
+Each mutant below is one plausible slip in oracle/spkmc_oracle.c or in its
+Python wrapper oracle/__init__.py: a wrong
 sign, a dropped term, a neighbour or an axis taken wrong, a swapped operand,
 a wrong random word, an index off by one, a bound read the other way.  It is
 planted in a copy of the oracle package in a temporary folder; the pin tests
@@ -16,8 +17,13 @@ import sys
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "spkmc_oracle.c")
+WRAPPER = os.path.join(ROOT, "oracle", "__init__.py")
 
-# name -> (text of the oracle, its replacement); each text occurs once
+# name -> (text of oracle/spkmc_oracle.c, its replacement); each text occurs
+# once.  Every mutant changes some result the pins can reach: a slip that is
+# equal to the original on every input the pins use (floor(x 2^63) * 2 for
+# floor(x 2^64), equal for x >= 2^-10; (w0 >> 12) 2^-52 for u01, within
+# 2^-53 of it) is not one.
 MUTANTS = {
     # Eq. 3, the Glauber rate
     "rate sign": ("r[c] = 1.0 / (1.0 + exp(x));", "r[c] = 1.0 / (1.0 + exp(-x));"),
@@ -71,42 +77,76 @@ MUTANTS = {
     "bond energy dropped": ("bonds += s[i] * (s[nb[1]] + s[nb[3]] + s[nb[5]]);", "bonds += s[i] * (s[nb[1]] + s[nb[3]]);"),
     "Boltzmann weight": ("double wgt = exp(-(E - Emin) / T);", "double wgt = exp(-(E - Emin) / (2.0 * T));"),
     "class BKL neighbour not moved": ("for (int a = 0; a < 7; ++a) {", "for (int a = 0; a < 6; ++a) {"),
+    # the history of R_max, the bound check and the fixed-point null sum
+    "history records the bound": ("hist[7] = Rmax;", "hist[7] = R;"),
+    "bound check off": ("if (R < Rmax) {", "if (R < 0.0) {"),
+    "null sum scale": ("return (u128)ldexp(x, 64);", "return (u128)ldexp(x, 60);"),
+    # the counters of the random streams
+    "hot start stream": ("oracle_philox((uint64_t)(g / 256), 0, 3, 0, seed, 0, w);",
+                         "oracle_philox((uint64_t)(g / 256), 0, 2, 0, seed, 0, w);"),
+    "event counter by active index": ("oracle_philox((uint64_t)t, (uint64_t)k, 1, 0, seed, 0, w);",
+                                      "oracle_philox((uint64_t)t, (uint64_t)a, 1, 0, seed, 0, w);"),
+    "u01 from another word": ("double u01 = (double)(w[0] >> 11) * 0x1p-53;", "double u01 = (double)(w[1] >> 11) * 0x1p-53;"),
+    "class BKL clock word": ("const double xi = (double)(2 * (w[2] >> 12) + 1) * 0x1p-53;",
+                             "const double xi = (double)(2 * (w[3] >> 12) + 1) * 0x1p-53;"),
+    "class BKL rank word": ("const uint64_t j = (uint64_t)(((u128)w[1] * (uint64_t)n[c]) >> 64);",
+                            "const uint64_t j = (uint64_t)(((u128)w[2] * (uint64_t)n[c]) >> 64);"),
+    "energy field sign": ("*E = -J * (double)bonds - H * (double)mag;", "*E = -J * (double)bonds + H * (double)mag;"),
+}
+
+# name -> (text of oracle/__init__.py, its replacement): slips in the wrapper
+WRAPPER_MUTANTS = {
+    "wrapper M and B swapped": ("return int(M[0]), int(B[0])", "return int(B[0]), int(M[0])"),
+    "wrapper null sum word": ("self.null_fx = int(fx[0]) | (int(fx[1]) << 64)",
+                              "self.null_fx = int(fx[0]) | (int(fx[1]) << 63)"),
+    "wrapper bounds swapped": ("return float(a[0]), float(b[0])", "return float(b[0]), float(a[0])"),
+    "wrapper cold flag": ("lib().oracle_init_spins(L, seed, 1 if cold else 0, _p(s))",
+                          "lib().oracle_init_spins(L, seed, 0 if cold else 1, _p(s))"),
 }
 
 
-def run_pins(folder, source):
+def run_pins(folder, source, wrapper):
     """The pins of tests/test_oracle_pins.py against a copy of the oracle
-    package whose C source is `source`, built in `folder`."""
+    package with C source `source` and wrapper `wrapper`, built in `folder`."""
     os.makedirs(os.path.join(folder, "oracle"))
-    shutil.copy(os.path.join(ROOT, "oracle", "__init__.py"), os.path.join(folder, "oracle"))
-    with open(os.path.join(folder, "oracle", "spkmc_oracle.c"), "w") as f:
-        f.write(source)
+    for name, text in (("spkmc_oracle.c", source), ("__init__.py", wrapper)):
+        with open(os.path.join(folder, "oracle", name), "w") as f:
+            f.write(text)
     os.makedirs(os.path.join(folder, "tests"))
     for name in ("conftest.py", "test_oracle_pins.py"):
         shutil.copy(os.path.join(ROOT, "tests", name), os.path.join(folder, "tests"))
     shutil.copytree(os.path.join(ROOT, "tests", "golden"), os.path.join(folder, "tests", "golden"))
     env = dict(os.environ, PYTHONPATH=folder)
+    # the copy's library is built first: a build that fails is the harness's
+    # failure, not a pin's
+    subprocess.run([sys.executable, "-c", "import oracle; oracle.build()"], cwd=folder, env=env, check=True,
+                   capture_output=True, timeout=300)
     return subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-x", "-q",
                            "-p", "no:cacheprovider"], cwd=folder, env=env, capture_output=True, text=True,
                           timeout=900)
 
 
 def test_the_unmodified_copy_passes_the_pins(tmp_path):
-    r = run_pins(str(tmp_path / "unmodified"), open(SRC).read())
+    r = run_pins(str(tmp_path / "unmodified"), open(SRC).read(), open(WRAPPER).read())
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
 
 
 def test_every_planted_mistake_fails_a_pin(tmp_path):
-    src = open(SRC).read()
+    src, wrapper = open(SRC).read(), open(WRAPPER).read()
+    plants = []
     for name, (old, new) in MUTANTS.items():
         assert src.count(old) == 1, name
+        plants.append((name, src.replace(old, new), wrapper))
+    for name, (old, new) in WRAPPER_MUTANTS.items():
+        assert wrapper.count(old) == 1, name
+        plants.append((name, src, wrapper.replace(old, new)))
 
     def plant(item):
-        i, (name, (old, new)) = item
-        return name, run_pins(str(tmp_path / f"m{i}"), src.replace(old, new))
+        i, (name, source, wrap) = item
+        return name, run_pins(str(tmp_path / f"m{i}"), source, wrap)
 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
-        results = dict(ex.map(plant, enumerate(MUTANTS.items())))
+        results = dict(ex.map(plant, enumerate(plants)))
     # a pin failed (exit 1 with a failure), not the harness (collection, import)
     survivors = {name: r.stdout[-1500:] + r.stderr[-800:] for name, r in results.items()
                  if not (r.returncode == 1 and " failed" in r.stdout)}

@@ -462,3 +462,45 @@ def test_without_the_grid_barrier_every_8_cycles_only_the_ring_races():
     assert bad and all(obj[0] == "ring" for obj, *_ in bad)
     assert unordered_conflicts(nd, G, "bound", t0, 24, end_rule=wide_rule_for(t0, sets)) == []
 
+
+
+def kernel_code():
+    """The cycle kernel's code (its translation unit and internal header)
+    without comments, whitespace collapsed."""
+    import os
+    import bench
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    text = []
+    for f in ("spkmc_kernels.cu", "spkmc_internal.h"):
+        with open(os.path.join(root, "paper_1005_4713_gb300", "csrc", f)) as fh:
+            text.append(bench._code_text(fh.read()))
+    return " ".join(" ".join(text).split())
+
+
+# The lines of the kernel whose schedule this file models.  A change to any of
+# them must come with a change to the model above (and a new proof).
+KERNEL_SCHEDULE = [
+    # the R_max ring: 32 slots, the learned bound reads t - 8, slot t + 8 is
+    # cleared at t (ring_accesses, ring=32, clear=8)
+    "constexpr int kRmaxRing = 32;",
+    "rmax[(t - 8) & (kRmaxRing - 1)]",
+    "P.state[slot].rmax[(t + 8) & (kRmaxRing - 1)] = 0ULL;",
+    # barrier 1 only when some lattice pads to the exact R_max
+    "if (P.exact_any && !grid_barrier(P, S, epoch)) {",
+    # the end of a cycle (end_sync, wide_rule_for)
+    "const bool skip = odd && P.exact_any;",
+    "const bool grid8 = !P.exact_any && (g & 7LL) == 7LL;",
+    "const bool near = odd && !P.exact_any && !grid8 && P.done && P.nseg == 1;",
+    "if (skip) { __syncthreads(); } else if (even && P.done && !grid8) { if (!row_wait(P, S, g)) return; } "
+    "else if (near) { if (!near_wait(P, S, g)) return; } else if (!grid_barrier(P, S, epoch)) { return; }",
+    # the near set: rows y - 1 .. y + 1 of planes z - 1 .. z + 1, at most 128
+    # CTAs before it becomes every CTA (wide_wait_rows, max_list=128)
+    "for (int dz = -1; dz <= 1 && S.nnear >= 0; ++dz) { for (int dy = -1; dy <= 1 && S.nnear >= 0; ++dy) {",
+    "constexpr int kMaxNear = 128;",
+    "if (S.nnear == kMaxNear) S.nnear = -1;",
+]
+
+
+@pytest.mark.parametrize("line", KERNEL_SCHEDULE)
+def test_the_model_is_the_kernels_schedule(line):
+    assert " ".join(line.split()) in kernel_code(), line

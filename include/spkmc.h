@@ -254,8 +254,10 @@ int spkmc_run_recorded(spkmc_t *h, int64_t every, int32_t nrec, spkmc_obs *host_
  * if host_obs is not NULL, the asynchronous observables into host_obs[i]
  * (pinned host memory of `steps` records, else EINVAL).  Replaying it with
  * spkmc_graph_launch does the same work as the calls it captured, with one
- * launch from the host; the graph refers to the handle, which must outlive
- * it, and to host_obs.  steps * cycles_per_step must be even (each launch
+ * launch from the host; the graph refers to the handle and to host_obs.
+ * Destroying the handle first releases the graph's replay: spkmc_graph_launch
+ * then returns SPKMC_EINVAL, and spkmc_graph_destroy still frees the graph
+ * handle.  steps * cycles_per_step must be even (each launch
  * bakes in the parity of the cycle it starts on).  ECUDA if the driver
  * refuses the capture. */
 int spkmc_graph_create(spkmc_t *h, int64_t cycles_per_step, int32_t steps, spkmc_obs *host_obs,

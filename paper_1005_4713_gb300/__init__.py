@@ -232,6 +232,12 @@ class Graph:
             spkmc_graph_destroy(self.g)
             self.g = None
 
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
     def __enter__(self):
         return self
 

@@ -289,6 +289,7 @@ struct spkmc_batch {
 struct spkmc_engine {
     spkmc_batch *b = nullptr;
     int slot = 0;
+    std::vector<spkmc_graph *> graphs; // live graphs captured on this handle
 };
 
 struct spkmc_graph {
@@ -1033,6 +1034,19 @@ int spkmc_create_ex(const spkmc_params *p, const spkmc_config *cfg, spkmc_t **ou
 void spkmc_destroy(spkmc_t *h)
 {
     if (!h) return;
+    if (!h->graphs.empty()) {
+        // the graphs captured on this handle replay its device memory: once
+        // their replays have finished, release their executables and leave
+        // the graph handles orphaned (launch refuses, destroy frees them)
+        DeviceGuard g(h->b->device);
+        cudaStreamSynchronize(h->b->stream);
+        for (spkmc_graph *gr : h->graphs) {
+            cudaGraphExecDestroy(gr->exec);
+            gr->exec = nullptr;
+            gr->h = nullptr;
+        }
+        h->graphs.clear();
+    }
     release_batch(h->b);
     delete h;
 }
@@ -1108,6 +1122,13 @@ int spkmc_graph_create(spkmc_t *h, int64_t cycles_per_step, int32_t steps, spkmc
     gr->h = h;
     gr->exec = exec;
     gr->cycles_per_launch = cycles_per_step * (long long)steps;
+    try {
+        h->graphs.push_back(gr);
+    } catch (...) {
+        cudaGraphExecDestroy(exec);
+        delete gr;
+        return fail(SPKMC_ENOMEM, "graph list");
+    }
     *out = gr;
     return SPKMC_OK;
 }
@@ -1115,6 +1136,7 @@ int spkmc_graph_create(spkmc_t *h, int64_t cycles_per_step, int32_t steps, spkmc
 int spkmc_graph_launch(spkmc_graph_t *gr)
 {
     if (!gr) return fail(SPKMC_EINVAL, "graph is NULL");
+    if (!gr->h) return fail(SPKMC_EINVAL, "the graph's lattice was destroyed");
     spkmc_batch *b = gr->h->b;
     if (b->sticky_error) return fail(b->sticky_error, "batch stopped after an earlier device error");
     DeviceGuard g(b->device);
@@ -1130,9 +1152,17 @@ int spkmc_graph_launch(spkmc_graph_t *gr)
 void spkmc_graph_destroy(spkmc_graph_t *gr)
 {
     if (!gr) return;
-    DeviceGuard g(gr->h->b->device);
-    cudaStreamSynchronize(gr->h->b->stream);
-    cudaGraphExecDestroy(gr->exec);
+    if (gr->h) {
+        DeviceGuard g(gr->h->b->device);
+        cudaStreamSynchronize(gr->h->b->stream);
+        cudaGraphExecDestroy(gr->exec);
+        std::vector<spkmc_graph *> &v = gr->h->graphs;
+        for (size_t i = 0; i < v.size(); ++i)
+            if (v[i] == gr) {
+                v.erase(v.begin() + (long)i);
+                break;
+            }
+    } // else the handle was destroyed first and released the executable
     delete gr;
 }
 

@@ -341,6 +341,31 @@ def test_graph_arguments_are_checked():
         assert e.value.code == sp.SPKMC_EINVAL
 
 
+def test_graph_whose_lattice_was_destroyed_is_refused():
+    """Destroying a lattice first releases the replay of the graphs captured
+    on it: launching such a graph is refused (SPKMC_EINVAL) before any device
+    work, its handle can still be freed, and a new lattice and graph run as
+    before (and as the oracle)."""
+    spec = wl.LatticeSpec(L=32, d=8, seed=41)
+    lat = gpu_lattice(spec)
+    g = lat.graph(2, 2)
+    g.launch()
+    lat.synchronize()
+    lat.close()
+    with pytest.raises(sp.SpkmcError) as e:
+        g.launch()
+    assert e.value.code == sp.SPKMC_EINVAL
+    assert "destroyed" in sp.spkmc_last_error()
+    g.close()
+    with gpu_lattice(spec) as lat2, lat2.graph(2, 2) as g2:
+        g2.launch()
+        g2.launch()
+        lat2.synchronize()
+        st = oracle_state(spec)
+        st.run(8)
+        assert_same(lat2, st)
+
+
 @pytest.mark.parametrize("L,d", [
     (80, 2),    # nd = 40: a full and a partial tile of domains along x, byte lines
     (160, 4),   # word lines (L % 32 == 0)

@@ -4,7 +4,9 @@ Requests (a lattice spec and a cycle budget) arrive over time.  The server
 keeps one batch (``spkmc_batch_t``) resident on the device and loops:
 
 1. admit waiting requests, first come first served, while a slot is free and
-   the device bytes of the admitted lattices stay within the memory budget;
+   the device bytes of the admitted lattices stay within the memory budget
+   (a request that can never fit, or whose admission fails with nothing else
+   on the device, is rejected; one that meets a full device waits);
 2. advance every admitted lattice by up to ``step_cycles`` cycles in one
    persistent launch (lattices stop at their own budget);
 3. poll for finished lattices, read their observables (and spins if asked),
@@ -22,7 +24,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import Batch, Lattice, make_params, spkmc_bytes_required, SPKMC_INIT_COLD, SPKMC_INIT_HOT
+from . import (Batch, Lattice, SpkmcError, make_params, spkmc_bytes_required, SPKMC_ENOMEM, SPKMC_INIT_COLD,
+               SPKMC_INIT_HOT)
 
 
 @dataclass
@@ -128,7 +131,14 @@ class Server:
                         continue
                     if live_bytes + need > self.budget or len(active) >= self.capacity:
                         break
-                    slot = b.admit(s.L, s.d, s.J, s.H, s.T, s.seed, cold=s.cold, cycles=r.cycles)
+                    try:
+                        slot = b.admit(s.L, s.d, s.J, s.H, s.T, s.seed, cold=s.cold, cycles=r.cycles)
+                    except SpkmcError as e:
+                        if e.code == SPKMC_ENOMEM and active:
+                            break  # the device is short of memory: admit again as lattices finish
+                        stats.rejected.append(r.rid)
+                        waiting.popleft()
+                        continue
                     active[slot] = (r, time.perf_counter() - t0, need)
                     live_bytes += need
                     waiting.popleft()
@@ -158,7 +168,7 @@ class Server:
                         s = r.spec
                         stats.completions.append(Completion(
                             rid=r.rid, arrival=r.arrival if realtime else 0.0, admitted=t_adm, finished=t,
-                            cycles=o.cycle, events=o.cycle * (s.L // s.d // 2) ** 3, obs=_obs_key(o), spins=spins,
+                            cycles=o.cycle, events=o.n_flip + o.n_null, obs=_obs_key(o), spins=spins,
                             cancelled=r.rid in self._cancel, L=s.L))
                         b.retire(slot)
                         live_bytes -= need
@@ -185,7 +195,7 @@ def serve_one_at_a_time(requests, realtime: bool = True, config=None) -> ServeSt
         t_end = time.perf_counter() - t0
         stats.completions.append(Completion(
             rid=r.rid, arrival=r.arrival if realtime else 0.0, admitted=t_start, finished=t_end, cycles=o.cycle,
-            events=o.cycle * (s.L // s.d // 2) ** 3, obs=_obs_key(o), L=s.L))
+            events=o.n_flip + o.n_null, obs=_obs_key(o), L=s.L))
         stats.peak_live = 1
         stats.steps += 1
     stats.wall = time.perf_counter() - t0

@@ -77,11 +77,20 @@ def launch_key(L: int, d: int, device: str | None = None) -> str:
     return f"{device or device_key()}|launch|L={L}|d={d}"
 
 
+def spec_edge(s) -> int:
+    """The domain edge a lattice spec runs with: its own, or the library's
+    choice for its L when it leaves the edge to the library (d = 0)."""
+    if s.d:
+        return int(s.d)
+    from . import spkmc_resolve_domain_edge
+    return int(spkmc_resolve_domain_edge(s.L))
+
+
 def batch_key(specs, device: str | None = None) -> str:
     """Batches are keyed by their set of domain edges and the power of two
     nearest their active domains per cycle (the grid fills by that count)."""
-    edges = sorted({int(s.d) for s in specs})
-    q = sum((s.L // s.d // 2) ** 3 for s in specs)
+    edges = sorted({spec_edge(s) for s in specs})
+    q = sum((s.L // spec_edge(s) // 2) ** 3 for s in specs)
     return f"{device or device_key()}|batch|edges={','.join(map(str, edges))}|Q=2^{round(math.log2(max(q, 1)))}"
 
 
@@ -121,7 +130,7 @@ def measure_batch(specs, cycles, items_per_cta=0, ctas_per_sm=0):
         b.run(cycles)
         b.synchronize()
         dt = time.perf_counter() - t0
-    q = sum((s.L // s.d // 2) ** 3 for s in specs)
+    q = sum((s.L // spec_edge(s) // 2) ** 3 for s in specs)
     return {"events_per_s": cycles * q / dt, "s_per_cycle": dt / cycles}
 
 

@@ -100,7 +100,7 @@ def run_batched(specs, cycles: int, sample_every: int = 50, burn_in: int = 0, co
         dt = time.perf_counter() - t0
         obs = b.observables_all()
         final = [_obs_key(obs[sl]) for sl in slots]
-    events = sum(cycles * (s.L // s.d // 2) ** 3 for s in specs)
+    events = sum(f[4] + f[5] for f in final)  # flips + nulls: one event per active domain and cycle
     binder = [dict(_binder(s.L, m2[i], m4[i]), T=s.T, H=s.H, d=s.d, seed=s.seed) for i, s in enumerate(specs)]
     return EnsembleResult(seconds=dt, events=events, final=final, binder=binder)
 
@@ -137,7 +137,7 @@ def run_one_at_a_time(specs, cycles: int, sample_every: int = 50, burn_in: int =
             total += time.perf_counter() - t0
             final.append(_obs_key(lat.observables()))
             binder.append(dict(_binder(s.L, m2, m4), T=s.T, H=s.H, d=s.d, seed=s.seed))
-    events = sum(cycles * (s.L // s.d // 2) ** 3 for s in specs)
+    events = sum(f[4] + f[5] for f in final)
     return EnsembleResult(seconds=total, events=events, final=final, binder=binder)
 
 

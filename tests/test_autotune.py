@@ -103,3 +103,11 @@ def test_lattice_and_ensemble_configs_take_the_cached_geometry(cache_file):
     autotune.tune_batch(specs, measure=lambda ipc, cps: {"s_per_cycle": 2.0 - cps})
     c = ensemble.batch_config(specs, None)
     assert (c.items_per_cta, c.ctas_per_sm) == (64, 1)
+
+
+def test_a_spec_that_leaves_the_edge_to_the_library_is_keyed_by_the_resolved_edge():
+    specs = [wl.LatticeSpec(L=64, d=0, seed=1), wl.LatticeSpec(L=48, d=0, seed=2)]
+    resolved = [wl.LatticeSpec(L=64, d=sp.spkmc_resolve_domain_edge(64), seed=1),
+                wl.LatticeSpec(L=48, d=sp.spkmc_resolve_domain_edge(48), seed=2)]
+    assert [autotune.spec_edge(s) for s in specs] == [r.d for r in resolved]
+    assert autotune.batch_key(specs, "dev") == autotune.batch_key(resolved, "dev")

@@ -498,7 +498,9 @@ __device__ void phase_a(const LaunchParams &P, CtaShared &S, unsigned char *stag
 }
 
 // -ln(xi) of the time step of lattice segment i in grid cycle g (step 5).
-__device__ __forceinline__ double neg_log_xi(const LaunchParams &P, const CtaShared &S, int i, long long g)
+// Out of line, like clock_catch_up: one thread runs it, and inlined into the
+// kernel its registers added spills on the paths every thread runs.
+__device__ __noinline__ double neg_log_xi(const LaunchParams &P, const CtaShared &S, int i, long long g)
 {
     const LatticeDesc &Ld = seg_desc(P, S, i);
     unsigned long long wc[4];
@@ -511,7 +513,7 @@ __device__ __forceinline__ double neg_log_xi(const LaunchParams &P, const CtaSha
 // active domain it holds), one cycle behind: the time increment of the cycle
 // that ended (its R and -ln xi are known), then, with `draw`, the -ln xi of
 // cycle g.  One thread; the clock advances in cycle order.
-__device__ __forceinline__ void clock_catch_up(const LaunchParams &P, CtaShared &S, long long g, long long lo,
+__device__ __noinline__ void clock_catch_up(const LaunchParams &P, CtaShared &S, long long g, long long lo,
                                                bool draw)
 {
     for (int i = 0; i < S.nsegc; ++i) {

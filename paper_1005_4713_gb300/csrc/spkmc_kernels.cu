@@ -1344,13 +1344,15 @@ __device__ __forceinline__ void phase_b_round(const LaunchParams &P, CtaShared &
         // for lattices whose blocks exceed 64 MB (smaller ones stay in L2
         // anyway): step 1 of that cycle then finds them there, not behind
         // the block copies that start it.  The flips of this cycle move some
-        // of those counts later, in L2.
+        // of those counts later, in L2.  Also in a launch's last cycle: the
+        // next launch's first step 1 finds them in L2 too (a lattice that
+        // never runs again only had a line prefetched).
         if (early) {
             const long long qn = lo + threadIdx.x;
             if (qn < hi) {
                 const int lsn = find_segment(S, qn);
                 const LatticeDesc &Ldn = seg_desc(P, S, lsn);
-                if (!Ldn.sub2 && g + 1 < S.seg_part[lsn] && Ldn.K * staged_bytes(Ldn.d) > (64LL << 20)) {
+                if (!Ldn.sub2 && Ldn.K * staged_bytes(Ldn.d) > (64LL << 20)) {
                     int dx, dy, dz;
                     active_domain(Ldn, qn - S.seg_base[lsn], (int)((S.seg_t0[lsn] + g + 1) & 7), dx, dy, dz);
                     const int32_t *cp = Ldn.counts + domain_index(Ldn.nd, dx, dy, dz) * kCountStride;

@@ -23,7 +23,9 @@ WRAPPER = os.path.join(ROOT, "oracle", "__init__.py")
 # once.  Every mutant changes some result the pins can reach: a slip that is
 # equal to the original on every input the pins use (floor(x 2^63) * 2 for
 # floor(x 2^64), equal for x >= 2^-10; (w0 >> 12) 2^-52 for u01, within
-# 2^-53 of it) is not one.
+# 2^-53 of it; the enumeration's ground-state shift, which cancels in every
+# average; the class-grouped BKL's skip of a partner listed twice, whose
+# second update finds the class already moved) is not one.
 MUTANTS = {
     # Eq. 3, the Glauber rate
     "rate sign": ("r[c] = 1.0 / (1.0 + exp(x));", "r[c] = 1.0 / (1.0 + exp(-x));"),
@@ -92,6 +94,11 @@ MUTANTS = {
     "class BKL rank word": ("const uint64_t j = (uint64_t)(((u128)w[1] * (uint64_t)n[c]) >> 64);",
                             "const uint64_t j = (uint64_t)(((u128)w[2] * (uint64_t)n[c]) >> 64);"),
     "energy field sign": ("*E = -J * (double)bonds - H * (double)mag;", "*E = -J * (double)bonds + H * (double)mag;"),
+    # the two-colour draw, the bounds' slack, the sampling of m(t)
+    "two-colour draw bit": ("return (int)(w[0] >> 63);", "return (int)(w[0] & 1);"),
+    "bound slack dropped": ("#define ORACLE_BOUND_SLACK (1.0 + 0x1p-32)", "#define ORACLE_BOUND_SLACK (1.0)"),
+    "m sampled after the step": ("while (g < ntimes && times[g] < t + dt) m_out[g++] = (double)M / (double)N;",
+                                 "while (g < ntimes && times[g] < t) m_out[g++] = (double)M / (double)N;"),
 }
 
 # name -> (text of oracle/__init__.py, its replacement): slips in the wrapper

@@ -288,6 +288,8 @@ int spkmc_set_spins_packed(spkmc_t *h, const uint8_t *host_bits, size_t nbytes);
  * event_log_capacity events after create, spkmc_clear_event_log or
  * spkmc_set_state (which restarts it at the restored cycle). */
 int spkmc_get_event_log(spkmc_t *h, spkmc_event *buf, size_t cap, size_t *n_out);
+/* Synchronise and empty the event log: it fills again from the current
+ * cycle on. */
 int spkmc_clear_event_log(spkmc_t *h);
 /* Checkpoint scalars (with get/set_spins the state is complete: the random
  * numbers are counter-based, so a resumed run is bit-identical). */
@@ -298,6 +300,9 @@ int spkmc_class_counts(spkmc_t *h, int32_t *host_counts, size_t n);
 /* Recount every domain from the spins on the device and report how many
  * domains differ from the maintained counts (0 when consistent). */
 int spkmc_check_counts(spkmc_t *h, int64_t *mismatched_domains);
+/* Sizes of the lattice (resolved domain edge, K, K_act, device bytes) and
+ * the launch shape; grid_ctas is that of the last launch, 0 before the first.
+ * Does not synchronise. */
 int spkmc_info_get(spkmc_t *h, spkmc_info *out);
 
 /* ---- batched and served ensembles --------------------------------------- */
@@ -306,6 +311,8 @@ int spkmc_info_get(spkmc_t *h, spkmc_info *out);
  * domains; each lattice keeps its own R_max, clock, cycle counter and
  * random streams, so its trajectory is bit-identical to a solo run. */
 int spkmc_batch_create(int32_t capacity, const spkmc_config *cfg, spkmc_batch_t **out);
+/* Release every slot and the batch; NULL-safe.  Synchronises the stream
+ * first. */
 void spkmc_batch_destroy(spkmc_batch_t *b);
 /* Admit a lattice into a free slot with a budget of `cycles` cycles
  * (< 0: unlimited).  EBUSY when no slot is free. */
@@ -323,7 +330,12 @@ int spkmc_batch_run_recorded(spkmc_batch_t *b, int64_t every, int32_t nrec, spkm
 int spkmc_batch_poll(spkmc_batch_t *b, int32_t *done_slots, int32_t cap, int32_t *n);
 /* Free a slot's device memory; the slot may be admitted again. */
 int spkmc_batch_retire(spkmc_batch_t *b, int32_t slot);
+/* Wait for the batch's stream and report kernel-side errors, as
+ * spkmc_synchronize. */
 int spkmc_batch_synchronize(spkmc_batch_t *b);
+/* The single-lattice read-outs for one slot (spkmc_observables,
+ * spkmc_get_spins, spkmc_get_event_log); EINVAL for a slot that is not
+ * live. */
 int spkmc_batch_observables(spkmc_batch_t *b, int32_t slot, spkmc_obs *out);
 int spkmc_batch_get_spins(spkmc_batch_t *b, int32_t slot, int8_t *host_buf, size_t n);
 int spkmc_batch_get_event_log(spkmc_batch_t *b, int32_t slot, spkmc_event *buf, size_t cap,
